@@ -1,0 +1,266 @@
+"""CPU oracle for the coset LDE + Poseidon-w12 Merkle commitment.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  The product
+library never loads it and shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, ``unsigned __int128`` and
+``%``); this module only builds it with gcc and marshals numpy arrays.
+Every function below follows one step of the commitment definition; the
+paper passage each follows is cited in ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+P = 0xFFFFFFFF00000001
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+_lock = threading.Lock()
+_lib = None
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain gcc, no CUDA)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, SRC, "-lpthread"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(LIB)
+            u64, u32, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+            sig = {
+                "orc_add": (u64, [u64, u64]),
+                "orc_sub": (u64, [u64, u64]),
+                "orc_mul": (u64, [u64, u64]),
+                "orc_pow": (u64, [u64, u64]),
+                "orc_inv": (u64, [u64]),
+                "orc_root_of_unity": (u64, [u32]),
+                "orc_bitrev": (u32, [u64, u32]),
+                "orc_ntt": (i32, [_u64p, u32, i32]),
+                "orc_lde": (i32, [_u64p, u32, u32, u32, _u64p, u32, i32]),
+                "orc_coeffs": (i32, [_u64p, u32, u32, _u64p, i32]),
+                "orc_lde_rows": (i32, [_u64p, u32, u32, u32, _u64p, u32, _u64p, i32]),
+                "orc_splitmix64_next": (u64, [_u64p]),
+                "orc_mds_check": (i32, [_u64p]),
+                "orc_poseidon_params": (u32, [_u64p, _u64p]),
+                "orc_permute": (None, [_u64p]),
+                "orc_hash": (None, [_u64p, u32, _u64p]),
+                "orc_compress": (None, [_u64p, _u64p, _u64p]),
+                "orc_leaf_hashes": (i32, [_u64p, u32, u32, u64, _u64p, i32]),
+                "orc_merkle_level": (i32, [_u64p, u64, _u64p, i32]),
+                "orc_merkle": (i32, [_u64p, u32, u32, u32, u32, _u64p, _u64p, i32]),
+                "orc_merkle_path": (i32, [_u64p, u32, u32, u64, _u64p]),
+                "orc_merkle_verify": (i32, [_u64p, u32, u32, u32, u64, _u64p, _u64p]),
+                "orc_commit": (i32, [_u64p, u32, u32, u32, u32, _u64p, u32, _u64p, _u64p, i32]),
+                "orc_domain_log2": (u32, [u64]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.uint64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_u64p)
+
+
+def _u64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+
+
+# --- field ------------------------------------------------------------
+def add(a: int, b: int) -> int:
+    return lib().orc_add(a, b)
+
+
+def sub(a: int, b: int) -> int:
+    return lib().orc_sub(a, b)
+
+
+def mul(a: int, b: int) -> int:
+    return lib().orc_mul(a, b)
+
+
+def pow_(a: int, e: int) -> int:
+    return lib().orc_pow(a, e)
+
+
+def inv(a: int) -> int:
+    return lib().orc_inv(a)
+
+
+def root_of_unity(log_m: int) -> int:
+    return lib().orc_root_of_unity(log_m)
+
+
+def bitrev(x: int, bits: int) -> int:
+    return lib().orc_bitrev(x, bits)
+
+
+# --- NTT / LDE ---------------------------------------------------------
+def ntt(x, inverse: bool = False) -> np.ndarray:
+    a = _u64(x).copy()
+    log_m = int(a.size).bit_length() - 1
+    assert a.size == 1 << log_m
+    assert lib().orc_ntt(_p(a), log_m, 1 if inverse else 0) == 0
+    return a
+
+
+def intt(x) -> np.ndarray:
+    return ntt(x, inverse=True)
+
+
+def ld_for(c: int) -> int:
+    return c + (c & 1)
+
+
+def lde(cols, rate_bits: int, ld: int | None = None, threads: int | None = None) -> np.ndarray:
+    """cols [c][n] -> row-major LDE [N][ld] in bit-reversed row order."""
+    a = _u64(cols)
+    c, n = a.shape
+    log_n = n.bit_length() - 1
+    ld = ld_for(c) if ld is None else ld
+    out = np.empty(((n << rate_bits), ld), dtype=np.uint64)
+    rc = lib().orc_lde(_p(a), c, log_n, rate_bits, _p(out), ld, threads or default_threads())
+    assert rc == 0
+    return out
+
+
+def coeffs(cols, threads: int | None = None) -> np.ndarray:
+    a = _u64(cols)
+    c, n = a.shape
+    out = np.empty_like(a)
+    lib().orc_coeffs(_p(a), c, n.bit_length() - 1, _p(out), threads or default_threads())
+    return out
+
+
+def lde_rows(coef, rate_bits: int, rows, threads: int | None = None) -> np.ndarray:
+    """Committed LDE rows ``rows`` (bit-reversed indices) by Horner evaluation
+    of the coefficient columns at 7 * w_N^bitrev(t)."""
+    a = _u64(coef)
+    c, n = a.shape
+    r = _u64(rows)
+    out = np.empty((r.size, c), dtype=np.uint64)
+    lib().orc_lde_rows(_p(a), c, n.bit_length() - 1, rate_bits, _p(r), r.size, _p(out),
+                       threads or default_threads())
+    return out
+
+
+# --- Poseidon ------------------------------------------------------------
+def poseidon_params() -> tuple[np.ndarray, np.ndarray, int]:
+    rc = np.zeros(360, np.uint64)
+    mds = np.zeros(144, np.uint64)
+    tries = lib().orc_poseidon_params(_p(rc), _p(mds))
+    return rc.reshape(30, 12), mds.reshape(12, 12), tries
+
+
+def mds_check(m) -> int:
+    a = _u64(m).reshape(144).copy()
+    return lib().orc_mds_check(_p(a))
+
+
+def permute(state) -> np.ndarray:
+    s = _u64(state).copy()
+    assert s.size == 12
+    lib().orc_permute(_p(s))
+    return s
+
+
+def hash_(x) -> np.ndarray:
+    a = _u64(x)
+    out = np.zeros(4, np.uint64)
+    lib().orc_hash(_p(a) if a.size else None, a.size, _p(out))
+    return out
+
+
+def compress(left, right) -> np.ndarray:
+    out = np.zeros(4, np.uint64)
+    lib().orc_compress(_p(_u64(left)), _p(_u64(right)), _p(out))
+    return out
+
+
+def leaf_hashes(rows: np.ndarray, width: int, threads: int | None = None) -> np.ndarray:
+    a = _u64(rows)
+    nrows, ld = a.shape
+    out = np.empty((nrows, 4), np.uint64)
+    lib().orc_leaf_hashes(_p(a), ld, width, nrows, _p(out), threads or default_threads())
+    return out
+
+
+def merkle_level(below: np.ndarray, threads: int | None = None) -> np.ndarray:
+    a = _u64(below).reshape(-1, 4)
+    cnt = a.shape[0] // 2
+    out = np.empty((cnt, 4), np.uint64)
+    lib().orc_merkle_level(_p(a), cnt, _p(out), threads or default_threads())
+    return out
+
+
+def tree_len(log_rows: int, cap_height: int) -> int:
+    """u64 words below the cap: levels 0 .. logN-h-1 of N >> k digests."""
+    N = 1 << log_rows
+    return (2 * N - (2 << cap_height)) * 4
+
+
+def merkle(rows: np.ndarray, width: int, cap_height: int, threads: int | None = None):
+    a = _u64(rows)
+    nrows, ld = a.shape
+    log_rows = nrows.bit_length() - 1
+    tree = np.zeros(tree_len(log_rows, cap_height), np.uint64)
+    cap = np.zeros((1 << cap_height) * 4, np.uint64)
+    rc = lib().orc_merkle(_p(a), ld, width, log_rows, cap_height, _p(tree) if tree.size else None,
+                          _p(cap), threads or default_threads())
+    assert rc == 0
+    return tree, cap.reshape(-1, 4)
+
+
+def merkle_path(tree: np.ndarray, log_rows: int, cap_height: int, t: int) -> np.ndarray:
+    path = np.zeros(max(1, log_rows - cap_height) * 4, np.uint64)
+    assert lib().orc_merkle_path(_p(_u64(tree)) if tree.size else None, log_rows, cap_height, t,
+                                 _p(path)) == 0
+    return path[: (log_rows - cap_height) * 4].reshape(-1, 4)
+
+
+def merkle_verify(row, width: int, log_rows: int, cap_height: int, t: int, path, cap) -> bool:
+    r = _u64(row)
+    pth = _u64(path).reshape(-1)
+    if pth.size == 0:
+        pth = np.zeros(4, np.uint64)
+    return bool(lib().orc_merkle_verify(_p(r), width, log_rows, cap_height, t, _p(pth),
+                                        _p(_u64(cap).reshape(-1))))
+
+
+def commit(cols, rate_bits: int, cap_height: int, threads: int | None = None):
+    """Full commitment: returns (lde [N][ld], tree, cap [2^h][4])."""
+    a = _u64(cols)
+    c, n = a.shape
+    e = lde(a, rate_bits, threads=threads)
+    tree, cap = merkle(e, c, cap_height, threads=threads)
+    return e, tree, cap
+
+
+def domain_log2(G: int) -> int:
+    return lib().orc_domain_log2(G)
