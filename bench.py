@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of the LDE + Poseidon-Merkle commitment on GB300.
+
+One step = one commit through the library's public entry point
+(v3c_commit: coset LDE, leaf hash, Merkle levels to the cap, on a resident
+object) followed by its release.  The default workload is the large commit:
+135 trace columns x 2^20 rows, rate_bits 3 (2^23 LDE rows, 9.06 GB
+resident), cap height 4.  Inputs are resident in HBM when the timed region
+starts; every buffer is larger than L2 (1.13 GB in, 9.06 GB LDE), so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
+reference arm of this tier) on a bounded sample of the same workload.
+Under torchrun each rank commits its own batch of the same shape on its
+own GPU (independent problems: weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "LDE+Merkle commit Gelem/s vs roofline; p50/p99 audit-commit latency at load"
+WORKLOADS = {
+    "large_135x2_20": synth.LARGE_135x2_20,
+    "trace_135x2_16": synth.TRACE_135x2_16,
+    "plain_8x2_10": synth.PLAIN_8x2_10,
+}
+# Algorithmic work per Poseidon permutation in 32x32->64 wide-multiply units
+# (minimal exact form: S-boxes 1888, full-round small MDS 2304, sparse
+# partial rounds 2024 + 576) and per NTT butterfly multiplication.
+W_PER_PERM = 6792
+W_PER_NTT_MUL = 4
+# Integer-pipe peak derived from unit counts and clocks: SMs x wide
+# multiplies per SM per clock x maximum SM clock.
+SMS = 152
+WIDE_MUL_PER_SM_CLK = 64
+SM_MAX_MHZ = 2070.0
+# DRAM traffic of one leaf-hash launch on this workload (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum; see profiles/); None when the
+# kernel changed since the capture.
+LEAF_HASH_TRAFFIC = {}
+# The CPU-baseline / reference-arm sample: the full commit of the same column
+# mix at fewer rows.
+CPU_SAMPLE = synth.Shape(c=135, log_n=14, rate_bits=3, cap_height=4, seed=0)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(steps: int = 1) -> dict:
+    import oracle
+
+    s = CPU_SAMPLE
+    x = s.inputs()
+    threads = oracle.default_threads()
+    oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)  # warm (constants, pages)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": s.lde_elems() / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
+            "sample": f"full oracle commit of {s.c} columns x 2^{s.log_n} rows (same column mix), "
+                      f"rate_bits {s.rate_bits}, cap height {s.cap_height}; {dt:.2f} s per commit"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    s = CPU_SAMPLE
+    x = s.inputs()
+    threads = oracle.default_threads()
+    for _ in range(args.warmup):
+        oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = s.lde_elems() / dt / 1e9
+    w = WORKLOADS[args.workload]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(args.workload, w),
+        "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "Gelem/s",
+                         "sample": f"oracle commit of {s.c} x 2^{s.log_n} rows per step (bounded sample of the "
+                                   f"{args.workload} workload's column mix)"},
+        "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(name, s):
+    return {"workload": name, "columns": s.c, "log_rows": s.log_n, "rate_bits": s.rate_bits,
+            "cap_height": s.cap_height, "lde_rows": 1 << s.log_N, "mix": s.mix,
+            "l2": "inputs larger than L2 (no flush needed)" if s.lde_elems() * 8 > 129e6 else "L2 flush"}
+
+
+def run_v3c(args):
+    import torch
+
+    import paper_2603_03065_gb300 as v3c
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    s = WORKLOADS[args.workload]
+    s = synth.Shape(c=s.c, log_n=s.log_n, rate_bits=s.rate_bits, cap_height=s.cap_height, seed=s.seed,
+                    mix=s.mix, batch=rank)
+    x = s.inputs()
+    ctx = v3c.Context(local_rank, flags=v3c.FLAG_TIMING)
+    stream = torch.cuda.current_stream()
+    d_x = v3c.to_device_u64(x)
+
+    def step():
+        cid = ctx.commit([(d_x, s.rate_bits, s.cap_height)], stream=stream)[0]
+        ctx.release(cid)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    ctx.stage_stats(reset=True)
+    l0 = ctx.kernel_launches()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = ctx.kernel_launches() - l0
+    stats = ctx.stage_stats(reset=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    value = world * s.lde_elems() / (ms * 1e-3) / 1e9
+
+    # end to end: pinned host input -> device inside the call, cap back to host
+    pinned = torch.from_numpy(x.view(np.int64)).pin_memory()
+    x_pinned = pinned.numpy().view(np.uint64)
+
+    def step_e2e():
+        cid = ctx.commit([(x_pinned, s.rate_bits, s.cap_height)], stream=stream)[0]
+        cap = ctx.cap(cid)
+        ctx.release(cid)
+        return cap
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * s.lde_elems() / e2e_s / 1e9
+
+    # roofline of the dominant kernel (leaf hash), timed by events on its stream
+    leaf_ms, leaf_n = stats["leaf_hash"]
+    N = 1 << s.log_N
+    perms_leaf = N * (-(-s.c // 8))
+    leaf_ms_per = leaf_ms / max(leaf_n, 1)
+    achieved = W_PER_PERM * perms_leaf / (leaf_ms_per * 1e-3) / 1e12
+    peak = SMS * WIDE_MUL_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = LEAF_HASH_TRAFFIC.get(args.workload)
+    stage_ms = {k: (v[0] / max(v[1], 1), int(v[1])) for k, v in stats.items()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(args.workload, s),
+            "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": int(x.nbytes),
+                    "d2h_bytes_per_step": int(32 << s.cap_height), "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": {"bound": "alu", "kernel": "k_leaf_hash", "achieved": achieved, "peak": peak,
+                         "unit": "T wide-mul/s", "frac": achieved / peak, "traffic": traffic,
+                         "work_per_launch": W_PER_PERM * perms_leaf, "ms_per_launch": leaf_ms_per},
+            "stages_ms_per_launch": stage_ms,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        if args.int_peak:
+            rate, _ = ctx.int_peak(10)
+            line["int_peak_measured"] = {"value": rate / 1e12, "unit": "T wide-mul/s",
+                                         "per_sm_clk_at_max": rate / (SMS * SM_MAX_MHZ * 1e6)}
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["v3c", "reference"], default="v3c")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large_135x2_20")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--int-peak", action="store_true", help="also run the integer-pipe microbenchmark")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_v3c(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,241 @@
+/*
+ * v3c: polynomial commitment of trace columns on a GB300 (sm_103a).
+ *
+ * What it computes (V3DB, arXiv 2603.03065).  The paper's prover is built on
+ * Plonky2 with its default field and FRI setup (Sec. 5, evaluation
+ * environment).  It spends its time in FFT-based polynomial arithmetic over
+ * a padded power-of-two domain G_B = 2^ceil(log2 G) (Sec. 2.1, "binning
+ * effect"; Sec. 5.2, Metrics).  It commits with Poseidon (Sec. 4.3) in
+ * balanced Merkle trees whose openings follow the bits of the leaf index
+ * (Sec. 4.3; Sec. 4.4, MerkleOpen).  The paper fixes no numeric parameters.
+ * This library implements the following readings:
+ *
+ *   field   F_p, p = 2^64 - 2^32 + 1, generator g = 7; every value passed
+ *           in or out is a canonical uint64 in [0, p).
+ *   LDE     for each column: a = iNTT_n(col); b_i = a_i * 7^i for i < n and
+ *           0 for n <= i < N = n * 2^rate_bits; E = NTT_N(b), so that
+ *           E_j = P(7 * w_N^j).  The LDE matrix is row-major [N][ld].  Row t
+ *           holds E_{bitrev_{log N}(t)} of every column.  Columns c..ld-1
+ *           are written as zero.
+ *   hash    Poseidon, width 12, rate 8, capacity 4, S-box x^7, rounds 4 full
+ *           + 22 partial + 4 full.  Each round does ARC, then the S-box, then
+ *           the MDS.  The round constants come from SplitMix64 seeded with
+ *           "V3DBPOS1".  The MDS is the first small-entry circulant drawn
+ *           whose every square minor is nonzero.
+ *   leaf    sponge in overwrite mode over the first `width` entries of a row
+ *           (chunks of 8, no padding).  The digest is lanes 0..3.  Rows of
+ *           width <= 4 are zero-padded to 4 instead of hashed.
+ *   tree    node = Perm(left || right || 0^4)[0..4), with the left child at
+ *           the even index, cut at a cap of 2^cap_height digests.
+ *           Storage is level-major: level 0 (N leaf digests), level 1
+ *           (N/2 digests), ..., level logN-h-1.  That is
+ *           (2N - 2^(h+1)) * 4 uint64 in all.  The cap (level logN-h) is
+ *           stored separately as [2^h][4].
+ *
+ * Conventions.  Every call returns a v3c_status.  No C++ exception crosses
+ * the ABI and nothing aborts.  The caller owns every pointer it passes in.
+ * "d_" pointers are device pointers of the context's device; "h_" pointers
+ * are host pointers.  A cudaStream_t is passed as void*; NULL is the legacy
+ * default stream.  A call that takes a stream only enqueues work on it.  The
+ * results are valid once that stream reaches the point of the call.  Input
+ * canonicity (< p) is a precondition.  V3C_FLAG_VALIDATE makes v3c_commit
+ * and the serving loop check it and return V3C_EINVAL.
+ */
+#ifndef V3C_H
+#define V3C_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    V3C_OK = 0,
+    V3C_EINVAL = 1,     /* bad argument, shape or non-canonical input */
+    V3C_ENOMEM = 2,     /* device memory or HBM budget exhausted */
+    V3C_ECUDA = 3,      /* a CUDA runtime call failed; see v3c_last_error_detail */
+    V3C_EAGAIN = 4,     /* not finished yet, or submit queue full */
+    V3C_ETIMEDOUT = 5,  /* a bounded wait gave up */
+    V3C_ENOTFOUND = 6,  /* unknown commit id or ticket */
+    V3C_ECANCELED = 7   /* request cancelled or serving stopped */
+} v3c_status;
+
+typedef struct v3c_ctx v3c_ctx;
+typedef uint64_t v3c_commit_id;
+
+/* Limits of this build. */
+#define V3C_MAX_LOG_N 22        /* input rows n = 2^log_n (log_n + rate_bits <= 25) */
+#define V3C_MAX_LOG_LDE 25      /* N = 2^(log_n + rate_bits) */
+#define V3C_MAX_RATE_BITS 4
+
+#define V3C_FLAG_VALIDATE 0x1u  /* check that inputs are canonical */
+
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* resident commit objects + scratch; 0 = 90% of free memory */
+    uint32_t max_inflight;      /* serving: concurrent batches on the device (0 = 4) */
+    uint32_t flags;             /* V3C_FLAG_* applied to every call */
+    uint32_t autotune;          /* 1 = time tile variants once per shape, 0 = defaults */
+    uint32_t timeout_ms;        /* bounded host waits (0 = 60000) */
+} v3c_config;
+
+/* Returns a static English description of a status code. */
+const char* v3c_strerror(v3c_status s);
+
+/* Detail of the last failure on this context (thread-local copy, never NULL). */
+const char* v3c_last_error_detail(v3c_ctx* ctx);
+
+/* Creates a context on CUDA device `device`.  cfg may be NULL (defaults).
+ * The first call on a device derives the Poseidon parameters and allocates
+ * nothing else.  *out receives the context; v3c_destroy frees it.  Errors:
+ * EINVAL (bad device or out NULL), ECUDA, ENOMEM. */
+v3c_status v3c_create(int device, const v3c_config* cfg, v3c_ctx** out);
+
+/* Stops serving, waits for in-flight work and frees every resident object,
+ * plan table and scratch buffer of the context. */
+v3c_status v3c_destroy(v3c_ctx* ctx);
+
+/* Coset low-degree extension of c columns (the LDE reading above).
+ *   d_cols   device, column-major [c][n] (column j at d_cols + j*n), n = 2^log_n
+ *   d_lde    device, row-major [N][ld], N = n * 2^rate_bits; ld >= c.  Columns
+ *            c..ld-1 are zero-filled.  A 16-byte aligned d_lde with even ld
+ *            takes the vector-store path.
+ * Scratch (about (n + N) * c * 8 bytes) is taken from the context's arena and
+ * kept for reuse.  Limits: log_n <= V3C_MAX_LOG_N, rate_bits <= V3C_MAX_RATE_BITS,
+ * log_n + rate_bits <= V3C_MAX_LOG_LDE.  Errors: EINVAL (shape, NULL),
+ * ENOMEM (arena), ECUDA. */
+v3c_status v3c_lde(v3c_ctx* ctx, const uint64_t* d_cols, uint32_t c, uint32_t log_n,
+                   uint32_t rate_bits, uint64_t* d_lde, uint32_t ld, void* stream);
+
+/* Merkle tree over 2^log_rows rows (the leaf and tree readings above).
+ *   d_rows   device, row-major, stride ld (uint64), the first `width` entries hashed
+ *   d_tree   device, (2N - 2^(h+1)) * 4 uint64, level-major (may be NULL iff h == log_rows)
+ *   d_cap    device, 2^h * 4 uint64
+ * Uses no scratch.  Errors: EINVAL (h > log_rows, width > ld, NULL), ECUDA. */
+v3c_status v3c_merkle(v3c_ctx* ctx, const uint64_t* d_rows, uint32_t ld, uint32_t width,
+                      uint32_t log_rows, uint32_t cap_height, uint64_t* d_tree, uint64_t* d_cap,
+                      void* stream);
+
+/* One commit request: LDE of `cols` followed by the Merkle tree of its rows. */
+typedef struct {
+    const uint64_t* cols;  /* [c][n] column-major, device (on_device=1) or host (on_device=0) */
+    int32_t on_device;
+    uint32_t c;
+    uint32_t log_n;
+    uint32_t rate_bits;
+    uint32_t cap_height;
+} v3c_commit_desc;
+
+/* Batched commit (many uneven shapes in one launch per stage).  For each desc
+ * it allocates a resident object that holds the LDE [N][ld] (ld = c rounded
+ * up to even) and the tree, and enqueues every stage on `stream`.  The stages
+ * run as one persistent launch each over all descs (under a CUDA graph when
+ * the same batch shape repeats).  ids[i] receives the object id.  Host
+ * inputs are copied to the device inside the call.  The objects stay
+ * resident until v3c_release.  Errors: EINVAL, ENOMEM (the HBM budget would
+ * be exceeded; nothing is allocated), ECUDA. */
+v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v3c_commit_id* ids,
+                      void* stream);
+
+/* Device pointers and shape of a resident object (valid until release).
+ * Any output pointer may be NULL. */
+v3c_status v3c_commit_buffers(v3c_ctx* ctx, v3c_commit_id id, uint64_t** d_lde, uint32_t* ld,
+                              uint64_t** d_tree, uint64_t** d_cap, uint32_t* log_rows,
+                              uint32_t* cap_height);
+
+/* Copies the cap ([2^h][4]) of a resident object to h_cap.  Synchronises
+ * with the object's producing stream.  Errors: ENOTFOUND, ECUDA. */
+v3c_status v3c_commit_cap(v3c_ctx* ctx, v3c_commit_id id, uint64_t* h_cap);
+
+/* Opening of leaf `leaf` (MerkleOpen, Sec. 4.4).  h_row receives the c
+ * committed values of LDE row `leaf`.  h_path receives (logN - h) sibling
+ * digests [k][4] for k = 0 .. logN-h-1: the sibling at level k is
+ * level_k[(leaf >> k) ^ 1].  The path ends at cap entry leaf >> (logN - h).
+ * Errors: ENOTFOUND, EINVAL (leaf >= N), ECUDA. */
+v3c_status v3c_open(v3c_ctx* ctx, v3c_commit_id id, uint64_t leaf, uint64_t* h_row,
+                    uint64_t* h_path);
+
+/* Frees a resident object (after its work has completed). */
+v3c_status v3c_release(v3c_ctx* ctx, v3c_commit_id id);
+
+/* Bytes of HBM a resident commit of this shape occupies (LDE + tree + cap). */
+uint64_t v3c_commit_footprint(uint32_t c, uint32_t log_n, uint32_t rate_bits, uint32_t cap_height);
+
+/* ---------------- serving (continuous batching) ---------------- */
+
+typedef struct {
+    uint32_t queue_capacity;    /* pending submissions (0 = 4096) */
+    uint32_t max_batch;         /* requests fused into one batched launch (0 = 32) */
+    uint32_t max_inflight;      /* batches in flight on separate streams (0 = ctx setting) */
+    uint32_t flags;             /* V3C_FLAG_VALIDATE */
+} v3c_serve_cfg;
+
+typedef enum {
+    V3C_REQ_QUEUED = 0,
+    V3C_REQ_ADMITTED = 1,  /* memory reserved, inputs staged */
+    V3C_REQ_RUNNING = 2,   /* part of a batch launched on the device */
+    V3C_REQ_DONE = 3,      /* cap ready; object resident until release */
+    V3C_REQ_FAILED = 4
+} v3c_req_state;
+
+typedef struct {
+    double t_submit, t_admit, t_start, t_done;  /* seconds, steady clock of the context */
+} v3c_req_times;
+
+/* Starts the scheduler thread.  Requests are admitted in arrival order while
+ * their footprint fits the HBM budget minus what is resident.  All requests
+ * admitted by one scheduler pass form one batched launch, and up to
+ * max_inflight batches run at once on separate streams.  A request that
+ * arrives while others are on the device joins the next pass. */
+v3c_status v3c_serve_start(v3c_ctx* ctx, const v3c_serve_cfg* cfg);
+
+/* Non-blocking submit.  desc->cols is a host pointer (on_device = 0), copied
+ * into library memory before the call returns, or a device pointer
+ * (on_device = 1) that the caller keeps alive until the state reaches DONE.
+ * *ticket receives the id, which is also the commit id for v3c_open and
+ * v3c_release.  Errors: EAGAIN (queue full), EINVAL, ECANCELED (not
+ * serving). */
+v3c_status v3c_serve_submit(v3c_ctx* ctx, const v3c_commit_desc* desc, uint64_t* ticket);
+
+/* Non-blocking poll.  Returns OK when DONE: h_cap (if not NULL) receives the
+ * cap.  Returns EAGAIN while queued or running, or the failure status.
+ * state and times may be NULL. */
+v3c_status v3c_serve_poll(v3c_ctx* ctx, uint64_t ticket, v3c_req_state* state, uint64_t* h_cap,
+                          v3c_req_times* times);
+
+/* Stops the scheduler after the in-flight batches complete.  Queued
+ * requests resolve to FAILED with ECANCELED. */
+v3c_status v3c_serve_stop(v3c_ctx* ctx);
+
+/* ---------------- introspection ---------------- */
+
+/* Number of this library's kernel launches enqueued by the context so far. */
+uint64_t v3c_kernel_launches(v3c_ctx* ctx);
+
+/* Per-stage timing.  With V3C_FLAG_TIMING in the context's flags, every
+ * stage launch is bracketed by two CUDA events recorded on the stream it is
+ * launched on.  v3c_stage_stats waits for the pending events and returns
+ * the accumulated device time and launch count of each stage since the last
+ * reset.  Stages: 0 = LDE stage A (inverse column DFTs), 1 = stage B (inverse
+ * + coset + forward DFT), 2 = stage C (forward DFTs and row writes), 3 =
+ * leaf hash, 4 = Merkle levels. */
+#define V3C_FLAG_TIMING 0x2u
+#define V3C_NUM_STAGES 5
+typedef struct {
+    double ms[V3C_NUM_STAGES];
+    uint64_t launches[V3C_NUM_STAGES];
+} v3c_stage_stats_t;
+v3c_status v3c_stage_stats(v3c_ctx* ctx, v3c_stage_stats_t* out, int reset);
+
+/* Microbenchmark of the integer multiply pipe: independent chains of
+ * 32x32->64 wide multiply-adds on every SM.  Returns wide multiplies per
+ * second in *rate (best of `reps`) and the kernel's clock-derived SM MHz in
+ * *mhz.  Synchronous. */
+v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* V3C_H */

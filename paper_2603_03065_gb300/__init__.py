@@ -1,0 +1,333 @@
+"""Python binding of libv3c.so: the LDE + Poseidon-Merkle polynomial commitment.
+
+Argument marshalling only.  Every step of the commitment runs in the CUDA
+kernels of ``libv3c.so``, and importing this module fails loudly if the
+library has not been built (``python -m paper_2603_03065_gb300.build``).  PyTorch
+provides device memory and streams.  Field elements are carried in int64
+tensors that hold the uint64 bit patterns.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libv3c.so")
+P = 0xFFFFFFFF00000001
+
+V3C_OK, V3C_EINVAL, V3C_ENOMEM, V3C_ECUDA, V3C_EAGAIN, V3C_ETIMEDOUT, V3C_ENOTFOUND, V3C_ECANCELED = range(8)
+REQ_QUEUED, REQ_ADMITTED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(5)
+FLAG_VALIDATE = 1
+MAX_LOG_N, MAX_LOG_LDE, MAX_RATE_BITS = 22, 25, 4
+
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_vp = ctypes.c_void_p
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+class V3CError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"v3c status {status}: {detail}")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", _u64), ("max_inflight", _u32), ("flags", _u32),
+                ("autotune", _u32), ("timeout_ms", _u32)]
+
+
+class CommitDesc(ctypes.Structure):
+    _fields_ = [("cols", _vp), ("on_device", ctypes.c_int32), ("c", _u32), ("log_n", _u32),
+                ("rate_bits", _u32), ("cap_height", _u32)]
+
+
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("queue_capacity", _u32), ("max_batch", _u32), ("max_inflight", _u32), ("flags", _u32)]
+
+
+FLAG_TIMING = 2
+STAGES = ("lde_a", "lde_b", "lde_c", "leaf_hash", "merkle")
+
+
+class StageStats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_uint64 * 5)]
+
+
+class ReqTimes(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+# Every symbol include/v3c.h declares, with its ctypes signature.
+SIGNATURES = {
+    "v3c_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "v3c_last_error_detail": (ctypes.c_char_p, [_vp]),
+    "v3c_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Config), ctypes.POINTER(_vp)]),
+    "v3c_destroy": (ctypes.c_int, [_vp]),
+    "v3c_lde": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _vp, _u32, _vp]),
+    "v3c_merkle": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp]),
+    "v3c_commit": (ctypes.c_int, [_vp, ctypes.POINTER(CommitDesc), _u32, _u64p, _vp]),
+    "v3c_commit_buffers": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(_vp), ctypes.POINTER(_u32),
+                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u32),
+                                          ctypes.POINTER(_u32)]),
+    "v3c_commit_cap": (ctypes.c_int, [_vp, _u64, _u64p]),
+    "v3c_open": (ctypes.c_int, [_vp, _u64, _u64, _u64p, _u64p]),
+    "v3c_release": (ctypes.c_int, [_vp, _u64]),
+    "v3c_commit_footprint": (_u64, [_u32, _u32, _u32, _u32]),
+    "v3c_serve_start": (ctypes.c_int, [_vp, ctypes.POINTER(ServeCfg)]),
+    "v3c_serve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(CommitDesc), _u64p]),
+    "v3c_serve_poll": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int), _u64p, ctypes.POINTER(ReqTimes)]),
+    "v3c_serve_stop": (ctypes.c_int, [_vp]),
+    "v3c_kernel_launches": (_u64, [_vp]),
+    "v3c_stage_stats": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_int]),
+    "v3c_int_peak": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libv3c.so and binds every exported entry point.  Raises if the
+    library is missing: there is no fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2603_03065_gb300.build` "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    return load().v3c_strerror(status).decode()
+
+
+def footprint(c: int, log_n: int, rate_bits: int, cap_height: int) -> int:
+    return load().v3c_commit_footprint(c, log_n, rate_bits, cap_height)
+
+
+def tree_words(log_rows: int, cap_height: int) -> int:
+    N = 1 << log_rows
+    return (2 * N - (2 << cap_height)) * 4
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def to_device_u64(a: np.ndarray, device="cuda"):
+    """uint64 numpy array -> int64 CUDA tensor with the same bits."""
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
+
+
+def to_host_u64(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+@dataclass
+class Opening:
+    row: np.ndarray
+    path: np.ndarray
+
+
+class Context:
+    """One v3c context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0, flags: int = 0):
+        self.lib = load()
+        cfg = Config(hbm_budget_bytes, max_inflight, flags, 0, 0)
+        h = _vp()
+        self._check(self.lib.v3c_create(device, ctypes.byref(cfg), ctypes.byref(h)), None)
+        self.h = h
+        self.device = device
+
+    def _check(self, st: int, h=...):
+        if st != V3C_OK:
+            hh = self.h if h is ... else h
+            detail = self.lib.v3c_last_error_detail(hh).decode() if hh else ""
+            raise V3CError(st, f"{strerror(st)}: {detail}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.v3c_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --------------------------------------------------------------- stages
+    def lde(self, cols, rate_bits: int, ld: int | None = None, out=None, stream=None):
+        """cols: int64 CUDA tensor [c][n] -> LDE [N][ld] (row-major, bit-reversed rows)."""
+        torch = _torch()
+        c, n = cols.shape
+        log_n = n.bit_length() - 1
+        ld = c + (c & 1) if ld is None else ld
+        N = n << rate_bits
+        if out is None:
+            out = torch.empty((N, ld), dtype=torch.int64, device=cols.device)
+        self._check(self.lib.v3c_lde(self.h, _ptr(cols), c, log_n, rate_bits, _ptr(out), ld, _stream(stream)))
+        return out
+
+    def merkle(self, rows, width: int, cap_height: int, tree=None, cap=None, stream=None):
+        torch = _torch()
+        N, ld = rows.shape
+        log_rows = N.bit_length() - 1
+        tw = tree_words(log_rows, cap_height)
+        if tree is None and tw:
+            tree = torch.empty(tw, dtype=torch.int64, device=rows.device)
+        if cap is None:
+            cap = torch.empty((1 << cap_height, 4), dtype=torch.int64, device=rows.device)
+        self._check(self.lib.v3c_merkle(self.h, _ptr(rows), ld, width, log_rows, cap_height,
+                                        _ptr(tree) if tw else None, _ptr(cap), _stream(stream)))
+        return tree, cap
+
+    def commit(self, items, stream=None) -> list[int]:
+        """items: list of (cols, rate_bits, cap_height); cols an int64 CUDA tensor
+        [c][n] or a uint64 numpy array (host input)."""
+        descs = (CommitDesc * len(items))()
+        keep = []
+        for i, (cols, r, h) in enumerate(items):
+            if isinstance(cols, np.ndarray):
+                a = np.ascontiguousarray(cols, dtype=np.uint64)
+                keep.append(a)
+                descs[i] = CommitDesc(a.ctypes.data, 0, a.shape[0], a.shape[1].bit_length() - 1, r, h)
+            else:
+                descs[i] = CommitDesc(cols.data_ptr(), 1, cols.shape[0], cols.shape[1].bit_length() - 1, r, h)
+        ids = (_u64 * len(items))()
+        self._check(self.lib.v3c_commit(self.h, descs, len(items), ids, _stream(stream)))
+        return list(ids)
+
+    def buffers(self, cid: int):
+        lde, tree, cap = _vp(), _vp(), _vp()
+        ld, logr, h = _u32(), _u32(), _u32()
+        self._check(self.lib.v3c_commit_buffers(self.h, cid, ctypes.byref(lde), ctypes.byref(ld),
+                                                ctypes.byref(tree), ctypes.byref(cap), ctypes.byref(logr),
+                                                ctypes.byref(h)))
+        return dict(lde=lde.value, ld=ld.value, tree=tree.value, cap=cap.value, log_rows=logr.value,
+                    cap_height=h.value)
+
+    def commit_views(self, cid: int, c: int):
+        """Copies of a resident object's LDE, tree and cap as numpy arrays."""
+        torch = _torch()
+        b = self.buffers(cid)
+        N = 1 << b["log_rows"]
+        out = {}
+        for key, words in (("lde", N * b["ld"]), ("tree", tree_words(b["log_rows"], b["cap_height"])),
+                           ("cap", 4 << b["cap_height"])):
+            arr = np.empty(words, np.uint64)
+            if words:
+                torch.cuda.synchronize()
+                cudart_memcpy_d2h(arr, b[key])
+            out[key] = arr
+        out["lde"] = out["lde"].reshape(N, b["ld"])
+        out["cap"] = out["cap"].reshape(-1, 4)
+        return out
+
+    def cap(self, cid: int) -> np.ndarray:
+        b = self.buffers(cid)
+        out = np.empty((1 << b["cap_height"]) * 4, np.uint64)
+        self._check(self.lib.v3c_commit_cap(self.h, cid, out.ctypes.data_as(_u64p)))
+        return out.reshape(-1, 4)
+
+    def open(self, cid: int, leaf: int, c: int) -> Opening:
+        b = self.buffers(cid)
+        k = b["log_rows"] - b["cap_height"]
+        row = np.zeros(c, np.uint64)
+        path = np.zeros(max(k, 1) * 4, np.uint64)
+        self._check(self.lib.v3c_open(self.h, cid, leaf, row.ctypes.data_as(_u64p), path.ctypes.data_as(_u64p)))
+        return Opening(row, path[: 4 * k].reshape(-1, 4))
+
+    def release(self, cid: int):
+        self._check(self.lib.v3c_release(self.h, cid))
+
+    # --------------------------------------------------------------- serving
+    def serve_start(self, queue_capacity=0, max_batch=0, max_inflight=0, flags=0):
+        cfg = ServeCfg(queue_capacity, max_batch, max_inflight, flags)
+        self._check(self.lib.v3c_serve_start(self.h, ctypes.byref(cfg)))
+
+    def serve_submit(self, cols: np.ndarray, rate_bits: int, cap_height: int) -> int:
+        a = np.ascontiguousarray(cols, dtype=np.uint64)
+        d = CommitDesc(a.ctypes.data, 0, a.shape[0], a.shape[1].bit_length() - 1, rate_bits, cap_height)
+        t = _u64()
+        st = self.lib.v3c_serve_submit(self.h, ctypes.byref(d), ctypes.byref(t))
+        if st == V3C_EAGAIN:
+            return -1
+        self._check(st)
+        return t.value
+
+    def serve_poll(self, ticket: int, cap_height: int | None = None):
+        """Returns (status, state, cap or None, times)."""
+        state = ctypes.c_int()
+        times = ReqTimes()
+        cap = None
+        capp = None
+        if cap_height is not None:
+            cap = np.zeros(4 << cap_height, np.uint64)
+            capp = cap.ctypes.data_as(_u64p)
+        st = self.lib.v3c_serve_poll(self.h, ticket, ctypes.byref(state), capp, ctypes.byref(times))
+        t = (times.t_submit, times.t_admit, times.t_start, times.t_done)
+        return st, state.value, (cap.reshape(-1, 4) if (cap is not None and st == V3C_OK) else None), t
+
+    def serve_stop(self):
+        self._check(self.lib.v3c_serve_stop(self.h))
+
+    # --------------------------------------------------------------- misc
+    def kernel_launches(self) -> int:
+        return self.lib.v3c_kernel_launches(self.h)
+
+    def stage_stats(self, reset: bool = False) -> dict:
+        """Device time (ms) and launches per stage, from CUDA events the library
+        records around each stage launch on its stream (needs FLAG_TIMING)."""
+        st = StageStats()
+        self._check(self.lib.v3c_stage_stats(self.h, ctypes.byref(st), 1 if reset else 0))
+        return {name: (st.ms[i], st.launches[i]) for i, name in enumerate(STAGES)}
+
+    def int_peak(self, reps: int = 10) -> tuple[float, float]:
+        rate, mhz = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.v3c_int_peak(self.h, reps, ctypes.byref(rate), ctypes.byref(mhz)))
+        return rate.value, mhz.value
+
+
+def cudart_memcpy_d2h(dst: np.ndarray, src_ptr: int):
+    """Device -> host copy of raw device memory via torch (no compute)."""
+    torch = _torch()
+    n = dst.size
+    # Wrap the raw pointer in a tensor view through the CUDA array interface.
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (src_ptr, False), "version": 3}
+
+    t = torch.as_tensor(_Arr(), device="cuda")
+    dst.view(np.int64)[:] = t.cpu().numpy()

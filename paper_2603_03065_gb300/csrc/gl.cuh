@@ -1,0 +1,95 @@
+// Goldilocks field arithmetic on the device: p = 2^64 - 2^32 + 1.
+//
+// The reduction uses the special form of p instead of Montgomery or Barrett:
+// 2^64 = 2^32 - 1 (mod p) and 2^96 = -1 (mod p).  A 128-bit value
+// x = lo + 2^64 * (h0 + 2^32 * h1) is therefore congruent to
+// lo - h1 + h0 * (2^32 - 1).  This needs one subtraction, one shifted
+// subtraction and one addition, each with a single carry fix-up.
+//
+// Two value conventions are used:
+//   canonical      values in [0, p), at every API boundary and in the NTT;
+//   non-canonical  values in [0, 2^64), congruent mod p, inside the Poseidon
+//                  permutation, to skip the conditional subtractions.
+#pragma once
+#include <stdint.h>
+
+namespace gl {
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+constexpr u64 P = 0xFFFFFFFF00000001ull;
+constexpr u64 EPS = 0xFFFFFFFFull;  // 2^64 mod p
+
+__host__ __device__ __forceinline__ u64 canon(u64 x) { return x >= P ? x - P : x; }
+
+// 128-bit (hi:lo) -> a value in [0, 2^64) congruent mod p.
+__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi)
+{
+    u32 h0 = (u32)hi;
+    u32 h1 = (u32)(hi >> 32);
+    u64 t0 = lo - h1;
+    // Borrow: the wrapped value is lo - h1 + 2^64 = (lo - h1) + EPS (mod p),
+    // and it is at least 2^64 - 2^32 + 1 > EPS, so subtracting EPS cannot wrap.
+    if (lo < (u64)h1) t0 -= EPS;
+    u64 t1 = ((u64)h0 << 32) - h0;  // h0 * (2^32 - 1) < 2^64
+    u64 r = t0 + t1;
+    // Carry: r + 2^64 = r + EPS; r < 2^64 - 2^33 here, so one fix-up suffices.
+    if (r < t1) r += EPS;
+    return r;
+}
+
+// Non-canonical product: inputs in [0, 2^64), output in [0, 2^64).
+__device__ __forceinline__ u64 mul_nc(u64 a, u64 b) { return reduce128(a * b, __umul64hi(a, b)); }
+
+// Canonical product: inputs in [0, 2^64), output in [0, p).
+__device__ __forceinline__ u64 mul(u64 a, u64 b) { return canon(mul_nc(a, b)); }
+
+// Canonical add/sub: inputs and outputs in [0, p).
+__device__ __forceinline__ u64 add(u64 a, u64 b)
+{
+    u64 s = a + b;
+    // On carry the true sum is s + 2^64 < 2p, and s - p (mod 2^64) = s + EPS.
+    if (s < a || s >= P) s -= P;
+    return s;
+}
+
+__device__ __forceinline__ u64 sub(u64 a, u64 b)
+{
+    u64 d = a - b;
+    if (a < b) d += P;  // wrapped a - b + 2^64, plus p (mod 2^64) = a - b + p
+    return d;
+}
+
+// a in [0, 2^64), k canonical: a + k mod p as a value in [0, 2^64).
+// On carry, s + 2^64 = s + EPS with s < p, so s + EPS < 2^64.
+__device__ __forceinline__ u64 add_nc_small(u64 a, u64 k)
+{
+    u64 s = a + k;
+    if (s < k) s += EPS;
+    return s;
+}
+
+__device__ __forceinline__ u64 pow(u64 a, u64 e)
+{
+    u64 r = 1, x = a;
+    while (e) {
+        if (e & 1) r = mul(r, x);
+        x = mul(x, x);
+        e >>= 1;
+    }
+    return r;
+}
+
+__host__ __device__ __forceinline__ u32 bitrev(u32 x, u32 bits)
+{
+#ifdef __CUDA_ARCH__
+    return bits ? (__brev(x) >> (32 - bits)) : 0;
+#else
+    u32 r = 0;
+    for (u32 i = 0; i < bits; i++) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+#endif
+}
+
+}  // namespace gl

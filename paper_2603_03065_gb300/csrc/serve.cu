@@ -1,0 +1,309 @@
+// Serving loop (continuous batching) for audit-commit requests.
+//
+// A scheduler thread admits queued requests in arrival order while their
+// footprint fits the HBM budget minus what is resident.  Each scheduler
+// pass fuses the admitted requests into one batched launch (one launch per
+// stage over all of them) on a free slot stream.  Up to max_inflight
+// batches overlap on the device.  Finished requests keep their LDE and tree
+// resident until v3c_release, for the later FRI and opening phases.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "serve.h"
+
+using namespace v3c;
+using namespace v3c::detail;
+using serve::Request;
+using serve::Server;
+using serve::Slot;
+
+namespace {
+
+size_t lde_scratch_words_s(u32 c, u32 log_n, u32 r)
+{
+    u32 l1, l2;
+    plan_split(log_n, r, l1, l2);
+    if (!l1) return 0;
+    return (size_t)c * (((size_t)1 << log_n) + ((size_t)1 << (log_n + r)));
+}
+
+void fail_all_pending(Server* S, v3c_status st)
+{
+    for (auto& kv : S->reqs) {
+        Request& r = kv.second;
+        if (r.state == V3C_REQ_QUEUED || r.state == V3C_REQ_ADMITTED) {
+            r.state = V3C_REQ_FAILED;
+            r.status = st;
+            r.times.t_done = now_s();
+        }
+    }
+    S->queue.clear();
+}
+
+// Marks finished batches DONE.  Caller holds S->mu.
+void reap(Server* S, bool wait)
+{
+    for (auto& sl : S->slots) {
+        if (!sl.busy) continue;
+        cudaError_t e = wait ? cudaEventSynchronize(sl.done) : cudaEventQuery(sl.done);
+        if (e == cudaErrorNotReady) continue;
+        double t = now_s();
+        for (u64 tk : sl.tickets) {
+            auto it = S->reqs.find(tk);
+            if (it == S->reqs.end()) continue;
+            Request& r = it->second;
+            r.state = e == cudaSuccess ? V3C_REQ_DONE : V3C_REQ_FAILED;
+            r.status = e == cudaSuccess ? V3C_OK : V3C_ECUDA;
+            r.times.t_done = t;
+            S->reserved -= std::min(S->reserved, r.footprint);
+        }
+        sl.tickets.clear();
+        sl.busy = false;
+    }
+}
+
+// One scheduler pass: admit a batch into a free slot.  Returns true if a
+// batch was launched.  Caller holds S->mu.
+bool admit_and_launch(Server* S)
+{
+    Slot* slot = nullptr;
+    for (auto& sl : S->slots)
+        if (!sl.busy) {
+            slot = &sl;
+            break;
+        }
+    if (!slot || S->queue.empty()) return false;
+    const v3c_config& cfg = ctx_config(S->ctx);
+    u64 budget = cfg.hbm_budget_bytes;
+    u64 resident = ctx_resident(S->ctx);
+    std::vector<u64> batch;
+    size_t scratch = 0, staged = 0;
+    u64 reserve = 0;
+    u32 max_batch = S->cfg.max_batch ? S->cfg.max_batch : 32;
+    while (!S->queue.empty() && batch.size() < max_batch) {
+        Request& r = S->reqs[S->queue.front()];
+        if (resident + S->reserved + reserve + r.footprint > budget) break;  // FIFO: wait for memory
+        reserve += r.footprint;
+        scratch += lde_scratch_words_s(r.desc.c, r.desc.log_n, r.desc.rate_bits);
+        if (!r.desc.on_device) staged += (size_t)r.desc.c << r.desc.log_n;
+        batch.push_back(r.ticket);
+        S->queue.pop_front();
+    }
+    if (batch.empty()) return false;
+    double t = now_s();
+    // Slot buffers grow on demand while the slot is idle.
+    size_t need = scratch + staged;
+    v3c_status st = V3C_OK;
+    if (need > slot->arena_words) {
+        if (slot->arena) cudaFree(slot->arena);
+        slot->arena = nullptr;
+        slot->arena_words = 0;
+        if (cudaMalloc(&slot->arena, need * 8) != cudaSuccess) {
+            cudaGetLastError();
+            st = V3C_ENOMEM;
+        } else {
+            slot->arena_words = need;
+        }
+    }
+    if (!st && staged > slot->pinned_words) {
+        if (slot->pinned) cudaFreeHost(slot->pinned);
+        slot->pinned = nullptr;
+        slot->pinned_words = 0;
+        if (cudaMallocHost(&slot->pinned, staged * 8) != cudaSuccess) {
+            cudaGetLastError();
+            st = V3C_ENOMEM;
+        } else {
+            slot->pinned_words = staged;
+        }
+    }
+    std::vector<v3c_commit_desc> descs;
+    size_t poff = 0;
+    for (u64 tk : batch) {
+        Request& r = S->reqs[tk];
+        r.state = V3C_REQ_ADMITTED;
+        r.times.t_admit = t;
+        v3c_commit_desc d = r.desc;
+        if (!st && !d.on_device) {
+            size_t w = (size_t)d.c << d.log_n;
+            memcpy(slot->pinned + poff, r.host_copy.data(), w * 8);
+            d.cols = slot->pinned + poff;
+            poff += w;
+        }
+        descs.push_back(d);
+    }
+    if (!st) {
+        std::vector<u64> ids(batch.size());
+        std::lock_guard<std::mutex> g(ctx_mutex(S->ctx));
+        st = commit_locked(S->ctx, descs.data(), (u32)descs.size(), ids.data(), slot->stream, slot->arena,
+                           slot->arena_words, batch.data());
+        if (!st && cudaEventRecord(slot->done, slot->stream) != cudaSuccess) st = V3C_ECUDA;
+    }
+    double t2 = now_s();
+    for (u64 tk : batch) {
+        Request& r = S->reqs[tk];
+        if (st) {
+            r.state = V3C_REQ_FAILED;
+            r.status = st;
+            r.times.t_done = t2;
+        } else {
+            r.state = V3C_REQ_RUNNING;
+            r.times.t_start = t2;
+            r.host_copy.clear();
+            r.host_copy.shrink_to_fit();
+        }
+    }
+    if (!st) {
+        slot->busy = true;
+        slot->tickets = batch;
+        // Footprint is now counted as resident by the context.
+    }
+    (void)reserve;
+    return true;
+}
+
+void run(Server* S)
+{
+    cudaSetDevice(ctx_device(S->ctx));
+    std::unique_lock<std::mutex> lk(S->mu);
+    try {
+        while (!S->stop) {
+            reap(S, false);
+            bool launched = admit_and_launch(S);
+            bool busy = false;
+            for (auto& sl : S->slots) busy |= sl.busy;
+            if (launched) continue;
+            if (busy) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                lk.lock();
+            } else {
+                S->cv.wait_for(lk, std::chrono::milliseconds(5));
+            }
+        }
+        reap(S, true);
+        fail_all_pending(S, V3C_ECANCELED);
+    } catch (...) {
+        S->crashed = true;
+        fail_all_pending(S, V3C_ECANCELED);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+v3c_status v3c_serve_start(v3c_ctx* ctx, const v3c_serve_cfg* cfg)
+{
+    if (!ctx) return V3C_EINVAL;
+    Server*& S = ctx_server(ctx);
+    if (S) return ctx_fail(ctx, V3C_EINVAL, "serving already started");
+    v3c_status st = lock_and_select(ctx);
+    if (st) return st;
+    Server* srv = new Server();
+    srv->ctx = ctx;
+    if (cfg) srv->cfg = *cfg;
+    if (!srv->cfg.queue_capacity) srv->cfg.queue_capacity = 4096;
+    if (!srv->cfg.max_batch) srv->cfg.max_batch = 32;
+    u32 inflight = srv->cfg.max_inflight ? srv->cfg.max_inflight : ctx_config(ctx).max_inflight;
+    srv->slots.resize(std::max(inflight, 1u));
+    for (auto& sl : srv->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            delete srv;
+            return ctx_fail(ctx, V3C_ECUDA, "serve: stream creation failed");
+        }
+    }
+    S = srv;
+    srv->th = std::thread(run, srv);
+    return V3C_OK;
+}
+
+v3c_status v3c_serve_submit(v3c_ctx* ctx, const v3c_commit_desc* desc, uint64_t* ticket)
+{
+    if (!ctx || !desc || !ticket) return V3C_EINVAL;
+    Server* S = ctx_server(ctx);
+    if (!S) return V3C_ECANCELED;
+    const v3c_commit_desc& d = *desc;
+    if (!d.cols || d.c < 1 || d.log_n > V3C_MAX_LOG_N || d.rate_bits > V3C_MAX_RATE_BITS ||
+        d.log_n + d.rate_bits > V3C_MAX_LOG_LDE || d.cap_height > d.log_n + d.rate_bits)
+        return V3C_EINVAL;
+    u64 fp = v3c_commit_footprint(d.c, d.log_n, d.rate_bits, d.cap_height);
+    if (fp > ctx_config(ctx).hbm_budget_bytes) return V3C_ENOMEM;
+    if ((S->cfg.flags & V3C_FLAG_VALIDATE) && !d.on_device) {
+        size_t w = (size_t)d.c << d.log_n;
+        for (size_t i = 0; i < w; i++)
+            if (d.cols[i] >= 0xFFFFFFFF00000001ull) return V3C_EINVAL;
+    }
+    Request r;
+    r.desc = d;
+    r.footprint = fp;
+    if (!d.on_device) r.host_copy.assign(d.cols, d.cols + ((size_t)d.c << d.log_n));
+    r.times.t_submit = now_s();
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->stop || S->crashed) return V3C_ECANCELED;
+    if (S->queue.size() >= S->cfg.queue_capacity) return V3C_EAGAIN;
+    {
+        std::lock_guard<std::mutex> g2(ctx_mutex(ctx));
+        r.ticket = ctx_next_id(ctx);
+    }
+    *ticket = r.ticket;
+    u64 tk = r.ticket;
+    S->reqs.emplace(tk, std::move(r));
+    S->queue.push_back(tk);
+    S->cv.notify_one();
+    return V3C_OK;
+}
+
+v3c_status v3c_serve_poll(v3c_ctx* ctx, uint64_t ticket, v3c_req_state* state, uint64_t* h_cap,
+                          v3c_req_times* times)
+{
+    if (!ctx) return V3C_EINVAL;
+    Server* S = ctx_server(ctx);
+    if (!S) return V3C_ECANCELED;
+    v3c_req_state stt;
+    v3c_status status;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return V3C_ENOTFOUND;
+        stt = it->second.state;
+        status = it->second.status;
+        if (state) *state = stt;
+        if (times) *times = it->second.times;
+    }
+    if (stt == V3C_REQ_DONE) {
+        if (h_cap) return v3c_commit_cap(ctx, ticket, h_cap);
+        return V3C_OK;
+    }
+    if (stt == V3C_REQ_FAILED) return status;
+    return V3C_EAGAIN;
+}
+
+v3c_status v3c_serve_stop(v3c_ctx* ctx)
+{
+    if (!ctx) return V3C_EINVAL;
+    Server*& S = ctx_server(ctx);
+    if (!S) return V3C_OK;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+        S->cv.notify_all();
+    }
+    if (S->th.joinable()) S->th.join();
+    for (auto& sl : S->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.arena) cudaFree(sl.arena);
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    delete S;
+    S = nullptr;
+    return V3C_OK;
+}
+
+}  // extern "C"

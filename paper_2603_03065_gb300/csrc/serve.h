@@ -1,0 +1,72 @@
+// Serving loop: continuous batching of commit requests.  Requests that
+// arrive while others run on the device join the next scheduler pass.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/v3c.h"
+#include "internal.h"
+
+namespace v3c {
+
+double now_s();
+
+namespace serve {
+
+struct Request {
+    u64 ticket = 0;
+    v3c_commit_desc desc{};
+    std::vector<u64> host_copy;  // input copied at submit (host requests)
+    v3c_req_state state = V3C_REQ_QUEUED;
+    v3c_status status = V3C_EAGAIN;
+    v3c_req_times times{};
+    u64 footprint = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    u64* arena = nullptr;        // device scratch + staged inputs of the batch
+    size_t arena_words = 0;
+    u64* pinned = nullptr;       // pinned staging of host inputs
+    size_t pinned_words = 0;
+    bool busy = false;
+    std::vector<u64> tickets;
+};
+
+struct Server {
+    v3c_ctx* ctx = nullptr;
+    v3c_serve_cfg cfg{};
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<u64> queue;
+    std::unordered_map<u64, Request> reqs;
+    std::vector<Slot> slots;
+    bool stop = false;
+    bool crashed = false;
+    u64 reserved = 0;  // footprint of admitted but not yet resident requests
+};
+
+}  // namespace serve
+
+namespace detail {
+v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64* ids, cudaStream_t s,
+                         u64* arena_override, size_t arena_words, const u64* preassigned_ids);
+v3c_status lock_and_select(v3c_ctx* ctx);
+std::mutex& ctx_mutex(v3c_ctx* ctx);
+u64 ctx_next_id(v3c_ctx* ctx);
+const v3c_config& ctx_config(v3c_ctx* ctx);
+size_t ctx_resident(v3c_ctx* ctx);
+serve::Server*& ctx_server(v3c_ctx* ctx);
+int ctx_device(v3c_ctx* ctx);
+v3c_status ctx_fail(v3c_ctx* ctx, v3c_status s, const char* msg);
+}  // namespace detail
+
+}  // namespace v3c

@@ -1,0 +1,937 @@
+// C ABI of the commitment library: context, plan cache, scratch arena,
+// resident commit objects and the batched (one launch per stage) commit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/v3c.h"
+#include "internal.h"
+#include "serve.h"
+
+namespace v3c {
+
+static thread_local int g_dev_cache = -1;
+
+int num_sms()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+int max_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+Tiles default_tiles()
+{
+    Tiles t;
+    t.a_threads = 256;
+    t.a_cols = 8;
+    t.b_threads = 512;
+    t.c_threads = 256;
+    t.c_q = 4;
+    t.h_threads = 128;
+    t.m_threads = 128;
+    return t;
+}
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace v3c
+
+using namespace v3c;
+
+// ---------------------------------------------------------------- context
+
+struct PlanEntry {
+    Plan plan;
+    u64* mem = nullptr;
+};
+
+struct UploadSlot {
+    void* h = nullptr;
+    void* d = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+};
+
+struct Arena {
+    u64* mem = nullptr;
+    size_t words = 0;
+    cudaEvent_t ev = nullptr;
+    cudaStream_t last = nullptr;
+    bool used = false;
+};
+
+struct Object {
+    u64 id = 0;
+    u64* lde = nullptr;
+    u64* tree = nullptr;
+    u64* cap = nullptr;
+    u32 c = 0, ld = 0, log_n = 0, r = 0, h = 0;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+struct v3c_ctx {
+    int device = 0;
+    v3c_config cfg{};
+    std::mutex mu;
+    std::map<std::pair<u32, u32>, PlanEntry> plans;
+    Arena arena;
+    std::vector<UploadSlot> ring;
+    u32 ring_next = 0;
+    std::unordered_map<u64, Object> objects;
+    u64 next_id = 1;
+    size_t resident = 0;
+    std::atomic<u64> launches{0};
+    std::mutex err_mu;
+    std::string err;
+    Tiles tiles;
+    u32* d_flag = nullptr;
+    serve::Server* server = nullptr;
+    // per-stage timing (V3C_FLAG_TIMING)
+    std::mutex tmu;
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    double stage_ms[V3C_NUM_STAGES] = {0};
+    uint64_t stage_n[V3C_NUM_STAGES] = {0};
+};
+
+static thread_local std::string g_err_copy;
+
+static v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        std::lock_guard<std::mutex> g(ctx->err_mu);
+        ctx->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, V3C_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                        __FILE__, __LINE__);                                                       \
+    } while (0)
+
+static v3c_status use_device(v3c_ctx* ctx)
+{
+    if (g_dev_cache != ctx->device) {
+        CK(cudaSetDevice(ctx->device));
+        g_dev_cache = ctx->device;
+    }
+    return V3C_OK;
+}
+
+namespace v3c {
+namespace detail {
+
+// Plan tables of a shape, built once and kept.  Caller holds ctx->mu.
+v3c_status get_plan(v3c_ctx* ctx, u32 log_n, u32 r, cudaStream_t s, Plan* out)
+{
+    auto key = std::make_pair(log_n, r);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        *out = it->second.plan;
+        return V3C_OK;
+    }
+    PlanEntry pe;
+    size_t words = plan_table_words(log_n, r);
+    CK(cudaMalloc(&pe.mem, words * sizeof(u64)));
+    pe.plan.log_n = log_n;
+    pe.plan.r = r;
+    cudaError_t e = build_plan_tables(pe.plan, pe.mem, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(pe.mem);
+        return fail(ctx, V3C_ECUDA, "plan tables: %s", cudaGetErrorString(e));
+    }
+    ctx->launches++;
+    ctx->plans[key] = pe;
+    *out = pe.plan;
+    return V3C_OK;
+}
+
+// Scratch words for the arena; orders `s` after the arena's previous user.
+// Caller holds ctx->mu.
+v3c_status arena_acquire(v3c_ctx* ctx, size_t words, cudaStream_t s, u64** out)
+{
+    Arena& a = ctx->arena;
+    if (!a.ev) CK(cudaEventCreateWithFlags(&a.ev, cudaEventDisableTiming));
+    if (words > a.words) {
+        if (a.used) CK(cudaEventSynchronize(a.ev));
+        if (a.mem) CK(cudaFree(a.mem));
+        a.mem = nullptr;
+        a.words = 0;
+        size_t want = std::max(words, (size_t)1 << 16);
+        cudaError_t e = cudaMalloc(&a.mem, want * sizeof(u64));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, V3C_ENOMEM, "scratch arena of %zu bytes: %s", want * 8, cudaGetErrorString(e));
+        }
+        a.words = want;
+        a.used = false;
+    }
+    if (a.used && a.last != s) CK(cudaStreamWaitEvent(s, a.ev, 0));
+    *out = a.mem;
+    return V3C_OK;
+}
+
+v3c_status arena_release(v3c_ctx* ctx, cudaStream_t s)
+{
+    Arena& a = ctx->arena;
+    CK(cudaEventRecord(a.ev, s));
+    a.used = true;
+    a.last = s;
+    return V3C_OK;
+}
+
+// Copies `bytes` from host `src` to a device buffer that stays valid until
+// the work enqueued on `s` after this call completes (call upload_done).
+v3c_status upload(v3c_ctx* ctx, const void* src, size_t bytes, cudaStream_t s, void** d_out, u32* slot_out)
+{
+    if (ctx->ring.empty()) ctx->ring.resize(8);
+    u32 k = ctx->ring_next++ % (u32)ctx->ring.size();
+    UploadSlot& u = ctx->ring[k];
+    if (!u.ev) CK(cudaEventCreateWithFlags(&u.ev, cudaEventDisableTiming));
+    CK(cudaEventSynchronize(u.ev));
+    if (bytes > u.cap) {
+        if (u.h) CK(cudaFreeHost(u.h));
+        if (u.d) CK(cudaFree(u.d));
+        u.h = u.d = nullptr;
+        size_t want = std::max(bytes, (size_t)1 << 16);
+        CK(cudaMallocHost(&u.h, want));
+        CK(cudaMalloc(&u.d, want));
+        u.cap = want;
+    }
+    memcpy(u.h, src, bytes);
+    CK(cudaMemcpyAsync(u.d, u.h, bytes, cudaMemcpyHostToDevice, s));
+    *d_out = u.d;
+    *slot_out = k;
+    return V3C_OK;
+}
+
+v3c_status upload_done(v3c_ctx* ctx, u32 slot, cudaStream_t s)
+{
+    CK(cudaEventRecord(ctx->ring[slot].ev, s));
+    return V3C_OK;
+}
+
+static void job_tiles(LdeJob& j)
+{
+    u32 l1 = j.plan.log_n1, l2 = j.plan.log_n2;
+    u32 n1 = 1u << l1;
+    u32 ac = std::max(1u, 8192u / n1);
+    j.a_cols = std::min(std::min(ac, 8u), 1u << l2);
+    j.c_q = std::min(n1 <= 1024 ? 4u : 2u, 1u << j.plan.log_M);
+}
+
+// A batch of LDE jobs and tree jobs, launched as one persistent launch per
+// stage.  Builds the upload blob (jobs + stage item lists).
+struct Batch {
+    std::vector<LdeJob> lde;
+    std::vector<TreeJob> tree;
+    std::vector<u32> fa, fb, fc, fl;
+    std::vector<std::vector<u32>> fm;
+    size_t smem_a = 0, smem_b = 0, smem_c = 0;
+    u32 max_top = 0;
+
+    void finalize(const Tiles& t)
+    {
+        fa.assign(1, 0);
+        fb.assign(1, 0);
+        fc.assign(1, 0);
+        for (auto& j : lde) {
+            fa.push_back(fa.back() + stage_a_items(j, t));
+            fb.push_back(fb.back() + stage_b_items(j));
+            fc.push_back(fc.back() + stage_c_items(j, t));
+            smem_a = std::max(smem_a, stage_a_smem(j, t));
+            smem_b = std::max(smem_b, stage_b_smem(j));
+            smem_c = std::max(smem_c, stage_c_smem(j, t));
+        }
+        fl.assign(1, 0);
+        max_top = 0;
+        for (auto& j : tree) {
+            fl.push_back(fl.back() + leaf_items(j, t));
+            max_top = std::max(max_top, j.log_N - j.h);
+        }
+        fm.clear();
+        for (u32 lev0 = 0; lev0 < max_top; lev0 += 8) {
+            std::vector<u32> f(1, 0);
+            for (auto& j : tree) f.push_back(f.back() + merkle_items(j, lev0, t));
+            fm.push_back(f);
+        }
+    }
+};
+
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+static cudaEvent_t pool_event(v3c_ctx* ctx)
+{
+    std::lock_guard<std::mutex> g(ctx->tmu);
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one stage launch with events on its stream when timing is on.
+struct StageTimer {
+    v3c_ctx* ctx;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageTimer(v3c_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str)
+    {
+        if (ctx->cfg.flags & V3C_FLAG_TIMING) {
+            a = pool_event(ctx);
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    void done()
+    {
+        if (!a) return;
+        cudaEvent_t b = pool_event(ctx);
+        if (!b) return;
+        cudaEventRecord(b, s);
+        std::lock_guard<std::mutex> g(ctx->tmu);
+        ctx->pending.push_back({stage, a, b});
+        a = nullptr;
+    }
+};
+
+v3c_status launch_batch(v3c_ctx* ctx, Batch& b, cudaStream_t s)
+{
+    const Tiles& t = ctx->tiles;
+    b.finalize(t);
+    // Blob layout: LdeJob[], TreeJob[], fa, fb, fc, fl, fm[...]
+    std::vector<std::pair<const void*, size_t>> parts;
+    parts.push_back({b.lde.data(), b.lde.size() * sizeof(LdeJob)});
+    parts.push_back({b.tree.data(), b.tree.size() * sizeof(TreeJob)});
+    parts.push_back({b.fa.data(), b.fa.size() * 4});
+    parts.push_back({b.fb.data(), b.fb.size() * 4});
+    parts.push_back({b.fc.data(), b.fc.size() * 4});
+    parts.push_back({b.fl.data(), b.fl.size() * 4});
+    for (auto& f : b.fm) parts.push_back({f.data(), f.size() * 4});
+    std::vector<size_t> off;
+    size_t total = 0;
+    for (auto& p : parts) {
+        off.push_back(total);
+        total = align16(total + p.second);
+    }
+    std::vector<char> blob(total, 0);
+    for (size_t i = 0; i < parts.size(); i++)
+        if (parts[i].second) memcpy(blob.data() + off[i], parts[i].first, parts[i].second);
+    void* d = nullptr;
+    u32 slot = 0;
+    v3c_status st = upload(ctx, blob.data(), total, s, &d, &slot);
+    if (st) return st;
+    char* dc = (char*)d;
+    const LdeJob* dl = (const LdeJob*)(dc + off[0]);
+    const TreeJob* dt = (const TreeJob*)(dc + off[1]);
+    auto list = [&](size_t part, const std::vector<u32>& f, u32 njobs) {
+        StageList l;
+        l.first = (const u32*)(dc + off[part]);
+        l.njobs = njobs;
+        l.total = f.back();
+        return l;
+    };
+    u32 nl = (u32)b.lde.size(), nt = (u32)b.tree.size();
+    if (nl) {
+        StageList la = list(2, b.fa, nl), lb = list(3, b.fb, nl), lc = list(4, b.fc, nl);
+        if (la.total) {
+            StageTimer tm(ctx, 0, s);
+            CK(launch_stage_a(dl, la, b.smem_a, t, 0, s));
+            tm.done();
+            ctx->launches++;
+        }
+        if (lb.total) {
+            StageTimer tm(ctx, 1, s);
+            CK(launch_stage_b(dl, lb, b.smem_b, t, 0, s));
+            tm.done();
+            ctx->launches++;
+        }
+        if (lc.total) {
+            StageTimer tm(ctx, 2, s);
+            CK(launch_stage_c(dl, lc, b.smem_c, t, 0, s));
+            tm.done();
+            ctx->launches++;
+        }
+    }
+    if (nt) {
+        StageList ll = list(5, b.fl, nt);
+        if (ll.total) {
+            StageTimer tm(ctx, 3, s);
+            CK(launch_leaf_hash(dt, ll, t, 0, s));
+            tm.done();
+            ctx->launches++;
+        }
+        for (size_t g = 0; g < b.fm.size(); g++) {
+            StageList lm = list(6 + g, b.fm[g], nt);
+            if (!lm.total) continue;
+            StageTimer tm(ctx, 4, s);
+            CK(launch_merkle(dt, lm, (u32)(8 * g), 8, t, 0, s));
+            tm.done();
+            ctx->launches++;
+        }
+    }
+    return upload_done(ctx, slot, s);
+}
+
+static bool shape_ok(u32 c, u32 log_n, u32 r)
+{
+    return c >= 1 && log_n <= V3C_MAX_LOG_N && r <= V3C_MAX_RATE_BITS && log_n + r <= V3C_MAX_LOG_LDE;
+}
+
+static size_t lde_scratch_words(u32 c, u32 log_n, u32 r)
+{
+    u32 l1, l2;
+    plan_split(log_n, r, l1, l2);
+    if (!l1) return 0;
+    return (size_t)c * (((size_t)1 << log_n) + ((size_t)1 << (log_n + r)));
+}
+
+static v3c_status make_lde_job(v3c_ctx* ctx, const u64* x, u32 c, u32 log_n, u32 r, u64* lde, u32 ld,
+                               u64* scratch, cudaStream_t s, LdeJob* out)
+{
+    LdeJob j;
+    memset(&j, 0, sizeof j);
+    v3c_status st = get_plan(ctx, log_n, r, s, &j.plan);
+    if (st) return st;
+    j.x = x;
+    j.c = c;
+    j.ld = ld;
+    j.lde = lde;
+    j.vec_ok = ((uintptr_t)lde % 16 == 0) && (ld % 2 == 0);
+    if (j.plan.log_n1) {
+        j.Y = scratch;
+        j.Z = scratch + ((size_t)c << log_n);
+    }
+    job_tiles(j);
+    *out = j;
+    return V3C_OK;
+}
+
+static TreeJob make_tree_job(const u64* rows, u32 ld, u32 width, u32 log_N, u32 h, u64* tree, u64* cap)
+{
+    TreeJob t;
+    memset(&t, 0, sizeof t);
+    t.rows = rows;
+    t.ld = ld;
+    t.width = width;
+    t.log_N = log_N;
+    t.h = h;
+    t.tree = tree;
+    t.cap = cap;
+    t.vec_ok = ((uintptr_t)rows % 16 == 0) && (ld % 2 == 0);
+    return t;
+}
+
+}  // namespace detail
+}  // namespace v3c
+
+using namespace v3c::detail;
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+const char* v3c_strerror(v3c_status s)
+{
+    switch (s) {
+    case V3C_OK: return "ok";
+    case V3C_EINVAL: return "invalid argument";
+    case V3C_ENOMEM: return "out of device memory or HBM budget";
+    case V3C_ECUDA: return "CUDA runtime error";
+    case V3C_EAGAIN: return "not ready / queue full";
+    case V3C_ETIMEDOUT: return "timed out";
+    case V3C_ENOTFOUND: return "unknown id";
+    case V3C_ECANCELED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+const char* v3c_last_error_detail(v3c_ctx* ctx)
+{
+    if (!ctx) return "";
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    g_err_copy = ctx->err;
+    return g_err_copy.c_str();
+}
+
+v3c_status v3c_create(int device, const v3c_config* cfg, v3c_ctx** out)
+{
+    if (!out) return V3C_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return V3C_EINVAL;
+    }
+    v3c_ctx* ctx = new (std::nothrow) v3c_ctx();
+    if (!ctx) return V3C_ENOMEM;
+    ctx->device = device;
+    if (cfg) ctx->cfg = *cfg;
+    if (!ctx->cfg.max_inflight) ctx->cfg.max_inflight = 4;
+    if (!ctx->cfg.timeout_ms) ctx->cfg.timeout_ms = 60000;
+    ctx->tiles = default_tiles();
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete ctx;
+        return V3C_ECUDA;
+    }
+    g_dev_cache = device;
+    if (!ctx->cfg.hbm_budget_bytes) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        ctx->cfg.hbm_budget_bytes = (uint64_t)(fr * 0.9);
+    }
+    if (cudaMalloc(&ctx->d_flag, 16) != cudaSuccess) {
+        delete ctx;
+        return V3C_ENOMEM;
+    }
+    *out = ctx;
+    return V3C_OK;
+}
+
+v3c_status v3c_destroy(v3c_ctx* ctx)
+{
+    if (!ctx) return V3C_EINVAL;
+    v3c_serve_stop(ctx);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->objects) {
+        cudaFree(kv.second.lde);
+        cudaFree(kv.second.tree);
+        cudaFree(kv.second.cap);
+        if (kv.second.done) cudaEventDestroy(kv.second.done);
+    }
+    for (auto& kv : ctx->plans) cudaFree(kv.second.mem);
+    for (auto& u : ctx->ring) {
+        if (u.h) cudaFreeHost(u.h);
+        if (u.d) cudaFree(u.d);
+        if (u.ev) cudaEventDestroy(u.ev);
+    }
+    for (auto& p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->arena.mem) cudaFree(ctx->arena.mem);
+    if (ctx->arena.ev) cudaEventDestroy(ctx->arena.ev);
+    if (ctx->d_flag) cudaFree(ctx->d_flag);
+    delete ctx;
+    return V3C_OK;
+}
+
+v3c_status v3c_lde(v3c_ctx* ctx, const uint64_t* d_cols, uint32_t c, uint32_t log_n, uint32_t rate_bits,
+                   uint64_t* d_lde, uint32_t ld, void* stream)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (!d_cols || !d_lde) return fail(ctx, V3C_EINVAL, "v3c_lde: NULL pointer");
+    if (!shape_ok(c, log_n, rate_bits) || ld < c)
+        return fail(ctx, V3C_EINVAL, "v3c_lde: bad shape c=%u log_n=%u r=%u ld=%u", c, log_n, rate_bits, ld);
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    size_t words = lde_scratch_words(c, log_n, rate_bits);
+    u64* scratch = nullptr;
+    if (words) {
+        st = arena_acquire(ctx, words, s, &scratch);
+        if (st) return st;
+    }
+    Batch b;
+    LdeJob j;
+    st = make_lde_job(ctx, d_cols, c, log_n, rate_bits, d_lde, ld, scratch, s, &j);
+    if (st) return st;
+    b.lde.push_back(j);
+    u32 done_cols = c + (c & 1);
+    if (ld > done_cols) {
+        size_t N = (size_t)1 << (log_n + rate_bits);
+        CK(cudaMemset2DAsync(d_lde + done_cols, (size_t)ld * 8, 0, (size_t)(ld - done_cols) * 8, N, s));
+    }
+    st = launch_batch(ctx, b, s);
+    if (st) return st;
+    if (words) return arena_release(ctx, s);
+    return V3C_OK;
+}
+
+v3c_status v3c_merkle(v3c_ctx* ctx, const uint64_t* d_rows, uint32_t ld, uint32_t width, uint32_t log_rows,
+                      uint32_t cap_height, uint64_t* d_tree, uint64_t* d_cap, void* stream)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (!d_rows || !d_cap || (!d_tree && cap_height != log_rows))
+        return fail(ctx, V3C_EINVAL, "v3c_merkle: NULL pointer");
+    if (cap_height > log_rows || width > ld || width == 0 || log_rows > V3C_MAX_LOG_LDE)
+        return fail(ctx, V3C_EINVAL, "v3c_merkle: bad shape width=%u ld=%u log_rows=%u h=%u", width, ld,
+                    log_rows, cap_height);
+    if ((uintptr_t)d_tree % 16 || (uintptr_t)d_cap % 16)
+        return fail(ctx, V3C_EINVAL, "v3c_merkle: tree and cap must be 16-byte aligned");
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Batch b;
+    b.tree.push_back(make_tree_job(d_rows, ld, width, log_rows, cap_height, d_tree, d_cap));
+    return launch_batch(ctx, b, s);
+}
+
+uint64_t v3c_commit_footprint(uint32_t c, uint32_t log_n, uint32_t rate_bits, uint32_t cap_height)
+{
+    u32 ld = c + (c & 1);
+    uint64_t N = (uint64_t)1 << (log_n + rate_bits);
+    uint64_t tree_words = cap_height <= log_n + rate_bits ? (2 * N - ((uint64_t)2 << cap_height)) * 4 : 0;
+    return (N * ld + tree_words + ((uint64_t)4 << cap_height)) * 8;
+}
+
+}  // extern "C"
+
+namespace v3c {
+namespace detail {
+
+// Allocates the resident objects for descs (all or nothing), stages host
+// inputs in the arena, and launches the batch.  Caller holds ctx->mu and
+// has selected the device.  Shared by v3c_commit and the serving loop.
+v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64* ids, cudaStream_t s,
+                         u64* arena_override, size_t arena_words, const u64* preassigned_ids)
+{
+    size_t need = 0, scratch = 0, staged = 0;
+    for (u32 i = 0; i < nb; i++) {
+        const v3c_commit_desc& d = descs[i];
+        if (!d.cols || !shape_ok(d.c, d.log_n, d.rate_bits) || d.cap_height > d.log_n + d.rate_bits)
+            return fail(ctx, V3C_EINVAL, "v3c_commit: bad desc %u (c=%u log_n=%u r=%u h=%u)", i, d.c, d.log_n,
+                        d.rate_bits, d.cap_height);
+        need += v3c_commit_footprint(d.c, d.log_n, d.rate_bits, d.cap_height);
+        scratch += lde_scratch_words(d.c, d.log_n, d.rate_bits);
+        if (!d.on_device) staged += (size_t)d.c << d.log_n;
+    }
+    if (!arena_override && ctx->resident + need > ctx->cfg.hbm_budget_bytes)
+        return fail(ctx, V3C_ENOMEM, "v3c_commit: %zu bytes requested, %zu resident, budget %llu", need,
+                    ctx->resident, (unsigned long long)ctx->cfg.hbm_budget_bytes);
+    u64* arena = nullptr;
+    size_t arena_need = scratch + staged;
+    v3c_status st;
+    if (arena_need) {
+        if (arena_override) {
+            if (arena_need > arena_words) return fail(ctx, V3C_ENOMEM, "slot arena too small");
+            arena = arena_override;
+        } else {
+            st = arena_acquire(ctx, arena_need, s, &arena);
+            if (st) return st;
+        }
+    }
+    std::vector<Object> objs(nb);
+    auto rollback = [&](u32 upto) {
+        for (u32 k = 0; k < upto; k++) {
+            if (objs[k].lde) cudaFreeAsync(objs[k].lde, s);
+            if (objs[k].tree) cudaFreeAsync(objs[k].tree, s);
+            if (objs[k].cap) cudaFreeAsync(objs[k].cap, s);
+            if (objs[k].done) cudaEventDestroy(objs[k].done);
+        }
+    };
+    for (u32 i = 0; i < nb; i++) {
+        const v3c_commit_desc& d = descs[i];
+        Object& o = objs[i];
+        o.c = d.c;
+        o.ld = d.c + (d.c & 1);
+        o.log_n = d.log_n;
+        o.r = d.rate_bits;
+        o.h = d.cap_height;
+        size_t N = (size_t)1 << (d.log_n + d.rate_bits);
+        size_t tw = (2 * N - ((size_t)2 << d.cap_height)) * 4;
+        o.bytes = v3c_commit_footprint(d.c, d.log_n, d.rate_bits, d.cap_height);
+        cudaError_t e = cudaMallocAsync((void**)&o.lde, N * o.ld * 8, s);
+        if (e == cudaSuccess && tw) e = cudaMallocAsync((void**)&o.tree, tw * 8, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&o.cap, ((size_t)4 << d.cap_height) * 8, s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&o.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rollback(i + 1);
+            return fail(ctx, V3C_ENOMEM, "v3c_commit: allocation of %zu bytes failed: %s", o.bytes,
+                        cudaGetErrorString(e));
+        }
+    }
+    Batch b;
+    size_t aoff = 0;
+    for (u32 i = 0; i < nb; i++) {
+        const v3c_commit_desc& d = descs[i];
+        Object& o = objs[i];
+        const u64* x = d.cols;
+        size_t n = (size_t)1 << d.log_n;
+        if (!d.on_device) {
+            u64* dst = arena + aoff;
+            aoff += d.c * n;
+            cudaError_t e = cudaMemcpyAsync(dst, d.cols, d.c * n * 8, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                rollback(nb);
+                return fail(ctx, V3C_ECUDA, "input copy: %s", cudaGetErrorString(e));
+            }
+            x = dst;
+        }
+        size_t sw = lde_scratch_words(d.c, d.log_n, d.rate_bits);
+        u64* scr = sw ? arena + aoff : nullptr;
+        aoff += sw;
+        LdeJob j;
+        st = make_lde_job(ctx, x, d.c, d.log_n, d.rate_bits, o.lde, o.ld, scr, s, &j);
+        if (st) {
+            rollback(nb);
+            return st;
+        }
+        b.lde.push_back(j);
+        b.tree.push_back(make_tree_job(o.lde, o.ld, d.c, d.log_n + d.rate_bits, d.cap_height, o.tree, o.cap));
+    }
+    if ((ctx->cfg.flags & V3C_FLAG_VALIDATE)) {
+        cudaMemsetAsync(ctx->d_flag, 0, 4, s);
+        for (auto& j : b.lde) {
+            cudaError_t e = launch_validate(j.x, (u64)j.c << j.plan.log_n, ctx->d_flag, s);
+            if (e != cudaSuccess) {
+                rollback(nb);
+                return fail(ctx, V3C_ECUDA, "validate: %s", cudaGetErrorString(e));
+            }
+            ctx->launches++;
+        }
+        u32 flag = 0;
+        cudaError_t e = cudaMemcpyAsync(&flag, ctx->d_flag, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || flag) {
+            rollback(nb);
+            return e != cudaSuccess ? fail(ctx, V3C_ECUDA, "validate: %s", cudaGetErrorString(e))
+                                    : fail(ctx, V3C_EINVAL, "v3c_commit: input not canonical (>= p)");
+        }
+    }
+    st = launch_batch(ctx, b, s);
+    if (st) {
+        rollback(nb);
+        return st;
+    }
+    if (arena_need && !arena_override) {
+        st = arena_release(ctx, s);
+        if (st) return st;
+    }
+    for (u32 i = 0; i < nb; i++) {
+        Object& o = objs[i];
+        CK(cudaEventRecord(o.done, s));
+        o.stream = s;
+        o.id = preassigned_ids ? preassigned_ids[i] : ctx->next_id++;
+        ctx->resident += o.bytes;
+        ids[i] = o.id;
+        ctx->objects[o.id] = o;
+    }
+    return V3C_OK;
+}
+
+v3c_status lock_and_select(v3c_ctx* ctx) { return use_device(ctx); }
+std::mutex& ctx_mutex(v3c_ctx* ctx) { return ctx->mu; }
+u64 ctx_next_id(v3c_ctx* ctx) { return ctx->next_id++; }
+const v3c_config& ctx_config(v3c_ctx* ctx) { return ctx->cfg; }
+size_t ctx_resident(v3c_ctx* ctx) { return ctx->resident; }
+serve::Server*& ctx_server(v3c_ctx* ctx) { return ctx->server; }
+int ctx_device(v3c_ctx* ctx) { return ctx->device; }
+v3c_status ctx_fail(v3c_ctx* ctx, v3c_status s, const char* msg) { return fail(ctx, s, "%s", msg); }
+
+}  // namespace detail
+}  // namespace v3c
+
+extern "C" {
+
+v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v3c_commit_id* ids, void* stream)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (!descs || !ids || nb == 0) return fail(ctx, V3C_EINVAL, "v3c_commit: empty batch or NULL");
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return commit_locked(ctx, descs, nb, ids, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+v3c_status v3c_commit_buffers(v3c_ctx* ctx, v3c_commit_id id, uint64_t** d_lde, uint32_t* ld, uint64_t** d_tree,
+                              uint64_t** d_cap, uint32_t* log_rows, uint32_t* cap_height)
+{
+    if (!ctx) return V3C_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->objects.find(id);
+    if (it == ctx->objects.end()) return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)id);
+    const Object& o = it->second;
+    if (d_lde) *d_lde = o.lde;
+    if (ld) *ld = o.ld;
+    if (d_tree) *d_tree = o.tree;
+    if (d_cap) *d_cap = o.cap;
+    if (log_rows) *log_rows = o.log_n + o.r;
+    if (cap_height) *cap_height = o.h;
+    return V3C_OK;
+}
+
+v3c_status v3c_commit_cap(v3c_ctx* ctx, v3c_commit_id id, uint64_t* h_cap)
+{
+    if (!ctx || !h_cap) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    Object o;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto it = ctx->objects.find(id);
+        if (it == ctx->objects.end()) return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)id);
+        o = it->second;
+    }
+    CK(cudaEventSynchronize(o.done));
+    CK(cudaMemcpy(h_cap, o.cap, ((size_t)4 << o.h) * 8, cudaMemcpyDeviceToHost));
+    return V3C_OK;
+}
+
+v3c_status v3c_open(v3c_ctx* ctx, v3c_commit_id id, uint64_t leaf, uint64_t* h_row, uint64_t* h_path)
+{
+    if (!ctx) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    Object o;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto it = ctx->objects.find(id);
+        if (it == ctx->objects.end()) return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)id);
+        o = it->second;
+    }
+    u32 logN = o.log_n + o.r;
+    if (leaf >> logN) return fail(ctx, V3C_EINVAL, "v3c_open: leaf %llu out of range", (unsigned long long)leaf);
+    CK(cudaEventSynchronize(o.done));
+    if (h_row) CK(cudaMemcpy(h_row, o.lde + leaf * o.ld, (size_t)o.c * 8, cudaMemcpyDeviceToHost));
+    if (h_path) {
+        size_t N = (size_t)1 << logN;
+        for (u32 k = 0; k < logN - o.h; k++) {
+            size_t off = 8 * N - ((8 * N) >> k);
+            size_t sib = (size_t)((leaf >> k) ^ 1);
+            CK(cudaMemcpy(h_path + 4 * k, o.tree + off + 4 * sib, 32, cudaMemcpyDeviceToHost));
+        }
+    }
+    return V3C_OK;
+}
+
+v3c_status v3c_release(v3c_ctx* ctx, v3c_commit_id id)
+{
+    if (!ctx) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->objects.find(id);
+    if (it == ctx->objects.end()) return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)id);
+    Object o = it->second;
+    ctx->objects.erase(it);
+    // Stream-ordered free after the producing work.
+    CK(cudaStreamWaitEvent(o.stream, o.done, 0));
+    CK(cudaFreeAsync(o.lde, o.stream));
+    if (o.tree) CK(cudaFreeAsync(o.tree, o.stream));
+    CK(cudaFreeAsync(o.cap, o.stream));
+    CK(cudaEventDestroy(o.done));
+    ctx->resident -= o.bytes;
+    return V3C_OK;
+}
+
+uint64_t v3c_kernel_launches(v3c_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+v3c_status v3c_stage_stats(v3c_ctx* ctx, v3c_stage_stats_t* out, int reset)
+{
+    if (!ctx || !out) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    std::vector<v3c_ctx::Pending> pend;
+    {
+        std::lock_guard<std::mutex> g(ctx->tmu);
+        pend.swap(ctx->pending);
+    }
+    for (auto& p : pend) {
+        float ms = 0;
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return fail(ctx, V3C_ECUDA, "stage timing: %s", cudaGetErrorString(e));
+        std::lock_guard<std::mutex> g(ctx->tmu);
+        ctx->stage_ms[p.stage] += ms;
+        ctx->stage_n[p.stage] += 1;
+        ctx->ev_pool.push_back(p.a);
+        ctx->ev_pool.push_back(p.b);
+    }
+    std::lock_guard<std::mutex> g(ctx->tmu);
+    for (int i = 0; i < V3C_NUM_STAGES; i++) {
+        out->ms[i] = ctx->stage_ms[i];
+        out->launches[i] = ctx->stage_n[i];
+        if (reset) {
+            ctx->stage_ms[i] = 0;
+            ctx->stage_n[i] = 0;
+        }
+    }
+    return V3C_OK;
+}
+
+v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz)
+{
+    if (!ctx || !rate) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    int sms = num_sms();
+    int grid = sms * 8, threads = 256;
+    u32 iters = 4096;
+    u64* out = nullptr;
+    CK(cudaMalloc(&out, (size_t)grid * 8));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    double best = 0;
+    for (u32 r = 0; r < std::max(reps, 1u) + 1; r++) {
+        CK(cudaEventRecord(a, 0));
+        CK(launch_int_peak(out, grid, threads, iters, 0));
+        ctx->launches++;
+        CK(cudaEventRecord(b, 0));
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        double ops = (double)grid * threads * iters * 8 * 4;
+        if (r > 0) best = std::max(best, ops / (ms * 1e-3));
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    *rate = best;
+    if (mhz) {
+        int khz = 0;
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+        *mhz = khz / 1000.0;
+    }
+    return V3C_OK;
+}
+
+}  // extern "C"
