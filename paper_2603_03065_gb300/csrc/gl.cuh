@@ -70,6 +70,19 @@ __device__ __forceinline__ u64 add_nc_small(u64 a, u64 k)
     return s;
 }
 
+// a, b in [0, 2^64): a + b mod p as a value in [0, 2^64).  After a carry,
+// s + EPS can carry again only when s > 2^64 - 2^32, and then the wrapped
+// value is below EPS, so a second EPS cannot carry.
+__device__ __forceinline__ u64 add_nc(u64 a, u64 b)
+{
+    u64 s = a + b;
+    if (s < b) {
+        s += EPS;
+        if (s < EPS) s += EPS;
+    }
+    return s;
+}
+
 __device__ __forceinline__ u64 pow(u64 a, u64 e)
 {
     u64 r = 1, x = a;

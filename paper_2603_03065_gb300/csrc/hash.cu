@@ -5,102 +5,23 @@
 // Here the tree is built over the rows of the LDE and cut at a cap.
 //
 // GB300 mapping: this is 64-bit modular integer work with no dense
-// contraction, so it runs on the integer pipes: one thread owns one 12-lane
-// state in registers.  The MDS row has entries below 64, so every MDS
-// product is two 32x32->64 multiply-adds into 42-bit accumulators, with one
-// special-form fold per output lane.  Inside the permutation values stay
-// non-canonical in [0, 2^64); digests are made canonical on output.  The
-// round loop is not unrolled, which keeps the kernel's code small enough to
-// stay resident in the instruction cache.  Round constants come from
-// constant memory as uniform loads.
+// contraction, so it runs on the integer pipes.  One thread owns one 12-lane
+// state in registers (poseidon.cuh).  The leaf kernel reads each LDE row
+// once, in 16-byte loads.  Large tree levels get one launch each with one
+// compression per thread.  The last levels of a tree are folded inside one
+// CTA in shared memory.
 #include <cuda_runtime.h>
 #include <algorithm>
 
 #include "gl.cuh"
 #include "internal.h"
-#include "poseidon_params.h"  // generated at build time by gen_params.cpp
+#include "poseidon.cuh"
 
 namespace v3c {
 
 using gl::u32;
 using gl::u64;
-
-__constant__ u64 c_rc[30][12] = V3C_RC_INIT;
-
-__host__ __device__ constexpr u32 mds_coef(int k)
-{
-    constexpr u32 row[12] = V3C_MDS_ROW_INIT;
-    return row[k];
-}
-
-// L + H * 2^32 for L, H < 2^42, folded to a value in [0, 2^64).
-__device__ __forceinline__ u64 mds_fold(u64 L, u64 H)
-{
-    u32 hl = (u32)H, hh = (u32)(H >> 32);
-    u64 v = L + ((u64)hl << 32);
-    u32 c = v < L;
-    u32 x = hh + c;              // < 2^11: the multiple of 2^64 still to fold
-    u64 t = ((u64)x << 32) - x;  // x * (2^64 mod p)
-    u64 r = v + t;
-    if (r < t) r += gl::EPS;
-    return r;
-}
-
-// s <- M s with M[i][j] = m[(j - i) mod 12].
-__device__ __forceinline__ void mds(u64 (&s)[12])
-{
-    u32 lo[12], hi[12];
-#pragma unroll
-    for (int j = 0; j < 12; j++) {
-        lo[j] = (u32)s[j];
-        hi[j] = (u32)(s[j] >> 32);
-    }
-#pragma unroll
-    for (int i = 0; i < 12; i++) {
-        u64 L = 0, H = 0;
-#pragma unroll
-        for (int j = 0; j < 12; j++) {
-            const u32 m = mds_coef((j - i + 12) % 12);
-            L += (u64)lo[j] * m;
-            H += (u64)hi[j] * m;
-        }
-        s[i] = mds_fold(L, H);
-    }
-}
-
-__device__ __forceinline__ u64 sbox(u64 x)
-{
-    u64 x2 = gl::mul_nc(x, x);
-    u64 x3 = gl::mul_nc(x2, x);
-    u64 x4 = gl::mul_nc(x2, x2);
-    return gl::mul_nc(x3, x4);
-}
-
-__device__ __forceinline__ void full_round(u64 (&s)[12], int r)
-{
-#pragma unroll
-    for (int i = 0; i < 12; i++) s[i] = sbox(gl::add_nc_small(s[i], c_rc[r][i]));
-    mds(s);
-}
-
-__device__ __forceinline__ void partial_round(u64 (&s)[12], int r)
-{
-#pragma unroll
-    for (int i = 0; i < 12; i++) s[i] = gl::add_nc_small(s[i], c_rc[r][i]);
-    s[0] = sbox(s[0]);
-    mds(s);
-}
-
-// Rounds 0-3 and 26-29 full, 4-25 partial.
-__device__ __forceinline__ void permute(u64 (&s)[12])
-{
-#pragma unroll 1
-    for (int r = 0; r < 4; r++) full_round(s, r);
-#pragma unroll 1
-    for (int r = 4; r < 26; r++) partial_round(s, r);
-#pragma unroll 1
-    for (int r = 26; r < 30; r++) full_round(s, r);
-}
+typedef pos::Default PC;
 
 __device__ __forceinline__ u32 find_job_t(const u32* first, u32 njobs, u32 item)
 {
@@ -113,7 +34,8 @@ __device__ __forceinline__ u32 find_job_t(const u32* first, u32 njobs, u32 item)
     return lo;
 }
 
-// Offset (in u64) of tree level k below the cap, or the cap itself.
+// Tree level k below the cap, or the cap itself for k = log N - h.
+// Level k starts at word 8N - 8N / 2^k of the level-major tree.
 __device__ __forceinline__ u64* level_ptr(const TreeJob& J, u32 k)
 {
     u32 top = J.log_N - J.h;
@@ -138,7 +60,7 @@ u32 leaf_items(const TreeJob& j, const Tiles& t)
 
 // One thread per row: sponge over the first `width` entries in chunks of 8
 // (overwrite mode), digest = lanes 0..3.
-__global__ void __launch_bounds__(128) k_leaf_hash(const TreeJob* __restrict__ jobs, StageList L)
+__global__ void __launch_bounds__(128, 6) k_leaf_hash(const TreeJob* __restrict__ jobs, StageList L)
 {
     for (u32 item = blockIdx.x; item < L.total; item += gridDim.x) {
         u32 jid = find_job_t(L.first, L.njobs, item);
@@ -157,27 +79,28 @@ __global__ void __launch_bounds__(128) k_leaf_hash(const TreeJob* __restrict__ j
             store_digest(dst, s);
             continue;
         }
+        const bool vec = J.vec_ok;
         for (u32 st = 0; st < width; st += 8) {
-            u32 len = min(8u, width - st);
-            u64 v[8];
-            if (J.vec_ok) {
+            // Overwrite lanes 0..len-1 with the next chunk of the row.
+            const u32 len = min(8u, width - st);
+            const u64* p = src + st;
+            if (vec) {
 #pragma unroll
                 for (u32 k = 0; k < 4; k++) {
                     if (2 * k < len) {
-                        ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(src + st + 2 * k));
-                        v[2 * k] = p.x;
-                        v[2 * k + 1] = p.y;
+                        // With len odd, 2k+1 = len <= width - st - 1 + 1 <= ld - st - 1:
+                        // width is odd then and ld is even, so the pair stays in the row.
+                        ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2*>(p + 2 * k));
+                        s[2 * k] = q.x;
+                        if (2 * k + 1 < len) s[2 * k + 1] = q.y;
                     }
                 }
             } else {
 #pragma unroll
                 for (u32 k = 0; k < 8; k++)
-                    if (k < len) v[k] = __ldg(src + st + k);
+                    if (k < len) s[k] = __ldg(p + k);
             }
-#pragma unroll
-            for (u32 k = 0; k < 8; k++)
-                if (k < len) s[k] = v[k];
-            permute(s);
+            pos::permute<PC>(s);
         }
         store_digest(dst, s);
     }
@@ -208,9 +131,9 @@ u32 merkle_items(const TreeJob& j, u32 lev0, const Tiles& t)
 }
 
 // Each CTA of T threads takes 2T digests of level lev0 and compresses them
-// to T digests of level lev0+1, then keeps halving in shared memory for up
-// to nlev levels.  Every level is written to its place in the level-major
-// tree, or to the cap for the top level.
+// to T digests of level lev0+1.  With nlev > 1 it keeps halving in shared
+// memory for up to nlev levels.  Every level is written to its place in
+// the level-major tree, or to the cap for the top level.
 __global__ void __launch_bounds__(128) k_merkle(const TreeJob* __restrict__ jobs, StageList L, u32 lev0, u32 nlev)
 {
     __shared__ ulonglong2 sm[128 * 2];
@@ -237,11 +160,13 @@ __global__ void __launch_bounds__(128) k_merkle(const TreeJob* __restrict__ jobs
             }
 #pragma unroll
             for (int k = 8; k < 12; k++) s[k] = 0;
-            permute(s);
+            pos::permute<PC>(s);
             u64* dst = level_ptr(J, lev0 + 1) + (base + tid) * 4;
             store_digest(dst, s);
-            sm[2 * tid] = make_ulonglong2(gl::canon(s[0]), gl::canon(s[1]));
-            sm[2 * tid + 1] = make_ulonglong2(gl::canon(s[2]), gl::canon(s[3]));
+            if (levels > 1) {
+                sm[2 * tid] = make_ulonglong2(gl::canon(s[0]), gl::canon(s[1]));
+                sm[2 * tid + 1] = make_ulonglong2(gl::canon(s[2]), gl::canon(s[3]));
+            }
         }
         for (u32 l = 2; l <= levels; l++) {
             __syncthreads();
@@ -255,7 +180,7 @@ __global__ void __launch_bounds__(128) k_merkle(const TreeJob* __restrict__ jobs
                 }
 #pragma unroll
                 for (int k = 8; k < 12; k++) s[k] = 0;
-                permute(s);
+                pos::permute<PC>(s);
             }
             __syncthreads();
             if (tid < cnt) {

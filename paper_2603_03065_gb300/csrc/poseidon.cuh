@@ -1,0 +1,337 @@
+// Poseidon-w12 permutation on the device (one thread per state).
+//
+// The hash is Poseidon (Sec. 4.3): width 12, S-box x^7, rounds 4 full,
+// 22 partial and 4 full, each round ARC -> S-box -> MDS.  The constants are
+// generated at build time (gen_params.cpp).
+//
+// Evaluation orders (all exact; selected by the Cfg template):
+//   plain  the round loop as defined, one loop body for all 30 rounds so the
+//          code stays small enough for the instruction cache;
+//   fast   the partial rounds in the equivalent sparse form of the Poseidon
+//          paper (Grassi et al., "efficient partial rounds").  Each partial
+//          round adds one scalar to lane 0, applies the S-box to lane 0 and
+//          multiplies by [[m_0, v_k^T], [w_k, I]].  A dense 11x11 block D_0 is
+//          applied after the MDS of round 3.  gen_params.cpp derives the
+//          constants and checks on the host that both orders agree.
+// MDS products (the MDS row has entries below 64):
+//   wide   each 32-bit half of a lane times the entry, a 32x32->64
+//          multiply-add into a 42-bit accumulator;
+//   limb   each lane in 22-bit limbs, so that every product and its
+//          12-term sum fit one 32-bit multiply-add (full-rate IMAD).
+// Values inside the permutation are non-canonical in [0, 2^64).
+#pragma once
+#include "gl.cuh"
+#include "poseidon_params.h"
+
+namespace v3c {
+namespace pos {
+
+using gl::u32;
+using gl::u64;
+
+__constant__ u64 c_rc[30][12] = V3C_RC_INIT;
+__constant__ u64 c_fast_a[22] = V3C_FAST_A_INIT;
+__constant__ u64 c_fast_v[22 * 11] = V3C_FAST_V_INIT;
+__constant__ u64 c_fast_w[22 * 11] = V3C_FAST_W_INIT;
+__constant__ u64 c_fast_d0[11 * 11] = V3C_FAST_D0_INIT;
+// Full rounds 0-3, then 26-29 with the constants carried out of the fast
+// partial rounds folded into round 26.
+__constant__ u64 c_rc_full[8 * 12] = V3C_FAST_RC_FULL_INIT;
+
+__host__ __device__ constexpr u32 mds_coef(int k)
+{
+    constexpr u32 row[12] = V3C_MDS_ROW_INIT;
+    return row[k];
+}
+
+enum MulKind { MUL_INTRINSIC = 0, MUL_PTX = 1, MUL_WIDE = 2 };
+enum MdsKind { MDS_WIDE = 0, MDS_LIMB = 1 };
+
+template <int MUL_, int MDS_, bool SQR_, bool FAST_>
+struct Cfg {
+    static constexpr int MUL = MUL_;
+    static constexpr int MDS = MDS_;
+    static constexpr bool SQR = SQR_;
+    static constexpr bool FAST = FAST_;
+};
+// The configuration the library's kernels use (fastest measured on GB300:
+// 32-bit limb MDS, compiler 64-bit products, plain round order).
+typedef Cfg<MUL_INTRINSIC, MDS_LIMB, false, false> Default;
+
+struct U128 {
+    u64 lo, hi;
+};
+
+__device__ __forceinline__ U128 mul128_ptx(u64 a, u64 b)
+{
+    u32 r0, r1, r2, r3;
+    asm("{\n\t"
+        ".reg .u32 a0, a1, b0, b1;\n\t"
+        "mov.b64 {a0, a1}, %4;\n\t"
+        "mov.b64 {b0, b1}, %5;\n\t"
+        "mul.lo.u32 %0, a0, b0;\n\t"
+        "mul.hi.u32 %1, a0, b0;\n\t"
+        "mad.lo.cc.u32 %1, a0, b1, %1;\n\t"
+        "madc.hi.u32 %2, a0, b1, 0;\n\t"
+        "mad.lo.cc.u32 %1, a1, b0, %1;\n\t"
+        "madc.hi.cc.u32 %2, a1, b0, %2;\n\t"
+        "madc.hi.u32 %3, a1, b1, 0;\n\t"
+        "mad.lo.cc.u32 %2, a1, b1, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "}"
+        : "=&r"(r0), "=&r"(r1), "=&r"(r2), "=&r"(r3)
+        : "l"(a), "l"(b));
+    U128 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.lo) : "r"(r0), "r"(r1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.hi) : "r"(r2), "r"(r3));
+    return r;
+}
+
+// Four 32x32->64 products assembled with 64-bit adds.
+__device__ __forceinline__ U128 mul128_wide(u64 a, u64 b)
+{
+    u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+    u64 p00 = (u64)a0 * b0, p01 = (u64)a0 * b1, p10 = (u64)a1 * b0, p11 = (u64)a1 * b1;
+    u64 mid = p01 + p10;
+    u64 cm = mid < p01;
+    u64 lo = p00 + (mid << 32);
+    u64 c = lo < p00;
+    u64 hi = p11 + (mid >> 32) + (cm << 32) + c;
+    return {lo, hi};
+}
+
+// x^2 from three 32x32->64 products (the cross term doubled).
+__device__ __forceinline__ U128 sqr128_wide(u64 x)
+{
+    u32 a0 = (u32)x, a1 = (u32)(x >> 32);
+    u64 p00 = (u64)a0 * a0, p11 = (u64)a1 * a1, p01 = (u64)a0 * a1;
+    u64 cm = p01 >> 63;
+    u64 mid = p01 << 1;
+    u64 lo = p00 + (mid << 32);
+    u64 c = lo < p00;
+    u64 hi = p11 + (mid >> 32) + (cm << 32) + c;
+    return {lo, hi};
+}
+
+template <class C>
+__device__ __forceinline__ U128 mul128(u64 a, u64 b)
+{
+    if (C::MUL == MUL_PTX) return mul128_ptx(a, b);
+    if (C::MUL == MUL_WIDE) return mul128_wide(a, b);
+    return {a * b, __umul64hi(a, b)};
+}
+
+template <class C>
+__device__ __forceinline__ u64 mulmod(u64 a, u64 b)
+{
+    U128 p = mul128<C>(a, b);
+    return gl::reduce128(p.lo, p.hi);
+}
+
+template <class C>
+__device__ __forceinline__ u64 sqrmod(u64 a)
+{
+    if (C::SQR) {
+        U128 p = sqr128_wide(a);
+        return gl::reduce128(p.lo, p.hi);
+    }
+    return mulmod<C>(a, a);
+}
+
+template <class C>
+__device__ __forceinline__ u64 sbox(u64 x)
+{
+    u64 x2 = sqrmod<C>(x);
+    u64 x3 = mulmod<C>(x2, x);
+    u64 x4 = sqrmod<C>(x2);
+    return mulmod<C>(x3, x4);
+}
+
+// L + H * 2^32 for L, H < 2^42, folded to [0, 2^64).
+__device__ __forceinline__ u64 mds_fold(u64 L, u64 H)
+{
+    u32 hl = (u32)H, hh = (u32)(H >> 32);
+    u64 v = L + ((u64)hl << 32);
+    u32 c = v < L;
+    u32 x = hh + c;
+    u64 t = ((u64)x << 32) - x;
+    u64 r = v + t;
+    if (r < t) r += gl::EPS;
+    return r;
+}
+
+// A + B 2^22 + C 2^44 for A, B, C < 2^32, folded to [0, 2^64).
+__device__ __forceinline__ u64 limb_fold(u32 A, u32 B, u32 Cc)
+{
+    u64 x = (u64)A + ((u64)B << 22);              // < 2^55
+    u64 y = x + ((u64)(Cc & 0xFFFFFu) << 44);     // may carry once
+    u32 c = y < x;
+    u32 h = (Cc >> 20) + c;                        // multiple of 2^64, < 2^13
+    u64 t = ((u64)h << 32) - h;                    // h * (2^64 mod p)
+    u64 r = y + t;
+    if (r < t) r += gl::EPS;
+    return r;
+}
+
+// s <- M s, M[i][j] = m[(j - i) mod 12].
+template <class C>
+__device__ __forceinline__ void mds(u64 (&s)[12])
+{
+    u64 out[12];
+    if (C::MDS == MDS_LIMB) {
+        u32 a[12], b[12], c[12];
+#pragma unroll
+        for (int j = 0; j < 12; j++) {
+            a[j] = (u32)s[j] & 0x3FFFFFu;
+            b[j] = (u32)(s[j] >> 22) & 0x3FFFFFu;
+            c[j] = (u32)(s[j] >> 44);
+        }
+#pragma unroll
+        for (int i = 0; i < 12; i++) {
+            u32 A = 0, B = 0, Cc = 0;
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                const u32 m = mds_coef((j - i + 12) % 12);
+                A += a[j] * m;
+                B += b[j] * m;
+                Cc += c[j] * m;
+            }
+            out[i] = limb_fold(A, B, Cc);
+        }
+    } else {
+        u32 lo[12], hi[12];
+#pragma unroll
+        for (int j = 0; j < 12; j++) {
+            lo[j] = (u32)s[j];
+            hi[j] = (u32)(s[j] >> 32);
+        }
+#pragma unroll
+        for (int i = 0; i < 12; i++) {
+            u64 L = 0, H = 0;
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                const u32 m = mds_coef((j - i + 12) % 12);
+                L += (u64)lo[j] * m;
+                H += (u64)hi[j] * m;
+            }
+            out[i] = mds_fold(L, H);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 12; i++) s[i] = out[i];
+}
+
+// ---------------------------------------------------------------- plain form
+
+// Rounds 0-3 and 26-29 full, 4-25 partial, in one loop body.
+template <class C>
+__device__ __forceinline__ void permute_plain(u64 (&s)[12])
+{
+#pragma unroll 1
+    for (int r = 0; r < 30; r++) {
+        if (r < 4 || r >= 26) {
+#pragma unroll
+            for (int i = 0; i < 12; i++) s[i] = sbox<C>(gl::add_nc_small(s[i], c_rc[r][i]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 12; i++) s[i] = gl::add_nc_small(s[i], c_rc[r][i]);
+            s[0] = sbox<C>(s[0]);
+        }
+        mds<C>(s);
+    }
+}
+
+// ---------------------------------------------------------------- fast form
+
+// Accumulates 64x64 products into a 3-word (lo, hi, top) integer.
+struct Acc {
+    u64 lo, hi;
+    u32 top;
+};
+
+template <class C>
+__device__ __forceinline__ void acc_add(Acc& a, u64 x, u64 k)
+{
+    U128 p = mul128<C>(x, k);
+    u64 lo = a.lo + p.lo;
+    u64 c1 = lo < p.lo;
+    u64 hi = a.hi + p.hi;
+    u32 c2 = hi < p.hi;
+    u64 hi2 = hi + c1;
+    c2 += hi2 < hi;
+    a.lo = lo;
+    a.hi = hi2;
+    a.top += c2;
+}
+
+// lo + 2^64 hi + 2^128 top (top < 2^32) to [0, 2^64); 2^128 = -2^32 (mod p).
+__device__ __forceinline__ u64 acc_reduce(const Acc& a)
+{
+    u64 r = gl::reduce128(a.lo, a.hi);
+    u64 t = (u64)a.top << 32;
+    u64 d = r - t;
+    // On borrow d = r - t + 2^64 = r - t + EPS (mod p), and d >= 2^64 - 2^36 > EPS.
+    if (r < t) d -= gl::EPS;
+    return d;
+}
+
+template <class C>
+__device__ __forceinline__ void apply_d0(u64 (&s)[12])
+{
+    u64 t[11];
+#pragma unroll
+    for (int i = 0; i < 11; i++) {
+        Acc a{0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 11; j++) acc_add<C>(a, s[1 + j], c_fast_d0[i * 11 + j]);
+        t[i] = acc_reduce(a);
+    }
+#pragma unroll
+    for (int i = 0; i < 11; i++) s[1 + i] = t[i];
+}
+
+template <class C>
+__device__ __forceinline__ void partial_fast(u64 (&s)[12], int k)
+{
+    u64 x0 = sbox<C>(gl::add_nc_small(s[0], c_fast_a[k]));
+    Acc a{0, 0, 0};
+    acc_add<C>(a, x0, (u64)mds_coef(0));
+#pragma unroll
+    for (int j = 0; j < 11; j++) acc_add<C>(a, s[1 + j], c_fast_v[k * 11 + j]);
+#pragma unroll
+    for (int j = 0; j < 11; j++) s[1 + j] = gl::add_nc(s[1 + j], mulmod<C>(x0, c_fast_w[k * 11 + j]));
+    s[0] = acc_reduce(a);
+}
+
+template <class C>
+__device__ __forceinline__ void full_round_idx(u64 (&s)[12], int f)
+{
+#pragma unroll
+    for (int i = 0; i < 12; i++) s[i] = sbox<C>(gl::add_nc_small(s[i], c_rc_full[f * 12 + i]));
+    mds<C>(s);
+}
+
+template <class C>
+__device__ __forceinline__ void permute_fast(u64 (&s)[12])
+{
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+#pragma unroll 1
+        for (int r = 0; r < 4; r++) full_round_idx<C>(s, 4 * h + r);
+        if (h == 0) {
+            apply_d0<C>(s);
+#pragma unroll 1
+            for (int k = 0; k < 22; k++) partial_fast<C>(s, k);
+        }
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void permute(u64 (&s)[12])
+{
+    if (C::FAST) permute_fast<C>(s);
+    else permute_plain<C>(s);
+}
+
+}  // namespace pos
+}  // namespace v3c

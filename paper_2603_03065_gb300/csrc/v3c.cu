@@ -111,6 +111,7 @@ struct v3c_ctx {
     Tiles tiles;
     u32* d_flag = nullptr;
     serve::Server* server = nullptr;
+    cudaStream_t release_stream = nullptr;  // orders frees of resident objects
     // per-stage timing (V3C_FLAG_TIMING)
     std::mutex tmu;
     struct Pending {
@@ -288,13 +289,24 @@ struct Batch {
             fl.push_back(fl.back() + leaf_items(j, t));
             max_top = std::max(max_top, j.log_N - j.h);
         }
+        // Merkle launches: one per level while the level has enough nodes to
+        // fill the GPU with one compression per thread, then one launch that
+        // folds up to 8 levels per CTA in shared memory.
         fm.clear();
-        for (u32 lev0 = 0; lev0 < max_top; lev0 += 8) {
+        mgroups.clear();
+        for (u32 lev0 = 0; lev0 < max_top;) {
+            u64 nodes = 0;
+            for (auto& j : tree)
+                if (j.log_N - j.h > lev0) nodes += (u64)1 << (j.log_N - lev0 - 1);
+            u32 nlev = nodes >= ((u64)1 << 17) ? 1 : 8;
             std::vector<u32> f(1, 0);
             for (auto& j : tree) f.push_back(f.back() + merkle_items(j, lev0, t));
             fm.push_back(f);
+            mgroups.push_back({lev0, nlev});
+            lev0 += nlev;
         }
     }
+    std::vector<std::pair<u32, u32>> mgroups;  // (first level, levels) of each Merkle launch
 };
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -407,7 +419,7 @@ v3c_status launch_batch(v3c_ctx* ctx, Batch& b, cudaStream_t s)
             StageList lm = list(6 + g, b.fm[g], nt);
             if (!lm.total) continue;
             StageTimer tm(ctx, 4, s);
-            CK(launch_merkle(dt, lm, (u32)(8 * g), 8, t, 0, s));
+            CK(launch_merkle(dt, lm, b.mgroups[g].first, b.mgroups[g].second, t, 0, s));
             tm.done();
             ctx->launches++;
         }
@@ -556,6 +568,7 @@ v3c_status v3c_destroy(v3c_ctx* ctx)
     if (ctx->arena.mem) cudaFree(ctx->arena.mem);
     if (ctx->arena.ev) cudaEventDestroy(ctx->arena.ev);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
+    if (ctx->release_stream) cudaStreamDestroy(ctx->release_stream);
     delete ctx;
     return V3C_OK;
 }
@@ -852,11 +865,14 @@ v3c_status v3c_release(v3c_ctx* ctx, v3c_commit_id id)
     if (it == ctx->objects.end()) return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)id);
     Object o = it->second;
     ctx->objects.erase(it);
-    // Stream-ordered free after the producing work.
-    CK(cudaStreamWaitEvent(o.stream, o.done, 0));
-    CK(cudaFreeAsync(o.lde, o.stream));
-    if (o.tree) CK(cudaFreeAsync(o.tree, o.stream));
-    CK(cudaFreeAsync(o.cap, o.stream));
+    // Stream-ordered free after the producing work, on the context's own
+    // release stream: the producing stream may belong to the caller or to a
+    // serving slot that no longer exists.
+    if (!ctx->release_stream) CK(cudaStreamCreateWithFlags(&ctx->release_stream, cudaStreamNonBlocking));
+    CK(cudaStreamWaitEvent(ctx->release_stream, o.done, 0));
+    CK(cudaFreeAsync(o.lde, ctx->release_stream));
+    if (o.tree) CK(cudaFreeAsync(o.tree, ctx->release_stream));
+    CK(cudaFreeAsync(o.cap, ctx->release_stream));
     CK(cudaEventDestroy(o.done));
     ctx->resident -= o.bytes;
     return V3C_OK;
