@@ -234,6 +234,36 @@ v3c_status v3c_stage_stats(v3c_ctx* ctx, v3c_stage_stats_t* out, int reset);
  * *mhz.  Synchronous. */
 v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz);
 
+/* ---------------- allocation-free LDE ---------------- */
+
+/* No counterpart in the paper: this entry point serves callers that cannot
+ * allocate device memory.  One example is a process that shares the GPU
+ * with a server whose caching allocator already owns the HBM.  Another is a
+ * latency-critical path that must not take the device-wide synchronisation
+ * that cudaMalloc/cudaFree may imply.  It computes exactly what v3c_lde
+ * computes, with the same arguments, on the CURRENT CUDA device and with no
+ * context.  It calls no cudaMalloc, no cudaFree and no other allocating
+ * routine.
+ *
+ * Its work space is one file-scope device array of V3C_NOALLOC_SCRATCH_BYTES.
+ * Every GPU that loads the library holds that array until the process exits.
+ * It needs 8 * (64 + T + c * (n + N)) bytes.  T is the shape's table size,
+ * at most 2n + N + 2^14 words.  The c * (n + N) term is 0 when
+ * n <= 2^(13 - rate_bits).
+ * A larger shape returns V3C_EINVAL before anything is enqueued; for example
+ * 135 x 2^14 rows at rate 3 is too large.  The caller still passes and owns
+ * the input and output buffers.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current.  Make that first call before any stream capture.  All
+ * calls share the array, which keeps the last call's contents.  Every word
+ * is rewritten before it is read, so nothing is cleared.  Calls whose work
+ * overlaps on the GPU (different streams, no ordering) race on the array,
+ * so order them.  Errors: EINVAL (shape, NULL, or over the limit), ECUDA. */
+#define V3C_NOALLOC_SCRATCH_BYTES (32u << 20)
+v3c_status v3c_lde_noalloc(const uint64_t* d_cols, uint32_t c, uint32_t log_n, uint32_t rate_bits,
+                           uint64_t* d_lde, uint32_t ld, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ SIGNATURES = {
     "v3c_serve_stop": (ctypes.c_int, [_vp]),
     "v3c_kernel_launches": (_u64, [_vp]),
     "v3c_stage_stats": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_int]),
+    "v3c_lde_noalloc": (ctypes.c_int, [_vp, _u32, _u32, _u32, _vp, _u32, _vp]),
     "v3c_int_peak": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
 
@@ -146,6 +147,19 @@ def to_device_u64(a: np.ndarray, device="cuda"):
 
 def to_host_u64(t) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint64)
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def lde_noalloc(cols, rate_bits: int, out, ld: int | None = None, stream=None) -> int:
+    """v3c_lde_noalloc on the current device: the LDE of ``cols`` into the
+    caller's preallocated ``out`` [N][ld].  The library allocates nothing;
+    its work space is a fixed device array, for callers that cannot allocate.
+    Returns the v3c status (0 = ok)."""
+    c, n = cols.shape
+    ld = out.shape[1] if ld is None else ld
+    return load().v3c_lde_noalloc(_ptr(cols), c, n.bit_length() - 1, rate_bits, _ptr(out), ld, _stream(stream))
 
 
 @dataclass
