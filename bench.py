@@ -44,15 +44,18 @@ WORKLOADS = {
 # partial rounds 2024 + 576) and per NTT butterfly multiplication.
 W_PER_PERM = 6792
 W_PER_NTT_MUL = 4
-# Integer-pipe peak derived from unit counts and clocks: SMs x wide
-# multiplies per SM per clock x maximum SM clock.
+# Integer-pipe peak derived from unit counts and clocks: 152 SMs x 32 wide
+# multiplies per SM per clock x 2070 MHz.  An SM issues 64 32-bit IMAD lanes
+# per clock (4 SMSPs x 16-lane FMA-heavy pipe; measured 62.6), and a
+# 32x32->64 product takes two of them (lo and hi; IMAD.WIDE measured 23.8 per
+# SM per clock).
 SMS = 152
-WIDE_MUL_PER_SM_CLK = 64
+WIDE_MUL_PER_SM_CLK = 32
 SM_MAX_MHZ = 2070.0
-# DRAM traffic of one leaf-hash launch on this workload (ncu
-# dram__bytes_read.sum + dram__bytes_write.sum; see profiles/); None when the
-# kernel changed since the capture.
-LEAF_HASH_TRAFFIC = {}
+# DRAM traffic of one leaf-hash launch on this workload, from an ncu capture
+# of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum,
+# profiles/launches_large_135x2_20.md).  Drop an entry when the kernel changes.
+LEAF_HASH_TRAFFIC = {"large_135x2_20": 9.715e9}
 # The CPU-baseline / reference-arm sample: the full commit of the same column
 # mix at fewer rows.
 CPU_SAMPLE = synth.Shape(c=135, log_n=14, rate_bits=3, cap_height=4, seed=0)
