@@ -387,6 +387,17 @@ int main(int argc, char** argv)
             rc_full[kRF + r][i] = r == 0 ? fp.rc_after[i] : rc[kRF + kRP + r][i];
         }
     emit_array(f, "V3C_FAST_RC_FULL_INIT", &rc_full[0][0], 2 * kRF * kW);
+    // Round constants split into 22-bit limbs (bits 0-21, 22-43, 44-63) for
+    // rounds 0..29, plus a zero row 30: the MDS of round r starts its limb
+    // accumulators from the constants of round r + 1.
+    fprintf(f, "#define V3C_RC_LIMBS_INIT {");
+    for (int r = 0; r <= kRounds; r++)
+        for (int i = 0; i < kW; i++) {
+            uint64_t v = r < kRounds ? rc[r][i] : 0;
+            fprintf(f, "%s%s%uu, %uu, %uu", (r || i) ? ", " : "", i == 0 ? "\\\n  " : "",
+                    (unsigned)(v & 0x3FFFFF), (unsigned)((v >> 22) & 0x3FFFFF), (unsigned)(v >> 44));
+        }
+    fprintf(f, "}\n");
     fclose(f);
     return 0;
 }

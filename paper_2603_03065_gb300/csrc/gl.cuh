@@ -39,8 +39,42 @@ __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi)
     return r;
 }
 
+// The same reduction as PTX carry chains (no compares or selects).
+// r = lo + h0 EPS carries c, then r - h1 borrows b; the true value is
+// r + (c - b) 2^64 = r + (c - b) EPS (mod p).  With c = 1, b = 0:
+// r < h0 EPS < 2^64 - 2^33, so r + EPS fits.  With c = 0, b = 1:
+// r >= 2^64 - 2^32, so r - EPS >= 0.  With c = b there is no correction.
+// The correction k EPS is added as a 64-bit two's-complement value: low word
+// -k, high word the sign of k.
+__device__ __forceinline__ u64 reduce128_ptx(u64 lo, u64 hi)
+{
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 l0, l1, h0, h1, u0, u1, r0, r1, c, b, k, nk, sk;\n\t"
+        "mov.b64 {l0, l1}, %1;\n\t"
+        "mov.b64 {h0, h1}, %2;\n\t"
+        "sub.cc.u32 u0, 0, h0;\n\t"
+        "subc.u32 u1, h0, 0;\n\t"
+        "add.cc.u32 r0, l0, u0;\n\t"
+        "addc.cc.u32 r1, l1, u1;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "sub.cc.u32 r0, r0, h1;\n\t"
+        "subc.cc.u32 r1, r1, 0;\n\t"
+        "subc.u32 b, 0, 0;\n\t"
+        "add.u32 k, c, b;\n\t"
+        "sub.u32 nk, 0, k;\n\t"
+        "shr.s32 sk, k, 31;\n\t"
+        "add.cc.u32 r0, r0, nk;\n\t"
+        "addc.u32 r1, r1, sk;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(lo), "l"(hi));
+    return r;
+}
+
 // Non-canonical product: inputs in [0, 2^64), output in [0, 2^64).
-__device__ __forceinline__ u64 mul_nc(u64 a, u64 b) { return reduce128(a * b, __umul64hi(a, b)); }
+__device__ __forceinline__ u64 mul_nc(u64 a, u64 b) { return reduce128_ptx(a * b, __umul64hi(a, b)); }
 
 // Canonical product: inputs in [0, 2^64), output in [0, p).
 __device__ __forceinline__ u64 mul(u64 a, u64 b) { return canon(mul_nc(a, b)); }

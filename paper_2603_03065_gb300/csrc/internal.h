@@ -71,6 +71,8 @@ struct Tiles {
     u32 m_threads;           // Merkle threads per CTA
 };
 Tiles default_tiles();
+// Per-job tile choice (stage A i2 columns, stage C / Z q-blocking) from the plan.
+void lde_job_tiles(LdeJob& j);
 
 // Stage launchers (ntt.cu / hash.cu).  Each enqueues one launch on `s`.
 cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s);

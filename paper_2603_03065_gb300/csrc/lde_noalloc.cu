@@ -109,10 +109,7 @@ extern "C" v3c_status v3c_lde_noalloc(const uint64_t* d_cols, uint32_t c, uint32
         j.Y = base + kHeaderWords + table_words;
         j.Z = j.Y + (size_t)c * n;
     }
-    // Same tile rules as the allocating path.
-    u32 n1 = 1u << l1;
-    j.a_cols = std::min(std::min(std::max(1u, 8192u / n1), 8u), 1u << l2);
-    j.c_q = std::min(n1 <= 1024 ? 4u : 2u, 1u << j.plan.log_M);
+    lde_job_tiles(j);  // same tile rules as the allocating path
 
     Tiles t = default_tiles();
     u32 na = stage_a_items(j, t), nb = stage_b_items(j), nc = stage_c_items(j, t);

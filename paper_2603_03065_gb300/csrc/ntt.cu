@@ -167,52 +167,138 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
 
 // ---------------------------------------------------------------- in-CTA DFTs
 
-// B transforms of size L = 2^logL stored back to back in shared memory.
-// Decimation in frequency: natural order in, bit-reversed order out.
-// tw[j] = w_L^j (or w_L^-j) for j < L/2.  Butterfly (i, i+h) of the stage
-// with half-span h uses w_{2h}^pos = tw[pos << s].
+// B transforms of size L = 2^logL stored back to back in shared memory,
+// radix-2 stages applied K at a time in registers: each thread loads the
+// 2^K elements that K consecutive stages combine, runs those stages, and
+// stores them back, so a transform costs ceil(logL / K) shared-memory
+// round trips instead of logL.
+//
+// Decimation in frequency (natural order in, bit-reversed out): stage s has
+// half-span h = L >> (s+1) and butterfly (e, e+h) uses w_{2h}^(e mod h) =
+// tw[(e mod h) << s], tw[j] = w_L^(+-j) for j < L/2.  A pass over stages
+// s0 .. s0+K-1 takes the elements base + j*stride, stride = L >> (s0+K).
+// Shared-memory arrays of 8-byte words are stored XOR-swizzled on 16-word
+// lines: word i lives at sw(i).  A half-warp that walks a column of a strided
+// pass then touches 16 different bank pairs instead of one.
+__device__ __forceinline__ u32 sw(u32 i) { return i ^ ((i >> 4) & 15u); }
+
+template <int K>
+__device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
+{
+    const u32 lst = logL - s0 - K;  // log2 of the stride
+    const u32 G = B << (logL - K);
+    for (u32 g = threadIdx.x; g < G; g += blockDim.x) {
+        u32 tr = g >> (logL - K);
+        u32 gg = g & ((1u << (logL - K)) - 1);
+        u32 lo = gg & ((1u << lst) - 1);
+        u32 hi = gg >> lst;
+        const u32 i0 = (tr << logL) + (hi << (lst + K)) + lo;
+        u64 v[1 << K];
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++) v[j] = a[sw(i0 + ((u32)j << lst))];
+#pragma unroll
+        for (int t = 0; t < K; t++) {
+            const u32 s = s0 + t;
+            const int hb = 1 << (K - 1 - t);
+#pragma unroll
+            for (int j = 0; j < (1 << K); j++) {
+                if (j & hb) continue;
+                const int jj = j | hb;
+                u64 u = v[j], y = v[jj];
+                v[j] = gl::add(u, y);
+                u64 d = gl::sub(u, y);
+                if (s + 1 == logL) {
+                    v[jj] = d;  // last stage: h = 1, twiddle 1
+                } else {
+                    u32 pos = lo + ((u32)(j & (hb - 1)) << lst);
+                    v[jj] = gl::mul(d, tw[sw(pos << s)]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++) a[sw(i0 + ((u32)j << lst))] = v[j];
+    }
+    __syncthreads();
+}
+
+// Decimation in time (bit-reversed order in, natural out): stage s has
+// half-span h = 2^s and butterfly (e, e+h) uses w_{2h}^(e mod h) =
+// tw[(e mod h) << (logL-1-s)].  A pass over stages s0 .. s0+K-1 takes the
+// elements base + (j << s0).
+template <int K>
+__device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
+{
+    const u32 G = B << (logL - K);
+    for (u32 g = threadIdx.x; g < G; g += blockDim.x) {
+        u32 tr = g >> (logL - K);
+        u32 gg = g & ((1u << (logL - K)) - 1);
+        u32 lo = gg & ((1u << s0) - 1);
+        u32 hi = gg >> s0;
+        const u32 i0 = (tr << logL) + (hi << (s0 + K)) + lo;
+        u64 v[1 << K];
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++) v[j] = a[sw(i0 + ((u32)j << s0))];
+#pragma unroll
+        for (int t = 0; t < K; t++) {
+            const u32 s = s0 + t;
+#pragma unroll
+            for (int j = 0; j < (1 << K); j++) {
+                if (j & (1 << t)) continue;
+                const int jj = j | (1 << t);
+                u64 tt;
+                if (s == 0) {
+                    tt = v[jj];  // first stage: h = 1, twiddle 1
+                } else {
+                    u32 pos = lo + ((u32)(j & ((1 << t) - 1)) << s0);
+                    tt = gl::mul(v[jj], tw[sw(pos << (logL - 1 - s))]);
+                }
+                v[jj] = gl::sub(v[j], tt);
+                v[j] = gl::add(v[j], tt);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++) a[sw(i0 + ((u32)j << s0))] = v[j];
+    }
+    __syncthreads();
+}
+
+// Largest radix exponent that keeps every thread busy, capped at 2^4 (32
+// registers of values per thread).
+__device__ __forceinline__ u32 pass_k(u32 B, u32 logL)
+{
+    u32 per = (B << logL) / blockDim.x;  // elements per thread
+    u32 k = per >= 16 ? 4 : per >= 8 ? 3 : per >= 4 ? 2 : 1;
+    return k;
+}
+
 __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw)
 {
-    if (logL == 0) return;
-    u32 half = 1u << (logL - 1);
-    u32 total = B << (logL - 1);
-    for (u32 s = 0; s < logL; s++) {
-        u32 h = half >> s;
-        for (u32 b = threadIdx.x; b < total; b += blockDim.x) {
-            u32 tr = b >> (logL - 1);
-            u32 bb = b & (half - 1);
-            u32 pos = bb & (h - 1);
-            u32 i = ((bb - pos) << 1) + pos;
-            u64* x = a + ((size_t)tr << logL);
-            u64 u = x[i], v = x[i + h];
-            x[i] = gl::add(u, v);
-            x[i + h] = gl::mul(gl::sub(u, v), tw[pos << s]);
+    const u32 kmax = pass_k(B, logL);
+    for (u32 s = 0; s < logL;) {
+        u32 k = min(kmax, logL - s);
+        switch (k) {
+        case 4: dif_pass<4>(a, B, logL, s, tw); break;
+        case 3: dif_pass<3>(a, B, logL, s, tw); break;
+        case 2: dif_pass<2>(a, B, logL, s, tw); break;
+        default: dif_pass<1>(a, B, logL, s, tw); break;
         }
-        __syncthreads();
+        s += k;
     }
 }
 
-// Decimation in time: bit-reversed order in, natural order out.  Stages
-// s < first are skipped (the caller has already applied them).
+// Stages s < first are skipped (the caller has already applied them).
 __device__ __forceinline__ void dft_dit(u64* a, u32 B, u32 logL, const u64* tw, u32 first)
 {
-    if (logL == 0) return;
-    u32 half = 1u << (logL - 1);
-    u32 total = B << (logL - 1);
-    for (u32 s = first; s < logL; s++) {
-        u32 h = 1u << s;
-        for (u32 b = threadIdx.x; b < total; b += blockDim.x) {
-            u32 tr = b >> (logL - 1);
-            u32 bb = b & (half - 1);
-            u32 pos = bb & (h - 1);
-            u32 i = ((bb - pos) << 1) + pos;
-            u64* x = a + ((size_t)tr << logL);
-            u64 u = x[i];
-            u64 t = gl::mul(x[i + h], tw[pos << (logL - 1 - s)]);
-            x[i] = gl::add(u, t);
-            x[i + h] = gl::sub(u, t);
+    const u32 kmax = pass_k(B, logL);
+    for (u32 s = first; s < logL;) {
+        u32 k = min(kmax, logL - s);
+        switch (k) {
+        case 4: dit_pass<4>(a, B, logL, s, tw); break;
+        case 3: dit_pass<3>(a, B, logL, s, tw); break;
+        case 2: dit_pass<2>(a, B, logL, s, tw); break;
+        default: dit_pass<1>(a, B, logL, s, tw); break;
         }
-        __syncthreads();
+        s += k;
     }
 }
 
@@ -245,6 +331,7 @@ size_t stage_a_smem(const LdeJob& j, const Tiles&)
 __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
+    u32 cur_job = 0xFFFFFFFFu;
     for (u32 item = blockIdx.x; item < L.total; item += gridDim.x) {
         u32 jid = find_job(L.first, L.njobs, item);
         const LdeJob& J = jobs[jid];
@@ -257,10 +344,13 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
         const u64* x = J.x + ((size_t)col << J.plan.log_n);
         u64* data = sm;
         u64* tw = sm + ((size_t)T2 << l1);
-        for (u32 e = threadIdx.x; e < n1 / 2; e += blockDim.x) tw[e] = J.plan.rinv_n1[e];
+        if (jid != cur_job) {  // a persistent CTA keeps the tables while the job is the same
+            for (u32 e = threadIdx.x; e < n1 / 2; e += blockDim.x) tw[sw(e)] = J.plan.rinv_n1[e];
+            cur_job = jid;
+        }
         for (u32 e = threadIdx.x; e < (T2 << l1); e += blockDim.x) {
             u32 u = e & (T2 - 1), i1 = e >> lT2;
-            data[((size_t)u << l1) + i1] = x[i20 + u + ((size_t)i1 << l2)];
+            data[sw((u << l1) + i1)] = __ldcs(x + i20 + u + ((size_t)i1 << l2));
         }
         __syncthreads();
         dft_dif(data, T2, l1, tw);
@@ -269,7 +359,7 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
             u32 u = e & (T2 - 1), t = e >> lT2;
             u32 k1 = gl::bitrev(t, l1);
             size_t o = ((size_t)k1 << l2) + i20 + u;
-            Y[o] = gl::mul(data[((size_t)u << l1) + t], J.plan.twa[o]);
+            __stcs(Y + o, gl::mul(data[sw((u << l1) + t)], J.plan.twa[o]));
         }
         __syncthreads();
     }
@@ -285,9 +375,10 @@ size_t stage_b_smem(const LdeJob& j)
     return (M + n2 + std::max<size_t>(n2 / 2, 1) + std::max<size_t>(M / 2, 1)) * sizeof(u64);
 }
 
-__global__ void __launch_bounds__(512) k_stage_b(const LdeJob* __restrict__ jobs, StageList L)
+__global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
+    u32 cur_job = 0xFFFFFFFFu;
     for (u32 item = blockIdx.x; item < L.total; item += gridDim.x) {
         u32 jid = find_job(L.first, L.njobs, item);
         const LdeJob& J = jobs[jid];
@@ -299,11 +390,14 @@ __global__ void __launch_bounds__(512) k_stage_b(const LdeJob* __restrict__ jobs
         u64* stage = sm + M;         // [n2]
         u64* twi = stage + n2;       // [n2/2]
         u64* twf = twi + std::max(n2 / 2, 1u);  // [M/2]
-        for (u32 e = threadIdx.x; e < n2 / 2; e += blockDim.x) twi[e] = J.plan.rinv_n2[e];
-        for (u32 e = threadIdx.x; e < M / 2; e += blockDim.x) twf[e] = J.plan.rfwd_M[e];
+        if (jid != cur_job) {  // a persistent CTA keeps the tables while the job is the same
+            for (u32 e = threadIdx.x; e < n2 / 2; e += blockDim.x) twi[sw(e)] = J.plan.rinv_n2[e];
+            for (u32 e = threadIdx.x; e < M / 2; e += blockDim.x) twf[sw(e)] = J.plan.rfwd_M[e];
+            cur_job = jid;
+        }
         const u64* src = l1 ? J.Y + ((size_t)col << J.plan.log_n) + ((size_t)k1 << l2)
                             : J.x + ((size_t)col << J.plan.log_n);
-        for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[e] = src[e];
+        for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[sw(e)] = __ldcs(src + e);
         __syncthreads();
         dft_dif(stage, 1, l2, twi);  // position t: n * a_{k1 + n1*bitrev(t)}
         const u64* sc = J.plan.scale + ((size_t)k1 << l2);
@@ -311,23 +405,28 @@ __global__ void __launch_bounds__(512) k_stage_b(const LdeJob* __restrict__ jobs
         // In bit-reversed order over log M bits, coefficient k2 sits at
         // bitrev_n2(k2) << r; the first r DIT stages only copy each value
         // into the 2^r slots after it, so they are applied here directly.
-        for (u32 e = threadIdx.x; e < M; e += blockDim.x) {
-            u32 t = e >> r;
-            data[e] = gl::mul(stage[t], sc[t]);
-        }
+        for (u32 t = threadIdx.x; t < n2; t += blockDim.x) stage[sw(t)] = gl::mul(stage[sw(t)], sc[t]);
+        __syncthreads();
+        for (u32 e = threadIdx.x; e < M; e += blockDim.x) data[sw(e)] = stage[sw(e >> r)];
         __syncthreads();
         dft_dit(data, 1, lM, twf, r);
         if (l1) {
-            u64* Z = J.Z + ((size_t)col << J.plan.log_N) + ((size_t)k1 << lM);
+            // Z is q-blocked: block q >> lQ holds [k1][q & (Q-1)], so that
+            // stage C reads one contiguous run per column.
+            u64* Z = J.Z + ((size_t)col << J.plan.log_N);
+            const u32 Q = J.c_q, lQ = __ffs(Q) - 1;
             const u64* tb = J.plan.twb + ((size_t)k1 << lM);
-            for (u32 e = threadIdx.x; e < M; e += blockDim.x) Z[e] = gl::mul(data[e], tb[e]);
+            for (u32 q = threadIdx.x; q < M; q += blockDim.x) {
+                size_t idx = ((size_t)(q >> lQ) << (l1 + lQ)) + ((size_t)k1 << lQ) + (q & (Q - 1));
+                __stcs(Z + idx, gl::mul(data[sw(q)], tb[q]));
+            }
         } else {
             // n1 = 1: this CTA holds the whole column; write committed rows.
             const bool pad = (col + 1 == J.c) && (J.c & 1) && J.c < J.ld;
             for (u32 e = threadIdx.x; e < M; e += blockDim.x) {
                 size_t row = gl::bitrev(e, lM);
-                J.lde[row * J.ld + col] = data[e];
-                if (pad) J.lde[row * J.ld + col + 1] = 0;
+                __stcs(J.lde + row * J.ld + col, data[sw(e)]);
+                if (pad) __stcs(J.lde + row * J.ld + col + 1, 0ull);
             }
         }
         __syncthreads();
@@ -336,23 +435,29 @@ __global__ void __launch_bounds__(512) k_stage_b(const LdeJob* __restrict__ jobs
 
 // ---------------------------------------------------------------- stage C
 
+// Stage C CTAs own 4 adjacent columns, so every row write is a whole 32-byte
+// sector; column groups vary fastest so that concurrent CTAs fill the same
+// rows.
+constexpr u32 kStageCCols = 4;
+
 u32 stage_c_items(const LdeJob& j, const Tiles&)
 {
     if (!j.plan.log_n1) return 0;
-    u32 pairs = (j.c + 1) / 2;
-    return pairs * ((1u << j.plan.log_M) / j.c_q);
+    u32 groups = (j.c + kStageCCols - 1) / kStageCCols;
+    return groups * ((1u << j.plan.log_M) / j.c_q);
 }
 
 size_t stage_c_smem(const LdeJob& j, const Tiles&)
 {
     if (!j.plan.log_n1) return 0;
     size_t n1 = (size_t)1 << j.plan.log_n1;
-    return (2 * j.c_q * n1 + n1 / 2) * sizeof(u64);
+    return (kStageCCols * j.c_q * n1 + n1 / 2) * sizeof(u64);
 }
 
 __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
+    u32 cur_job = 0xFFFFFFFFu;
     for (u32 item = blockIdx.x; item < L.total; item += gridDim.x) {
         u32 jid = find_job(L.first, L.njobs, item);
         const LdeJob& J = jobs[jid];
@@ -360,40 +465,58 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
         const u32 l1 = J.plan.log_n1, lM = J.plan.log_M;
         const u32 n1 = 1u << l1;
         const u32 Q = J.c_q, lQ = __ffs(Q) - 1;
-        const u32 pairs = (J.c + 1) / 2;
-        const u32 cp = local % pairs, q0 = (local / pairs) << lQ;  // pairs fastest: shared rows
-        u64* data = sm;                          // [2][Q][n1]
-        u64* tw = sm + ((size_t)2 * Q << l1);    // [n1/2]
-        for (u32 e = threadIdx.x; e < n1 / 2; e += blockDim.x) tw[e] = J.plan.rfwd_n1[e];
+        const u32 groups = (J.c + kStageCCols - 1) / kStageCCols;
+        const u32 cg = local % groups, qb = local / groups;
+        const u32 q0 = qb << lQ;
+        u64* data = sm;                                   // [4][Q][n1]
+        u64* tw = sm + ((size_t)kStageCCols * Q << l1);   // [n1/2]
+        if (jid != cur_job) {  // a persistent CTA keeps the tables while the job is the same
+            for (u32 e = threadIdx.x; e < n1 / 2; e += blockDim.x) tw[sw(e)] = J.plan.rfwd_n1[e];
+            cur_job = jid;
+        }
+        // Block qb of each column is one contiguous run of n1*Q words, [k1][v].
         const u32 per = Q << l1;
-        for (u32 e = threadIdx.x; e < 2 * per; e += blockDim.x) {
-            u32 w = e / per, rem = e - w * per;
+        for (u32 e = threadIdx.x; e < kStageCCols * per; e += blockDim.x) {
+            u32 w = e >> (l1 + lQ), rem = e & (per - 1);
             u32 v = rem & (Q - 1), k1 = rem >> lQ;
-            u32 col = 2 * cp + w;
+            u32 col = kStageCCols * cg + w;
             u64 val = 0;
-            if (col < J.c)
-                val = J.Z[((size_t)col << J.plan.log_N) + ((size_t)k1 << lM) + q0 + v];
-            data[((size_t)(w * Q + v) << l1) + k1] = val;
+            if (col < J.c) val = __ldcs(J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQ)) + rem);
+            data[sw(((w * Q + v) << l1) + k1)] = val;
         }
         __syncthreads();
-        dft_dif(data, 2 * Q, l1, tw);
-        const u32 c0 = 2 * cp;
-        const bool two = c0 + 1 < J.ld;
+        dft_dif(data, kStageCCols * Q, l1, tw);
+        const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
             size_t row = ((size_t)gl::bitrev(q0 + v, lM) << l1) + u;
-            u64 a = data[((size_t)v << l1) + u];
-            u64 b = data[((size_t)(Q + v) << l1) + u];
+            u64 a[kStageCCols];
+#pragma unroll
+            for (u32 w = 0; w < kStageCCols; w++) a[w] = data[sw(((w * Q + v) << l1) + u)];
             u64* dst = J.lde + row * J.ld + c0;
-            if (J.vec_ok) {
-                *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(a, b);
-            } else {
-                dst[0] = a;
-                if (two) dst[1] = b;
+#pragma unroll
+            for (u32 p = 0; p < kStageCCols; p += 2) {
+                if (J.vec_ok && c0 + p + 2 <= J.ld) {
+                    __stcs(reinterpret_cast<ulonglong2*>(dst + p), make_ulonglong2(a[p], a[p + 1]));
+                } else {
+                    if (c0 + p < J.ld) __stcs(dst + p, a[p]);
+                    if (c0 + p + 1 < J.ld) __stcs(dst + p + 1, a[p + 1]);
+                }
             }
         }
         __syncthreads();
     }
+}
+
+void lde_job_tiles(LdeJob& j)
+{
+    u32 l1 = j.plan.log_n1, l2 = j.plan.log_n2;
+    u32 n1 = 1u << l1;
+    // Stage A: i2 columns per CTA, up to 8 (64-byte runs), within 64 KiB.
+    j.a_cols = std::min(std::min(std::max(1u, 8192u / n1), 8u), 1u << l2);
+    // Stage C / Z blocking: q values per CTA, within 64 KiB for 4 columns.
+    j.c_q = std::min(std::max(1u, 2048u / n1), 1u << j.plan.log_M);
+    j.c_q = std::min(j.c_q, 8u);
 }
 
 // ---------------------------------------------------------------- launchers

@@ -37,6 +37,8 @@ __constant__ u64 c_fast_d0[11 * 11] = V3C_FAST_D0_INIT;
 // Full rounds 0-3, then 26-29 with the constants carried out of the fast
 // partial rounds folded into round 26.
 __constant__ u64 c_rc_full[8 * 12] = V3C_FAST_RC_FULL_INIT;
+// Round constants as 22-bit limbs [round 0..30][lane][3]; row 30 is zero.
+__constant__ u32 c_rc_limbs[31 * 12 * 3] = V3C_RC_LIMBS_INIT;
 
 __host__ __device__ constexpr u32 mds_coef(int k)
 {
@@ -47,16 +49,60 @@ __host__ __device__ constexpr u32 mds_coef(int k)
 enum MulKind { MUL_INTRINSIC = 0, MUL_PTX = 1, MUL_WIDE = 2 };
 enum MdsKind { MDS_WIDE = 0, MDS_LIMB = 1 };
 
-template <int MUL_, int MDS_, bool SQR_, bool FAST_>
+// FOLD2: the limb sums are recombined with 32x32->64 multiply-adds and one
+// carry chain instead of shifts and compares.  ARCM: the round constants of
+// round r+1 start the limb accumulators of round r's MDS, so the constant
+// addition costs nothing after round 0.
+// FOLD3 / RED: the limb fold and the 128-bit reduction written as PTX
+// carry chains (no compares or selects).
+template <int MUL_, int MDS_, bool SQR_, bool FAST_, bool FOLD2_ = false, bool ARCM_ = false,
+          bool FOLD3_ = false, bool RED_ = false>
 struct Cfg {
     static constexpr int MUL = MUL_;
     static constexpr int MDS = MDS_;
     static constexpr bool SQR = SQR_;
     static constexpr bool FAST = FAST_;
+    static constexpr bool FOLD2 = FOLD2_;
+    static constexpr bool ARCM = ARCM_;
+    static constexpr bool FOLD3 = FOLD3_;
+    static constexpr bool RED = RED_;
 };
+
+// A + B 2^22 + C 2^44 (A, B, C < 2^32) to [0, 2^64) with carry chains:
+// w0 = A + (B << 22) carries c0; w1 = (B >> 10) + (C << 12 mod 2^32) + c0
+// carries c1; the multiple of 2^64 is h = (C >> 20) + c1 < 2^13, folded as
+// h EPS = h 2^32 - h.  (w1:w0) + h EPS carries at most once, and after a
+// carry the sum is below 2^45, so adding EPS cannot carry again.
+__device__ __forceinline__ u64 limb_fold3(u32 A, u32 B, u32 Cc)
+{
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 t, u, v, w0, w1, hh, h, u0, u1, r0, r1, c;\n\t"
+        "shl.b32 t, %2, 22;\n\t"
+        "add.cc.u32 w0, %1, t;\n\t"
+        "shr.b32 u, %2, 10;\n\t"
+        "shl.b32 v, %3, 12;\n\t"
+        "addc.cc.u32 w1, u, v;\n\t"
+        "shr.b32 hh, %3, 20;\n\t"
+        "addc.u32 h, hh, 0;\n\t"
+        "sub.cc.u32 u0, 0, h;\n\t"
+        "subc.u32 u1, h, 0;\n\t"
+        "add.cc.u32 r0, w0, u0;\n\t"
+        "addc.cc.u32 r1, w1, u1;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "sub.cc.u32 r0, r0, c;\n\t"       // + c EPS = + c 2^32 - c
+        "subc.u32 r1, r1, 0;\n\t"
+        "add.u32 r1, r1, c;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "r"(A), "r"(B), "r"(Cc));
+    return r;
+}
 // The configuration the library's kernels use (fastest measured on GB300:
-// 32-bit limb MDS, compiler 64-bit products, plain round order).
-typedef Cfg<MUL_INTRINSIC, MDS_LIMB, false, false> Default;
+// PTX 64x64 products, 22-bit-limb MDS, round constants merged into the MDS
+// accumulators, PTX carry-chain fold and reduction, plain round order).
+typedef Cfg<MUL_PTX, MDS_LIMB, false, false, false, true, true, true> Default;
 
 struct U128 {
     u64 lo, hi;
@@ -122,19 +168,21 @@ __device__ __forceinline__ U128 mul128(u64 a, u64 b)
 }
 
 template <class C>
+__device__ __forceinline__ u64 reduce(U128 p)
+{
+    return C::RED ? gl::reduce128_ptx(p.lo, p.hi) : gl::reduce128(p.lo, p.hi);
+}
+
+template <class C>
 __device__ __forceinline__ u64 mulmod(u64 a, u64 b)
 {
-    U128 p = mul128<C>(a, b);
-    return gl::reduce128(p.lo, p.hi);
+    return reduce<C>(mul128<C>(a, b));
 }
 
 template <class C>
 __device__ __forceinline__ u64 sqrmod(u64 a)
 {
-    if (C::SQR) {
-        U128 p = sqr128_wide(a);
-        return gl::reduce128(p.lo, p.hi);
-    }
+    if (C::SQR) return reduce<C>(sqr128_wide(a));
     return mulmod<C>(a, a);
 }
 
@@ -173,9 +221,39 @@ __device__ __forceinline__ u64 limb_fold(u32 A, u32 B, u32 Cc)
     return r;
 }
 
-// s <- M s, M[i][j] = m[(j - i) mod 12].
+// A + B 2^22 + C 2^44 for A, B, C < 2^32, folded to [0, 2^64) with wide
+// multiply-adds: x = A + B 2^22 (< 2^55); t = hi32(x) + C 2^12 (< 2^45) is the
+// word above bit 32, so V = lo32(x) + lo32(t) 2^32 + h 2^64 with h = t >> 32
+// (< 2^13), and 2^64 = EPS (mod p).  v + h EPS carries at most once, and
+// after a carry the sum is below 2^45, so adding EPS cannot carry again.
+__device__ __forceinline__ u64 limb_fold2(u32 A, u32 B, u32 Cc)
+{
+    u64 x = (u64)B * (1u << 22) + A;
+    u64 t = (u64)Cc * (1u << 12) + (u32)(x >> 32);
+    u32 h = (u32)(t >> 32);
+    u64 v = ((u64)(u32)t << 32) | (u32)x;
+    u64 u = (u64)h * 0xFFFFFFFFu;
+    u64 r;
+    u32 c;
+    asm("{\n\t"
+        ".reg .u32 v0, v1, u0, u1, r0, r1;\n\t"
+        "mov.b64 {v0, v1}, %2;\n\t"
+        "mov.b64 {u0, u1}, %3;\n\t"
+        "add.cc.u32 r0, v0, u0;\n\t"
+        "addc.cc.u32 r1, v1, u1;\n\t"
+        "addc.u32 %1, 0, 0;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r), "=r"(c)
+        : "l"(v), "l"(u));
+    return (u64)c * 0xFFFFFFFFu + r;
+}
+
+// s <- M s, M[i][j] = m[(j - i) mod 12].  With C::ARCM the accumulators start
+// from the limbs `init` (the next round's constants), so the output is
+// M s + RC.
 template <class C>
-__device__ __forceinline__ void mds(u64 (&s)[12])
+__device__ __forceinline__ void mds(u64 (&s)[12], const u32* init = nullptr)
 {
     u64 out[12];
     if (C::MDS == MDS_LIMB) {
@@ -188,7 +266,13 @@ __device__ __forceinline__ void mds(u64 (&s)[12])
         }
 #pragma unroll
         for (int i = 0; i < 12; i++) {
+            // Bounds: 12 * 63 * (2^22 - 1) + 2^22 < 2^32, so no limb sum wraps.
             u32 A = 0, B = 0, Cc = 0;
+            if (C::ARCM) {
+                A = init[3 * i];
+                B = init[3 * i + 1];
+                Cc = init[3 * i + 2];
+            }
 #pragma unroll
             for (int j = 0; j < 12; j++) {
                 const u32 m = mds_coef((j - i + 12) % 12);
@@ -196,7 +280,7 @@ __device__ __forceinline__ void mds(u64 (&s)[12])
                 B += b[j] * m;
                 Cc += c[j] * m;
             }
-            out[i] = limb_fold(A, B, Cc);
+            out[i] = C::FOLD3 ? limb_fold3(A, B, Cc) : C::FOLD2 ? limb_fold2(A, B, Cc) : limb_fold(A, B, Cc);
         }
     } else {
         u32 lo[12], hi[12];
@@ -227,6 +311,22 @@ __device__ __forceinline__ void mds(u64 (&s)[12])
 template <class C>
 __device__ __forceinline__ void permute_plain(u64 (&s)[12])
 {
+    if (C::ARCM) {
+        // Round 0's constants are added here; every MDS adds the next round's.
+#pragma unroll
+        for (int i = 0; i < 12; i++) s[i] = gl::add_nc_small(s[i], c_rc[0][i]);
+#pragma unroll 1
+        for (int r = 0; r < 30; r++) {
+            if (r < 4 || r >= 26) {
+#pragma unroll
+                for (int i = 0; i < 12; i++) s[i] = sbox<C>(s[i]);
+            } else {
+                s[0] = sbox<C>(s[0]);
+            }
+            mds<C>(s, c_rc_limbs + (r + 1) * 36);
+        }
+        return;
+    }
 #pragma unroll 1
     for (int r = 0; r < 30; r++) {
         if (r < 4 || r >= 26) {

@@ -43,7 +43,7 @@ Tiles default_tiles()
     Tiles t;
     t.a_threads = 256;
     t.a_cols = 8;
-    t.b_threads = 512;
+    t.b_threads = 256;
     t.c_threads = 256;
     t.c_q = 4;
     t.h_threads = 128;
@@ -251,14 +251,7 @@ v3c_status upload_done(v3c_ctx* ctx, u32 slot, cudaStream_t s)
     return V3C_OK;
 }
 
-static void job_tiles(LdeJob& j)
-{
-    u32 l1 = j.plan.log_n1, l2 = j.plan.log_n2;
-    u32 n1 = 1u << l1;
-    u32 ac = std::max(1u, 8192u / n1);
-    j.a_cols = std::min(std::min(ac, 8u), 1u << l2);
-    j.c_q = std::min(n1 <= 1024 ? 4u : 2u, 1u << j.plan.log_M);
-}
+static void job_tiles(LdeJob& j) { lde_job_tiles(j); }
 
 // A batch of LDE jobs and tree jobs, launched as one persistent launch per
 // stage.  Builds the upload blob (jobs + stage item lists).
