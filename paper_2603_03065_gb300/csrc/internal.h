@@ -40,8 +40,8 @@ struct LdeJob {
     u32 c, ld;
     u32 vec_ok;    // lde 16-byte aligned and ld even
     u32 a_cols;    // stage A: i2 columns per CTA (power of two, <= n2)
-    u32 c_q;       // stage C: q values per CTA (power of two, <= M)
-    u32 pad;
+    u32 c_q;       // Z block: q values per block (power of two, <= M)
+    u32 c_qc;      // stage C: q values per CTA (power of two, <= c_q)
 };
 
 // One Merkle job: leaf hashes then tree levels up to the cap.

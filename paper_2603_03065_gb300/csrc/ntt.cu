@@ -444,14 +444,14 @@ u32 stage_c_items(const LdeJob& j, const Tiles&)
 {
     if (!j.plan.log_n1) return 0;
     u32 groups = (j.c + kStageCCols - 1) / kStageCCols;
-    return groups * ((1u << j.plan.log_M) / j.c_q);
+    return groups * ((1u << j.plan.log_M) / j.c_qc);
 }
 
 size_t stage_c_smem(const LdeJob& j, const Tiles&)
 {
     if (!j.plan.log_n1) return 0;
     size_t n1 = (size_t)1 << j.plan.log_n1;
-    return (kStageCCols * j.c_q * n1 + n1 / 2) * sizeof(u64);
+    return (kStageCCols * j.c_qc * n1 + n1 / 2) * sizeof(u64);
 }
 
 __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
@@ -464,24 +464,29 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
         u32 local = item - L.first[jid];
         const u32 l1 = J.plan.log_n1, lM = J.plan.log_M;
         const u32 n1 = 1u << l1;
-        const u32 Q = J.c_q, lQ = __ffs(Q) - 1;
+        const u32 Qz = J.c_q, lQz = __ffs(Qz) - 1;  // Z block size
+        const u32 Q = J.c_qc, lQ = __ffs(Q) - 1;    // q values of this CTA
         const u32 groups = (J.c + kStageCCols - 1) / kStageCCols;
-        const u32 cg = local % groups, qb = local / groups;
-        const u32 q0 = qb << lQ;
+        const u32 cg = local % groups, qt = local / groups;
+        const u32 q0 = qt << lQ;
+        const u32 qb = q0 >> lQz, qoff = q0 & (Qz - 1);
         u64* data = sm;                                   // [4][Q][n1]
         u64* tw = sm + ((size_t)kStageCCols * Q << l1);   // [n1/2]
         if (jid != cur_job) {  // a persistent CTA keeps the tables while the job is the same
             for (u32 e = threadIdx.x; e < n1 / 2; e += blockDim.x) tw[sw(e)] = J.plan.rfwd_n1[e];
             cur_job = jid;
         }
-        // Block qb of each column is one contiguous run of n1*Q words, [k1][v].
+        // Block qb of each column is one contiguous run of n1*Qz words, [k1][v];
+        // this CTA takes v in [qoff, qoff + Q).
         const u32 per = Q << l1;
         for (u32 e = threadIdx.x; e < kStageCCols * per; e += blockDim.x) {
             u32 w = e >> (l1 + lQ), rem = e & (per - 1);
             u32 v = rem & (Q - 1), k1 = rem >> lQ;
             u32 col = kStageCCols * cg + w;
             u64 val = 0;
-            if (col < J.c) val = __ldcs(J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQ)) + rem);
+            if (col < J.c)
+                val = __ldcg(J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQz)) +
+                             ((size_t)k1 << lQz) + qoff + v);
             data[sw(((w * Q + v) << l1) + k1)] = val;
         }
         __syncthreads();
@@ -514,9 +519,15 @@ void lde_job_tiles(LdeJob& j)
     u32 n1 = 1u << l1;
     // Stage A: i2 columns per CTA, up to 8 (64-byte runs), within 64 KiB.
     j.a_cols = std::min(std::min(std::max(1u, 8192u / n1), 8u), 1u << l2);
-    // Stage C / Z blocking: q values per CTA, within 64 KiB for 4 columns.
-    j.c_q = std::min(std::max(1u, 2048u / n1), 1u << j.plan.log_M);
+    // Stage C / Z blocking: q values per block, so that stage B writes runs of
+    // at least 32 bytes (whole sectors) where n1 allows; 4 columns x c_q x n1
+    // stay within 128 KiB of shared memory.
+    j.c_q = std::min(std::max(1u, 4096u / n1), 1u << j.plan.log_M);
     j.c_q = std::min(j.c_q, 8u);
+    // Stage C CTAs take c_qc <= c_q of those q values (4 columns x c_qc x n1
+    // within 64 KiB, two CTAs per SM); the CTAs sharing a block run side by
+    // side, so each 32-byte run is fetched from DRAM once.
+    j.c_qc = std::min(j.c_q, std::max(1u, 2048u / n1));
 }
 
 // ---------------------------------------------------------------- launchers
