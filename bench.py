@@ -146,7 +146,7 @@ def run_reference(args):
         oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)
     dt = (time.perf_counter() - t0) / args.steps
     value = s.lde_elems() / dt / 1e9
-    w = WORKLOADS[args.workload]
+    w = WORKLOADS.get(args.workload, synth.LARGE_135x2_20)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
@@ -294,18 +294,191 @@ def run_v3c(args):
     return 0
 
 
+def run_batched(args):
+    """64 uneven column-batches (seed 3): one v3c_commit over all of them
+    (one persistent launch per stage, replayed from a CUDA graph) against 64
+    one-batch commits (per-batch launches), on the same device-resident
+    inputs.  Not the default bench line; see the design doc."""
+    import torch
+
+    import paper_2603_03065_gb300 as v3c
+
+    torch.cuda.set_device(0)
+    shapes = synth.uneven_batches(3)
+    xs = [s.inputs() for s in shapes]
+    elems = sum(s.lde_elems() for s in shapes)
+    out = {"metric": METRIC, "unit": "Gelem/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "dtype": "u64", "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": "uneven_64", "batches": len(shapes), "lde_elems": elems,
+                      "log_rows": [s.log_n for s in shapes], "columns": [s.c for s in shapes],
+                      "rate_bits": [s.rate_bits for s in shapes], "cap_height": 4, "seed": 3}}
+    stream = torch.cuda.current_stream()
+    for tag, flags, tune in (("batched_graph_autotune", 0, True), ("batched_graph", 0, False),
+                             ("batched_direct", v3c.FLAG_NO_GRAPH, False)):
+        ctx = v3c.Context(0, flags=flags, autotune=tune)
+        ds = [v3c.to_device_u64(x) for x in xs]
+        items = [(d, s.rate_bits, s.cap_height) for d, s in zip(ds, shapes)]
+
+        def batched():
+            ids = ctx.commit(items, stream=stream)
+            for i in ids:
+                ctx.release(i)
+
+        def per_batch():
+            for it in items:
+                ctx.release(ctx.commit([it], stream=stream)[0])
+
+        for name, fn in (("all_in_one", batched), ("one_per_commit", per_batch)):
+            if tag != "batched_graph" and name == "one_per_commit":
+                continue
+            for _ in range(max(args.warmup, 1)):
+                fn()
+            torch.cuda.synchronize()
+            l0 = ctx.kernel_launches()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            out[f"{tag}.{name}"] = {"ms_per_step": ms, "Gelem/s": elems / (ms * 1e-3) / 1e9,
+                                    "launches_per_step": (ctx.kernel_launches() - l0) / args.steps}
+        ctx.close()
+    best = out["batched_graph_autotune.all_in_one"]
+    out["value"] = best["Gelem/s"]
+    out["ms_per_step"] = best["ms_per_step"]
+    out["vs_per_batch_launches"] = best["Gelem/s"] / out["batched_graph.one_per_commit"]["Gelem/s"]
+    print(json.dumps(out))
+    return 0
+
+
+def run_serving(args):
+    """Poisson arrivals (rate --rate, --duration s, seed 5) of commits drawn
+    from the mixture 50 % 2^14 x 80, 35 % 2^16 x 135, 15 % 2^18 x 135 (rate 3,
+    cap 4), served by the continuous-batching loop from pinned host inputs
+    (borrowed, copied at admission), each released as soon as it is done.
+    Reports p50/p99 submit->done latency after a 5 s warm-up and Gelem/s, and
+    the same trace through the serial one-at-a-time commit path.  Not the
+    default bench line; see the design doc."""
+    import torch
+
+    import paper_2603_03065_gb300 as v3c
+
+    torch.cuda.set_device(0)
+    trace = synth.poisson_trace(rate=args.rate, duration=args.duration, seed=5)
+    # A pool of two distinct inputs per mixture shape, pinned on the host.
+    pool = {}
+    for k, (_, log_n, c) in enumerate(synth.SERVE_MIX):
+        for b in range(2):
+            s = synth.Shape(c=c, log_n=log_n, rate_bits=3, cap_height=4, batch=1000 + 2 * k + b, seed=5)
+            t = torch.from_numpy(s.inputs().view(np.int64)).pin_memory()
+            pool[(log_n, c, b)] = t.numpy().view(np.uint64)
+
+    def src(i, req):
+        return pool[(req.shape.log_n, req.shape.c, i % 2)]
+
+    def summarize(lat, t_first, t_last, elems):
+        lat = sorted(lat)
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None  # noqa: E731
+        return {"requests": len(lat), "p50_ms": q(0.50) * 1e3 if lat else None,
+                "p99_ms": q(0.99) * 1e3 if lat else None,
+                "Gelem/s": elems / max(t_last - t_first, 1e-9) / 1e9}
+
+    ctx = v3c.Context(0, hbm_budget_bytes=150 << 30, max_inflight=args.inflight)
+    # warm plans and graphs for the three shapes
+    for (log_n, c, b), a in pool.items():
+        if b == 0:
+            ctx.release(ctx.commit([(a, 3, 4)])[0])
+    torch.cuda.synchronize()
+    ctx.serve_start(max_batch=args.max_batch)
+    pending = {}
+    lat, done_elems, t_first, t_last = [], 0, None, None
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(trace) or pending:
+        now = time.perf_counter() - t0
+        while i < len(trace) and trace[i].t_arrive <= now:
+            req = trace[i]
+            tk = ctx.serve_submit(src(i, req), 3, 4, borrow=True)
+            if tk < 0:
+                break                                   # queue full: retry on the next pass
+            pending[tk] = req
+            i += 1
+        for tk in list(pending):
+            st, state, _, times = ctx.serve_poll(tk)
+            if st == v3c.V3C_EAGAIN:
+                continue
+            req = pending.pop(tk)
+            if st != v3c.V3C_OK:
+                raise RuntimeError(f"request failed with status {st}")
+            ctx.release(tk)
+            if req.t_arrive >= 5.0 or args.duration <= 5.0:
+                lat.append(times[3] - times[0])
+                done_elems += req.shape.lde_elems()
+                t_first = times[0] if t_first is None else min(t_first, times[0])
+                t_last = times[3] if t_last is None else max(t_last, times[3])
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    ctx.serve_stop()
+    served = summarize(lat, t_first or 0, t_last or 1, done_elems)
+    served["wall_s"] = wall
+
+    # Serial path: one commit at a time, in arrival order, from the same pinned
+    # inputs; latency = done - arrival.
+    stream = torch.cuda.current_stream()
+    lat_s, elems_s = [], 0
+    t0 = time.perf_counter()
+    t_first_s = None
+    for k, req in enumerate(trace):
+        now = time.perf_counter() - t0
+        if req.t_arrive > now:
+            time.sleep(req.t_arrive - now)
+        cid = ctx.commit([(src(k, req), 3, 4)], stream=stream)[0]
+        ctx.cap(cid)
+        ctx.release(cid)
+        t_done = time.perf_counter() - t0
+        if req.t_arrive >= 5.0 or args.duration <= 5.0:
+            lat_s.append(t_done - req.t_arrive)
+            elems_s += req.shape.lde_elems()
+            t_first_s = req.t_arrive if t_first_s is None else t_first_s
+    serial = summarize(lat_s, t_first_s or 0, time.perf_counter() - t0, elems_s)
+    ctx.close()
+    mean_elems = sum(r.shape.lde_elems() for r in trace) / max(len(trace), 1)
+    out = {"metric": METRIC, "unit": "Gelem/s", "value": served["Gelem/s"], "higher_is_better": True,
+           "n_gpus": 1, "dtype": "u64", "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": "serve_poisson", "rate_rps": args.rate, "duration_s": args.duration,
+                      "requests": len(trace), "mix": [list(m) for m in synth.SERVE_MIX], "rate_bits": 3,
+                      "cap_height": 4, "hbm_budget_gb": 150, "max_batch": args.max_batch,
+                      "max_inflight": args.inflight, "offered_Gelem_per_s": args.rate * mean_elems / 1e9},
+           "served": served, "serial": serial,
+           "vs_serial_throughput": served["Gelem/s"] / max(serial["Gelem/s"], 1e-12)}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["v3c", "reference"], default="v3c")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large_135x2_20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven_64", "serve_poisson"],
+                    default="large_135x2_20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--int-peak", action="store_true", help="also run the integer-pipe microbenchmark")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve_poisson: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve_poisson: trace length in seconds")
+    ap.add_argument("--max-batch", type=int, default=32, help="serve_poisson: requests per batched pass")
+    ap.add_argument("--inflight", type=int, default=4, help="serve_poisson: batches in flight")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven_64":
+        return run_batched(args)
+    if args.workload == "serve_poisson":
+        return run_serving(args)
     return run_v3c(args)
 
 

@@ -71,12 +71,15 @@ typedef uint64_t v3c_commit_id;
 #define V3C_MAX_RATE_BITS 4
 
 #define V3C_FLAG_VALIDATE 0x1u  /* check that inputs are canonical */
+#define V3C_FLAG_NO_GRAPH 0x4u  /* v3c_commit: launch stages directly instead of replaying a CUDA graph */
 
 typedef struct {
     uint64_t hbm_budget_bytes;  /* resident commit objects + scratch; 0 = 90% of free memory */
     uint32_t max_inflight;      /* serving: concurrent batches on the device (0 = 4) */
     uint32_t flags;             /* V3C_FLAG_* applied to every call */
-    uint32_t autotune;          /* 1 = time tile variants once per shape, 0 = defaults */
+    uint32_t autotune;          /* 1 = v3c_commit times tile variants (NTT radix cap, stage tiles,
+                                   leaf-hash CTA size) once per (log_n, rate_bits) shape on a
+                                   synthetic problem and keeps the fastest; 0 = built-in defaults */
     uint32_t timeout_ms;        /* bounded host waits (0 = 60000) */
 } v3c_config;
 
@@ -117,10 +120,16 @@ v3c_status v3c_merkle(v3c_ctx* ctx, const uint64_t* d_rows, uint32_t ld, uint32_
                       uint32_t log_rows, uint32_t cap_height, uint64_t* d_tree, uint64_t* d_cap,
                       void* stream);
 
+/* Where a request's input lives (v3c_commit_desc.on_device). */
+#define V3C_INPUT_HOST_COPY 0   /* host memory; the serving loop copies it at submit */
+#define V3C_INPUT_DEVICE 1      /* device memory, kept alive by the caller until DONE */
+#define V3C_INPUT_HOST_BORROW 2 /* host memory (pinned for an asynchronous copy), kept alive by the
+                                   caller until DONE; copied to the device at admission */
+
 /* One commit request: LDE of `cols` followed by the Merkle tree of its rows. */
 typedef struct {
-    const uint64_t* cols;  /* [c][n] column-major, device (on_device=1) or host (on_device=0) */
-    int32_t on_device;
+    const uint64_t* cols;  /* [c][n] column-major; see on_device */
+    int32_t on_device;     /* V3C_INPUT_*; v3c_commit treats both host kinds alike (copied in the call) */
     uint32_t c;
     uint32_t log_n;
     uint32_t rate_bits;
@@ -130,11 +139,14 @@ typedef struct {
 /* Batched commit (many uneven shapes in one launch per stage).  For each desc
  * it allocates a resident object that holds the LDE [N][ld] (ld = c rounded
  * up to even) and the tree, and enqueues every stage on `stream`.  The stages
- * run as one persistent launch each over all descs (under a CUDA graph when
- * the same batch shape repeats).  ids[i] receives the object id.  Host
- * inputs are copied to the device inside the call.  The objects stay
- * resident until v3c_release.  Errors: EINVAL, ENOMEM (the HBM budget would
- * be exceeded; nothing is allocated), ECUDA. */
+ * run as one persistent launch each over all descs.  The first call with a
+ * given batch signature (shapes, tiles) captures the stage launches, together
+ * with the copy of the job table, into a CUDA graph.  Later calls with that
+ * signature rewrite the job table and replay the graph.  V3C_FLAG_NO_GRAPH
+ * or V3C_FLAG_TIMING selects direct launches instead.  ids[i] receives the
+ * object id.  Host inputs are copied to the device inside the call.  The
+ * objects stay resident until v3c_release.  Errors: EINVAL, ENOMEM (the HBM
+ * budget would be exceeded; nothing is allocated), ECUDA. */
 v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v3c_commit_id* ids,
                       void* stream);
 
@@ -169,6 +181,8 @@ typedef struct {
     uint32_t max_batch;         /* requests fused into one batched launch (0 = 32) */
     uint32_t max_inflight;      /* batches in flight on separate streams (0 = ctx setting) */
     uint32_t flags;             /* V3C_FLAG_VALIDATE */
+    uint64_t slot_scratch_bytes; /* LDE scratch + staged inputs one pass may take (0 = 16 GiB);
+                                    a pass always takes at least one request */
 } v3c_serve_cfg;
 
 typedef enum {
@@ -190,11 +204,13 @@ typedef struct {
  * arrives while others are on the device joins the next pass. */
 v3c_status v3c_serve_start(v3c_ctx* ctx, const v3c_serve_cfg* cfg);
 
-/* Non-blocking submit.  desc->cols is a host pointer (on_device = 0), copied
- * into library memory before the call returns, or a device pointer
- * (on_device = 1) that the caller keeps alive until the state reaches DONE.
- * *ticket receives the id, which is also the commit id for v3c_open and
- * v3c_release.  Errors: EAGAIN (queue full), EINVAL, ECANCELED (not
+/* Non-blocking submit.  desc->on_device says where desc->cols lives:
+ * V3C_INPUT_HOST_COPY copies the host input into library memory before the
+ * call returns.  V3C_INPUT_HOST_BORROW (pinned host memory) and
+ * V3C_INPUT_DEVICE borrow the caller's buffer, which must stay alive until
+ * the state reaches DONE.  *ticket receives the id, which is also the commit
+ * id for v3c_open and v3c_release.  Errors: EAGAIN (queue full), EINVAL,
+ * ENOMEM (the footprint exceeds the whole budget), ECANCELED (not
  * serving). */
 v3c_status v3c_serve_submit(v3c_ctx* ctx, const v3c_commit_desc* desc, uint64_t* ticket);
 

@@ -46,7 +46,12 @@ class CommitDesc(ctypes.Structure):
 
 
 class ServeCfg(ctypes.Structure):
-    _fields_ = [("queue_capacity", _u32), ("max_batch", _u32), ("max_inflight", _u32), ("flags", _u32)]
+    _fields_ = [("queue_capacity", _u32), ("max_batch", _u32), ("max_inflight", _u32), ("flags", _u32),
+                ("slot_scratch_bytes", _u64)]
+
+
+FLAG_NO_GRAPH = 4
+INPUT_HOST_COPY, INPUT_DEVICE, INPUT_HOST_BORROW = 0, 1, 2
 
 
 FLAG_TIMING = 2
@@ -171,9 +176,11 @@ class Opening:
 class Context:
     """One v3c context on one CUDA device."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0, flags: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 0, flags: int = 0,
+                 autotune: bool = False):
         self.lib = load()
-        cfg = Config(hbm_budget_bytes, max_inflight, flags, 0, 0)
+        cfg = Config(hbm_budget_bytes, max_inflight, flags, 1 if autotune else 0, 0)
+        self._borrowed = {}
         h = _vp()
         self._check(self.lib.v3c_create(device, ctypes.byref(cfg), ctypes.byref(h)), None)
         self.h = h
@@ -286,20 +293,33 @@ class Context:
 
     def release(self, cid: int):
         self._check(self.lib.v3c_release(self.h, cid))
+        self._borrowed.pop(cid, None)
 
     # --------------------------------------------------------------- serving
-    def serve_start(self, queue_capacity=0, max_batch=0, max_inflight=0, flags=0):
-        cfg = ServeCfg(queue_capacity, max_batch, max_inflight, flags)
+    def serve_start(self, queue_capacity=0, max_batch=0, max_inflight=0, flags=0, slot_scratch_bytes=0):
+        cfg = ServeCfg(queue_capacity, max_batch, max_inflight, flags, slot_scratch_bytes)
         self._check(self.lib.v3c_serve_start(self.h, ctypes.byref(cfg)))
 
-    def serve_submit(self, cols: np.ndarray, rate_bits: int, cap_height: int) -> int:
-        a = np.ascontiguousarray(cols, dtype=np.uint64)
-        d = CommitDesc(a.ctypes.data, 0, a.shape[0], a.shape[1].bit_length() - 1, rate_bits, cap_height)
+    def serve_submit(self, cols, rate_bits: int, cap_height: int, borrow: bool = False) -> int:
+        """Submit one commit request.  ``cols``: uint64 numpy [c][n] (copied at
+        submit, or borrowed when ``borrow``: then it must be pinned and kept
+        alive until DONE), or an int64 CUDA tensor (borrowed)."""
+        if isinstance(cols, np.ndarray):
+            a = np.ascontiguousarray(cols, dtype=np.uint64)
+            kind = INPUT_HOST_BORROW if borrow else INPUT_HOST_COPY
+            ptr, c, n = a.ctypes.data, a.shape[0], a.shape[1]
+        else:
+            a = cols
+            kind = INPUT_DEVICE
+            ptr, c, n = cols.data_ptr(), cols.shape[0], cols.shape[1]
+        d = CommitDesc(ptr, kind, c, n.bit_length() - 1, rate_bits, cap_height)
         t = _u64()
         st = self.lib.v3c_serve_submit(self.h, ctypes.byref(d), ctypes.byref(t))
         if st == V3C_EAGAIN:
             return -1
         self._check(st)
+        if kind != INPUT_HOST_COPY:
+            self._borrowed[t.value] = a   # keep the borrowed buffer alive until release
         return t.value
 
     def serve_poll(self, ticket: int, cap_height: int | None = None):

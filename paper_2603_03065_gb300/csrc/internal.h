@@ -42,6 +42,13 @@ struct LdeJob {
     u32 a_cols;    // stage A: i2 columns per CTA (power of two, <= n2)
     u32 c_q;       // Z block: q values per block (power of two, <= M)
     u32 c_qc;      // stage C: q values per CTA (power of two, <= c_q)
+    u32 kcap;      // largest radix exponent of the in-register DFT passes (1..4)
+    u32 pad;
+};
+
+// Tile choice of one (log_n, rate_bits) shape, from the autotuner.
+struct TuneEntry {
+    u32 a_cols, c_q, c_qc, kcap, h_threads;
 };
 
 // One Merkle job: leaf hashes then tree levels up to the cap.
@@ -73,6 +80,8 @@ struct Tiles {
 Tiles default_tiles();
 // Per-job tile choice (stage A i2 columns, stage C / Z q-blocking) from the plan.
 void lde_job_tiles(LdeJob& j);
+// Applies an autotuned choice if it is valid for the job's plan.
+bool lde_job_apply_tune(LdeJob& j, const TuneEntry& t);
 
 // Stage launchers (ntt.cu / hash.cu).  Each enqueues one launch on `s`.
 cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s);

@@ -264,16 +264,16 @@ __device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const 
 
 // Largest radix exponent that keeps every thread busy, capped at 2^4 (32
 // registers of values per thread).
-__device__ __forceinline__ u32 pass_k(u32 B, u32 logL)
+__device__ __forceinline__ u32 pass_k(u32 B, u32 logL, u32 kcap)
 {
     u32 per = (B << logL) / blockDim.x;  // elements per thread
     u32 k = per >= 16 ? 4 : per >= 8 ? 3 : per >= 4 ? 2 : 1;
-    return k;
+    return max(1u, min(k, kcap));
 }
 
-__device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw)
+__device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, u32 kcap)
 {
-    const u32 kmax = pass_k(B, logL);
+    const u32 kmax = pass_k(B, logL, kcap);
     for (u32 s = 0; s < logL;) {
         u32 k = min(kmax, logL - s);
         switch (k) {
@@ -287,9 +287,9 @@ __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw)
 }
 
 // Stages s < first are skipped (the caller has already applied them).
-__device__ __forceinline__ void dft_dit(u64* a, u32 B, u32 logL, const u64* tw, u32 first)
+__device__ __forceinline__ void dft_dit(u64* a, u32 B, u32 logL, const u64* tw, u32 first, u32 kcap)
 {
-    const u32 kmax = pass_k(B, logL);
+    const u32 kmax = pass_k(B, logL, kcap);
     for (u32 s = first; s < logL;) {
         u32 k = min(kmax, logL - s);
         switch (k) {
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
             data[sw((u << l1) + i1)] = __ldcs(x + i20 + u + ((size_t)i1 << l2));
         }
         __syncthreads();
-        dft_dif(data, T2, l1, tw);
+        dft_dif(data, T2, l1, tw, J.kcap);
         u64* Y = J.Y + ((size_t)col << J.plan.log_n);
         for (u32 e = threadIdx.x; e < (T2 << l1); e += blockDim.x) {
             u32 u = e & (T2 - 1), t = e >> lT2;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
                             : J.x + ((size_t)col << J.plan.log_n);
         for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[sw(e)] = __ldcs(src + e);
         __syncthreads();
-        dft_dif(stage, 1, l2, twi);  // position t: n * a_{k1 + n1*bitrev(t)}
+        dft_dif(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
         const u64* sc = J.plan.scale + ((size_t)k1 << l2);
         // Scale by 7^j / n and spread for the zero-padded size-M transform.
         // In bit-reversed order over log M bits, coefficient k2 sits at
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
         __syncthreads();
         for (u32 e = threadIdx.x; e < M; e += blockDim.x) data[sw(e)] = stage[sw(e >> r)];
         __syncthreads();
-        dft_dit(data, 1, lM, twf, r);
+        dft_dit(data, 1, lM, twf, r, J.kcap);
         if (l1) {
             // Z is q-blocked: block q >> lQ holds [k1][q & (Q-1)], so that
             // stage C reads one contiguous run per column.
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
             data[sw(((w * Q + v) << l1) + k1)] = val;
         }
         __syncthreads();
-        dft_dif(data, kStageCCols * Q, l1, tw);
+        dft_dif(data, kStageCCols * Q, l1, tw, J.kcap);
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
@@ -528,6 +528,22 @@ void lde_job_tiles(LdeJob& j)
     // within 64 KiB, two CTAs per SM); the CTAs sharing a block run side by
     // side, so each 32-byte run is fetched from DRAM once.
     j.c_qc = std::min(j.c_q, std::max(1u, 2048u / n1));
+    j.kcap = 4;
+}
+
+bool lde_job_apply_tune(LdeJob& j, const TuneEntry& t)
+{
+    // A tuned choice is used only if it is valid for this job's plan.
+    u32 n1 = 1u << j.plan.log_n1, n2 = 1u << j.plan.log_n2, M = 1u << j.plan.log_M;
+    auto pow2 = [](u32 x) { return x && !(x & (x - 1)); };
+    if (!pow2(t.a_cols) || !pow2(t.c_q) || !pow2(t.c_qc) || t.kcap < 1 || t.kcap > 4) return false;
+    if (t.a_cols > n2 || t.c_q > M || t.c_qc > t.c_q) return false;
+    if ((size_t)t.a_cols * n1 > 16384 || (size_t)kStageCCols * t.c_qc * n1 > 16384) return false;
+    j.a_cols = t.a_cols;
+    j.c_q = t.c_q;
+    j.c_qc = t.c_qc;
+    j.kcap = t.kcap;
+    return true;
 }
 
 // ---------------------------------------------------------------- launchers

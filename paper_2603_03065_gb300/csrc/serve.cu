@@ -80,15 +80,22 @@ bool admit_and_launch(Server* S)
     u64 budget = cfg.hbm_budget_bytes;
     u64 resident = ctx_resident(S->ctx);
     std::vector<u64> batch;
-    size_t scratch = 0, staged = 0;
+    size_t scratch = 0, staged = 0, copied = 0;
     u64 reserve = 0;
     u32 max_batch = S->cfg.max_batch ? S->cfg.max_batch : 32;
+    const u64 slot_cap = S->cfg.slot_scratch_bytes ? S->cfg.slot_scratch_bytes : (16ull << 30);
     while (!S->queue.empty() && batch.size() < max_batch) {
         Request& r = S->reqs[S->queue.front()];
         if (resident + S->reserved + reserve + r.footprint > budget) break;  // FIFO: wait for memory
+        size_t sw = lde_scratch_words_s(r.desc.c, r.desc.log_n, r.desc.rate_bits);
+        size_t iw = r.desc.on_device == V3C_INPUT_DEVICE ? 0 : (size_t)r.desc.c << r.desc.log_n;
+        // A pass takes at least one request; more only while its scratch
+        // and staged inputs stay within the slot cap.
+        if (!batch.empty() && (scratch + staged + sw + iw) * 8 > slot_cap) break;
         reserve += r.footprint;
-        scratch += lde_scratch_words_s(r.desc.c, r.desc.log_n, r.desc.rate_bits);
-        if (!r.desc.on_device) staged += (size_t)r.desc.c << r.desc.log_n;
+        scratch += sw;
+        staged += iw;
+        if (r.desc.on_device == V3C_INPUT_HOST_COPY) copied += iw;
         batch.push_back(r.ticket);
         S->queue.pop_front();
     }
@@ -108,15 +115,15 @@ bool admit_and_launch(Server* S)
             slot->arena_words = need;
         }
     }
-    if (!st && staged > slot->pinned_words) {
+    if (!st && copied > slot->pinned_words) {
         if (slot->pinned) cudaFreeHost(slot->pinned);
         slot->pinned = nullptr;
         slot->pinned_words = 0;
-        if (cudaMallocHost(&slot->pinned, staged * 8) != cudaSuccess) {
+        if (cudaMallocHost(&slot->pinned, copied * 8) != cudaSuccess) {
             cudaGetLastError();
             st = V3C_ENOMEM;
         } else {
-            slot->pinned_words = staged;
+            slot->pinned_words = copied;
         }
     }
     std::vector<v3c_commit_desc> descs;
@@ -126,12 +133,14 @@ bool admit_and_launch(Server* S)
         r.state = V3C_REQ_ADMITTED;
         r.times.t_admit = t;
         v3c_commit_desc d = r.desc;
-        if (!st && !d.on_device) {
+        if (!st && d.on_device == V3C_INPUT_HOST_COPY) {
+            // Copied at submit: stage through the slot's pinned buffer.
             size_t w = (size_t)d.c << d.log_n;
             memcpy(slot->pinned + poff, r.host_copy.data(), w * 8);
             d.cols = slot->pinned + poff;
             poff += w;
         }
+        if (d.on_device == V3C_INPUT_HOST_BORROW) d.on_device = V3C_INPUT_HOST_COPY;  // caller's pinned memory
         descs.push_back(d);
     }
     if (!st) {
@@ -233,7 +242,9 @@ v3c_status v3c_serve_submit(v3c_ctx* ctx, const v3c_commit_desc* desc, uint64_t*
         return V3C_EINVAL;
     u64 fp = v3c_commit_footprint(d.c, d.log_n, d.rate_bits, d.cap_height);
     if (fp > ctx_config(ctx).hbm_budget_bytes) return V3C_ENOMEM;
-    if ((S->cfg.flags & V3C_FLAG_VALIDATE) && !d.on_device) {
+    if (d.on_device != V3C_INPUT_HOST_COPY && d.on_device != V3C_INPUT_DEVICE && d.on_device != V3C_INPUT_HOST_BORROW)
+        return V3C_EINVAL;
+    if ((S->cfg.flags & V3C_FLAG_VALIDATE) && d.on_device != V3C_INPUT_DEVICE) {
         size_t w = (size_t)d.c << d.log_n;
         for (size_t i = 0; i < w; i++)
             if (d.cols[i] >= 0xFFFFFFFF00000001ull) return V3C_EINVAL;
@@ -241,7 +252,7 @@ v3c_status v3c_serve_submit(v3c_ctx* ctx, const v3c_commit_desc* desc, uint64_t*
     Request r;
     r.desc = d;
     r.footprint = fp;
-    if (!d.on_device) r.host_copy.assign(d.cols, d.cols + ((size_t)d.c << d.log_n));
+    if (d.on_device == V3C_INPUT_HOST_COPY) r.host_copy.assign(d.cols, d.cols + ((size_t)d.c << d.log_n));
     r.times.t_submit = now_s();
     std::lock_guard<std::mutex> g(S->mu);
     if (S->stop || S->crashed) return V3C_ECANCELED;

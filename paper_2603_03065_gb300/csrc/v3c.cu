@@ -68,6 +68,21 @@ struct PlanEntry {
     u64* mem = nullptr;
 };
 
+// One captured instance of a batch signature (see launch_batch_graph).
+struct GraphInst {
+    cudaGraphExec_t exec = nullptr;
+    void* h_blob = nullptr;
+    void* d_blob = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+    uint32_t kernels = 0;
+};
+struct GraphSet {
+    std::vector<GraphInst> inst;
+    uint32_t next = 0;
+};
+constexpr uint32_t kGraphRing = 3;
+
 struct UploadSlot {
     void* h = nullptr;
     void* d = nullptr;
@@ -112,6 +127,11 @@ struct v3c_ctx {
     u32* d_flag = nullptr;
     serve::Server* server = nullptr;
     cudaStream_t release_stream = nullptr;  // orders frees of resident objects
+    // CUDA graphs of batch signatures, and the autotuner's per-shape choices
+    std::unordered_map<std::string, GraphSet> graphs;
+    cudaStream_t capture_stream = nullptr;
+    std::atomic<u64> graph_replays{0};
+    std::map<std::pair<u32, u32>, TuneEntry> tuned;
     // per-stage timing (V3C_FLAG_TIMING)
     std::mutex tmu;
     struct Pending {
@@ -300,6 +320,7 @@ struct Batch {
         }
     }
     std::vector<std::pair<u32, u32>> mgroups;  // (first level, levels) of each Merkle launch
+    u32 h_threads = 0;                          // leaf-hash CTA size (0 = context default)
 };
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -325,7 +346,7 @@ struct StageTimer {
     cudaEvent_t a = nullptr;
     StageTimer(v3c_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str)
     {
-        if (ctx->cfg.flags & V3C_FLAG_TIMING) {
+        if ((ctx->cfg.flags & V3C_FLAG_TIMING) && st >= 0) {
             a = pool_event(ctx);
             if (a) cudaEventRecord(a, s);
         }
@@ -342,11 +363,10 @@ struct StageTimer {
     }
 };
 
-v3c_status launch_batch(v3c_ctx* ctx, Batch& b, cudaStream_t s)
+// Job table + stage item lists of a batch, packed into one upload.
+// Layout: LdeJob[], TreeJob[], fa, fb, fc, fl, fm[...], 16-byte aligned parts.
+static void build_blob(Batch& b, std::vector<char>& blob, std::vector<size_t>& off)
 {
-    const Tiles& t = ctx->tiles;
-    b.finalize(t);
-    // Blob layout: LdeJob[], TreeJob[], fa, fb, fc, fl, fm[...]
     std::vector<std::pair<const void*, size_t>> parts;
     parts.push_back({b.lde.data(), b.lde.size() * sizeof(LdeJob)});
     parts.push_back({b.tree.data(), b.tree.size() * sizeof(TreeJob)});
@@ -355,20 +375,22 @@ v3c_status launch_batch(v3c_ctx* ctx, Batch& b, cudaStream_t s)
     parts.push_back({b.fc.data(), b.fc.size() * 4});
     parts.push_back({b.fl.data(), b.fl.size() * 4});
     for (auto& f : b.fm) parts.push_back({f.data(), f.size() * 4});
-    std::vector<size_t> off;
+    off.clear();
     size_t total = 0;
     for (auto& p : parts) {
         off.push_back(total);
         total = align16(total + p.second);
     }
-    std::vector<char> blob(total, 0);
+    blob.assign(total, 0);
     for (size_t i = 0; i < parts.size(); i++)
         if (parts[i].second) memcpy(blob.data() + off[i], parts[i].first, parts[i].second);
-    void* d = nullptr;
-    u32 slot = 0;
-    v3c_status st = upload(ctx, blob.data(), total, s, &d, &slot);
-    if (st) return st;
-    char* dc = (char*)d;
+}
+
+// Enqueues every stage of a finalised batch whose blob sits at device
+// address dc.  timed = record per-stage events (not inside graph capture).
+static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, char* dc,
+                                 const std::vector<size_t>& off, cudaStream_t s, bool timed)
+{
     const LdeJob* dl = (const LdeJob*)(dc + off[0]);
     const TreeJob* dt = (const TreeJob*)(dc + off[1]);
     auto list = [&](size_t part, const std::vector<u32>& f, u32 njobs) {
@@ -379,45 +401,136 @@ v3c_status launch_batch(v3c_ctx* ctx, Batch& b, cudaStream_t s)
         return l;
     };
     u32 nl = (u32)b.lde.size(), nt = (u32)b.tree.size();
+    auto stage = [&](int id, cudaError_t (*fn)(const Batch&, const Tiles&, StageList, const LdeJob*,
+                                               const TreeJob*, size_t, cudaStream_t),
+                     StageList l, size_t g) -> v3c_status {
+        if (!l.total) return V3C_OK;
+        StageTimer tm(ctx, timed ? id : -1, s);
+        CK(fn(b, t, l, dl, dt, g, s));
+        tm.done();
+        ctx->launches++;
+        return V3C_OK;
+    };
+    v3c_status st;
     if (nl) {
-        StageList la = list(2, b.fa, nl), lb = list(3, b.fb, nl), lc = list(4, b.fc, nl);
-        if (la.total) {
-            StageTimer tm(ctx, 0, s);
-            CK(launch_stage_a(dl, la, b.smem_a, t, 0, s));
-            tm.done();
-            ctx->launches++;
-        }
-        if (lb.total) {
-            StageTimer tm(ctx, 1, s);
-            CK(launch_stage_b(dl, lb, b.smem_b, t, 0, s));
-            tm.done();
-            ctx->launches++;
-        }
-        if (lc.total) {
-            StageTimer tm(ctx, 2, s);
-            CK(launch_stage_c(dl, lc, b.smem_c, t, 0, s));
-            tm.done();
-            ctx->launches++;
-        }
+        st = stage(0, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
+                         cudaStream_t s) { return launch_stage_a(dl, l, b.smem_a, t, 0, s); },
+                   list(2, b.fa, nl), 0);
+        if (st) return st;
+        st = stage(1, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
+                         cudaStream_t s) { return launch_stage_b(dl, l, b.smem_b, t, 0, s); },
+                   list(3, b.fb, nl), 0);
+        if (st) return st;
+        st = stage(2, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
+                         cudaStream_t s) { return launch_stage_c(dl, l, b.smem_c, t, 0, s); },
+                   list(4, b.fc, nl), 0);
+        if (st) return st;
     }
     if (nt) {
-        StageList ll = list(5, b.fl, nt);
-        if (ll.total) {
-            StageTimer tm(ctx, 3, s);
-            CK(launch_leaf_hash(dt, ll, t, 0, s));
-            tm.done();
-            ctx->launches++;
-        }
+        st = stage(3, [](const Batch&, const Tiles& t, StageList l, const LdeJob*, const TreeJob* dt, size_t,
+                         cudaStream_t s) { return launch_leaf_hash(dt, l, t, 0, s); },
+                   list(5, b.fl, nt), 0);
+        if (st) return st;
         for (size_t g = 0; g < b.fm.size(); g++) {
-            StageList lm = list(6 + g, b.fm[g], nt);
-            if (!lm.total) continue;
-            StageTimer tm(ctx, 4, s);
-            CK(launch_merkle(dt, lm, b.mgroups[g].first, b.mgroups[g].second, t, 0, s));
-            tm.done();
-            ctx->launches++;
+            st = stage(4, [](const Batch& b, const Tiles& t, StageList l, const LdeJob*, const TreeJob* dt,
+                             size_t g, cudaStream_t s) {
+                return launch_merkle(dt, l, b.mgroups[g].first, b.mgroups[g].second, t, 0, s);
+            }, list(6 + g, b.fm[g], nt), g);
+            if (st) return st;
         }
     }
+    return V3C_OK;
+}
+
+// Direct path: upload the blob through the ring and launch every stage.
+v3c_status launch_batch(v3c_ctx* ctx, Batch& b, cudaStream_t s)
+{
+    Tiles t = ctx->tiles;
+    if (b.h_threads) t.h_threads = b.h_threads;
+    b.finalize(t);
+    std::vector<char> blob;
+    std::vector<size_t> off;
+    build_blob(b, blob, off);
+    void* d = nullptr;
+    u32 slot = 0;
+    v3c_status st = upload(ctx, blob.data(), blob.size(), s, &d, &slot);
+    if (st) return st;
+    st = enqueue_stages(ctx, b, t, (char*)d, off, s, true);
+    if (st) return st;
     return upload_done(ctx, slot, s);
+}
+
+// Graph path: every distinct batch signature (shapes, tiles, launch
+// configuration) is captured once as [job-table copy, stage launches] on a
+// ring of kGraphRing instances, each with its own pinned host and device
+// table.  A call rewrites the table of the next instance (after that
+// instance's previous replay has finished) and replays the graph.
+static std::string batch_signature(const Batch& b, const Tiles& t)
+{
+    std::string k;
+    char buf[96];
+    snprintf(buf, sizeof buf, "t%u.%u.%u.%u.%u|", t.a_threads, t.b_threads, t.c_threads, b.h_threads ? b.h_threads : t.h_threads,
+             t.m_threads);
+    k += buf;
+    for (auto& j : b.lde) {
+        snprintf(buf, sizeof buf, "L%u.%u.%u.%u.%u.%u.%u.%u.%u|", j.c, j.ld, j.plan.log_n, j.plan.r, j.vec_ok, j.a_cols,
+                 j.c_q, j.c_qc, j.kcap);
+        k += buf;
+    }
+    for (auto& j : b.tree) {
+        snprintf(buf, sizeof buf, "T%u.%u.%u.%u.%u|", j.ld, j.width, j.log_N, j.h, j.vec_ok);
+        k += buf;
+    }
+    return k;
+}
+
+v3c_status launch_batch_graph(v3c_ctx* ctx, Batch& b, cudaStream_t s)
+{
+    Tiles t = ctx->tiles;
+    if (b.h_threads) t.h_threads = b.h_threads;
+    b.finalize(t);
+    std::vector<char> blob;
+    std::vector<size_t> off;
+    build_blob(b, blob, off);
+    std::string key = batch_signature(b, t);
+    GraphSet& gs = ctx->graphs[key];
+    if (gs.inst.empty()) gs.inst.resize(kGraphRing);
+    GraphInst& gi = gs.inst[gs.next++ % kGraphRing];
+    if (!gi.exec) {
+        gi.bytes = blob.size();
+        CK(cudaMallocHost(&gi.h_blob, gi.bytes));
+        CK(cudaMalloc(&gi.d_blob, gi.bytes));
+        CK(cudaEventCreateWithFlags(&gi.done, cudaEventDisableTiming));
+        if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = ctx->capture_stream;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        cudaError_t e = cudaMemcpyAsync(gi.d_blob, gi.h_blob, gi.bytes, cudaMemcpyHostToDevice, cs);
+        u64 before = ctx->launches.load();
+        v3c_status st = e == cudaSuccess ? enqueue_stages(ctx, b, t, (char*)gi.d_blob, off, cs, false) : V3C_ECUDA;
+        ctx->launches = before;  // captured launches are counted when replayed
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (st || e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st ? st : fail(ctx, V3C_ECUDA, "graph capture failed: %s", cudaGetErrorString(e ? e : e2));
+        }
+        size_t nnodes = 0;
+        cudaGraphGetNodes(g, nullptr, &nnodes);
+        gi.kernels = (u32)(nnodes ? nnodes - 1 : 0);
+        e = cudaGraphInstantiate(&gi.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(ctx, V3C_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    if (blob.size() != gi.bytes) return fail(ctx, V3C_ECUDA, "graph table size mismatch");
+    CK(cudaEventSynchronize(gi.done));  // the previous replay of this instance read h_blob/d_blob
+    memcpy(gi.h_blob, blob.data(), gi.bytes);
+    CK(cudaStreamWaitEvent(s, gi.done, 0));
+    CK(cudaGraphLaunch(gi.exec, s));
+    CK(cudaEventRecord(gi.done, s));
+    ctx->launches += gi.kernels;
+    ctx->graph_replays++;
+    return V3C_OK;
 }
 
 static bool shape_ok(u32 c, u32 log_n, u32 r)
@@ -450,7 +563,142 @@ static v3c_status make_lde_job(v3c_ctx* ctx, const u64* x, u32 c, u32 log_n, u32
         j.Z = scratch + ((size_t)c << log_n);
     }
     job_tiles(j);
+    auto it = ctx->tuned.find(std::make_pair(log_n, r));
+    if (it != ctx->tuned.end()) lde_job_apply_tune(j, it->second);
     *out = j;
+    return V3C_OK;
+}
+
+static TreeJob make_tree_job(const u64* rows, u32 ld, u32 width, u32 log_N, u32 h, u64* tree, u64* cap);
+
+// Autotuner.  For one (log_n, rate_bits) shape it times candidate tile
+// choices on a synthetic 32-column problem of that shape, once, and keeps
+// the fastest.  The candidates are the in-register radix cap, the Z
+// blocking / stage-C q values, the stage-A column tile, and the leaf-hash
+// CTA size (hash-lane mapping: one state per thread, 64 or 128 threads per
+// CTA).  Coordinate descent in that order, best of 2 runs per candidate
+// after a warm-up.  Synchronous; caller holds ctx->mu.
+static v3c_status autotune_shape(v3c_ctx* ctx, u32 log_n, u32 r)
+{
+    auto key = std::make_pair(log_n, r);
+    if (ctx->tuned.count(key)) return V3C_OK;
+    const u32 c = 32, ld = 32;
+    const size_t n = (size_t)1 << log_n, N = n << r;
+    const size_t sw = lde_scratch_words(c, log_n, r);
+    cudaStream_t ts = nullptr;
+    u64 *x = nullptr, *lde = nullptr, *scr = nullptr, *leaves = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    v3c_status st = V3C_OK;
+    TuneEntry best{};
+    auto cleanup = [&]() {
+        if (ts) cudaStreamSynchronize(ts);
+        cudaFree(x);
+        cudaFree(lde);
+        cudaFree(scr);
+        cudaFree(leaves);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (ts) cudaStreamDestroy(ts);
+    };
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && !st) st = fail(ctx, V3C_ECUDA, "autotune: %s", cudaGetErrorString(e));
+        return e == cudaSuccess;
+    };
+    if (!ck(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking)) || !ck(cudaMalloc(&x, c * n * 8)) ||
+        !ck(cudaMalloc(&lde, N * ld * 8)) || (sw && !ck(cudaMalloc(&scr, sw * 8))) ||
+        !ck(cudaMalloc(&leaves, N * 32)) || !ck(cudaEventCreate(&e0)) || !ck(cudaEventCreate(&e1)) ||
+        !ck(cudaMemsetAsync(x, 0x11, c * n * 8, ts))) {  // 0x1111... is a canonical field element
+        cleanup();
+        return st;
+    }
+    LdeJob base;
+    memset(&base, 0, sizeof base);
+    st = get_plan(ctx, log_n, r, ts, &base.plan);
+    if (st) {
+        cleanup();
+        return st;
+    }
+    base.x = x;
+    base.c = c;
+    base.ld = ld;
+    base.lde = lde;
+    base.vec_ok = 1;
+    if (base.plan.log_n1) {
+        base.Y = scr;
+        base.Z = scr + (size_t)c * n;
+    }
+    lde_job_tiles(base);
+    const u32 saved_flags = ctx->cfg.flags;
+    ctx->cfg.flags &= ~V3C_FLAG_TIMING;
+    auto time_lde = [&](const TuneEntry& t, float* ms) -> bool {
+        LdeJob j = base;
+        if (!lde_job_apply_tune(j, t)) return false;
+        float bestms = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            Batch b;
+            b.lde.push_back(j);
+            if (!ck(cudaEventRecord(e0, ts))) return false;
+            if (launch_batch(ctx, b, ts)) return false;
+            if (!ck(cudaEventRecord(e1, ts)) || !ck(cudaEventSynchronize(e1))) return false;
+            float m = 0;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (rep) bestms = std::min(bestms, m);
+        }
+        *ms = bestms;
+        return true;
+    };
+    best = TuneEntry{base.a_cols, base.c_q, base.c_qc, base.kcap, ctx->tiles.h_threads};
+    float best_ms = 1e30f;
+    time_lde(best, &best_ms);
+    auto consider = [&](TuneEntry t) {
+        float m;
+        if (!st && time_lde(t, &m) && m < best_ms) {
+            best_ms = m;
+            best = t;
+        }
+    };
+    for (u32 k : {3u, 4u}) {
+        TuneEntry t = best;
+        t.kcap = k;
+        consider(t);
+    }
+    const u32 qz[][2] = {{2, 2}, {4, 2}, {4, 4}, {8, 2}, {8, 4}, {8, 8}, {1, 1}};
+    for (auto& q : qz) {
+        TuneEntry t = best;
+        t.c_q = q[0];
+        t.c_qc = q[1];
+        consider(t);
+    }
+    for (u32 a : {2u, 4u, 8u, 16u}) {
+        TuneEntry t = best;
+        t.a_cols = a;
+        consider(t);
+    }
+    // Leaf hash CTA size on the trial LDE (cap = leaves, no tree levels).
+    float leaf_best = 1e30f;
+    for (u32 ht : {64u, 128u}) {
+        if (st) break;
+        float bestms = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            Batch b;
+            b.h_threads = ht;
+            b.tree.push_back(make_tree_job(lde, ld, c, log_n + r, log_n + r, nullptr, leaves));
+            if (!ck(cudaEventRecord(e0, ts)) || launch_batch(ctx, b, ts) || !ck(cudaEventRecord(e1, ts)) ||
+                !ck(cudaEventSynchronize(e1)))
+                break;
+            float m = 0;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (rep) bestms = std::min(bestms, m);
+        }
+        if (bestms < leaf_best) {
+            leaf_best = bestms;
+            best.h_threads = ht;
+        }
+    }
+    ctx->cfg.flags = saved_flags;
+    cleanup();
+    if (st) return st;
+    ctx->tuned[key] = best;
     return V3C_OK;
 }
 
@@ -562,6 +810,14 @@ v3c_status v3c_destroy(v3c_ctx* ctx)
     if (ctx->arena.ev) cudaEventDestroy(ctx->arena.ev);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
     if (ctx->release_stream) cudaStreamDestroy(ctx->release_stream);
+    for (auto& kv : ctx->graphs)
+        for (auto& gi : kv.second.inst) {
+            if (gi.exec) cudaGraphExecDestroy(gi.exec);
+            if (gi.h_blob) cudaFreeHost(gi.h_blob);
+            if (gi.d_blob) cudaFree(gi.d_blob);
+            if (gi.done) cudaEventDestroy(gi.done);
+        }
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
     return V3C_OK;
 }
@@ -646,11 +902,23 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
                         d.rate_bits, d.cap_height);
         need += v3c_commit_footprint(d.c, d.log_n, d.rate_bits, d.cap_height);
         scratch += lde_scratch_words(d.c, d.log_n, d.rate_bits);
-        if (!d.on_device) staged += (size_t)d.c << d.log_n;
+        if (d.on_device != V3C_INPUT_DEVICE) staged += (size_t)d.c << d.log_n;
     }
     if (!arena_override && ctx->resident + need > ctx->cfg.hbm_budget_bytes)
         return fail(ctx, V3C_ENOMEM, "v3c_commit: %zu bytes requested, %zu resident, budget %llu", need,
                     ctx->resident, (unsigned long long)ctx->cfg.hbm_budget_bytes);
+    u32 h_threads = 0, biggest = 0;
+    if (ctx->cfg.autotune) {
+        for (u32 i = 0; i < nb; i++) {
+            v3c_status st = autotune_shape(ctx, descs[i].log_n, descs[i].rate_bits);
+            if (st) return st;
+            u32 logN = descs[i].log_n + descs[i].rate_bits;
+            if (logN >= biggest) {
+                biggest = logN;
+                h_threads = ctx->tuned[std::make_pair(descs[i].log_n, descs[i].rate_bits)].h_threads;
+            }
+        }
+    }
     u64* arena = nullptr;
     size_t arena_need = scratch + staged;
     v3c_status st;
@@ -701,7 +969,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         Object& o = objs[i];
         const u64* x = d.cols;
         size_t n = (size_t)1 << d.log_n;
-        if (!d.on_device) {
+        if (d.on_device != V3C_INPUT_DEVICE) {
             u64* dst = arena + aoff;
             aoff += d.c * n;
             cudaError_t e = cudaMemcpyAsync(dst, d.cols, d.c * n * 8, cudaMemcpyHostToDevice, s);
@@ -742,7 +1010,11 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
                                     : fail(ctx, V3C_EINVAL, "v3c_commit: input not canonical (>= p)");
         }
     }
-    st = launch_batch(ctx, b, s);
+    b.h_threads = h_threads;
+    // Replay a captured graph of this batch signature unless graphs are off
+    // or per-stage timing (events around each launch) is requested.
+    if (ctx->cfg.flags & (V3C_FLAG_NO_GRAPH | V3C_FLAG_TIMING)) st = launch_batch(ctx, b, s);
+    else st = launch_batch_graph(ctx, b, s);
     if (st) {
         rollback(nb);
         return st;

@@ -22,6 +22,7 @@ padded domain G_B = 2^ceil(log2 G) of Sec. 2.1 and Table zkivfpq-bench):
 """
 from __future__ import annotations
 
+import itertools
 import math
 from dataclasses import dataclass
 
@@ -95,12 +96,7 @@ def column(seed: int, batch: int, col: int, n: int, kind: int) -> np.ndarray:
         return draws(st, 0, n) & np.uint64(1)
     if kind == RUNNING_PRODUCT:
         u = _filtered(st, n, lambda d: (d < np.uint64(P)) & (d != np.uint64(0))).tolist()
-        out = [0] * n
-        r = 1
-        for i, ui in enumerate(u):
-            r = (r * ui) % P if i else ui
-            out[i] = r
-        return np.array(out, dtype=np.uint64)
+        return np.array(list(itertools.accumulate(u, lambda r, ui: (r * ui) % P)), dtype=np.uint64)
     raise ValueError(f"unknown column kind {kind}")
 
 

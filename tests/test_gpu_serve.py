@@ -111,3 +111,25 @@ def test_admission_waits_for_budget_and_stop_cancels(v3c):
                 ctx.release(t)
             except v3c.V3CError:
                 pass
+
+
+def test_borrowed_pinned_and_device_inputs(v3c):
+    import torch
+
+    shapes = [synth.Shape(c=24, log_n=12, rate_bits=2, cap_height=4, seed=8, batch=b) for b in range(4)]
+    xs = [s.inputs() for s in shapes]
+    pinned = [torch.from_numpy(x.view(np.int64)).pin_memory() for x in xs]
+    with v3c.Context(0) as ctx:
+        ctx.serve_start(max_batch=3, slot_scratch_bytes=1 << 20)   # tiny cap: one request per pass
+        tickets, caps = [], {}
+        for i, (s, x, p) in enumerate(zip(shapes, xs, pinned)):
+            src = p.numpy().view(np.uint64) if i % 2 == 0 else v3c.to_device_u64(x)
+            t = ctx.serve_submit(src, s.rate_bits, s.cap_height, borrow=True)
+            tickets.append(t)
+            caps[t] = s.cap_height
+        done = wait_done(ctx, v3c, tickets, caps)
+        for t, s, x in zip(tickets, shapes, xs):
+            _, _, want_cap = oracle.commit(x, s.rate_bits, s.cap_height)
+            assert np.array_equal(done[t][0], want_cap)
+            ctx.release(t)
+        ctx.serve_stop()
