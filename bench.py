@@ -65,6 +65,25 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def shard_workload(s: "synth.Shape", rank: int) -> "synth.Shape":
+    """Rank r commits its own independent batch of the same shape (batch
+    index r of the same seed): weak scaling with no data-path collective."""
+    return synth.Shape(c=s.c, log_n=s.log_n, rate_bits=s.rate_bits, cap_height=s.cap_height, seed=s.seed,
+                       mix=s.mix, batch=rank)
+
+
+def max_over_ranks(value: float, device: str = "cuda") -> float:
+    """The slowest rank's time (the only collective: timing, not data)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -179,9 +198,7 @@ def run_v3c(args):
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
-    s = WORKLOADS[args.workload]
-    s = synth.Shape(c=s.c, log_n=s.log_n, rate_bits=s.rate_bits, cap_height=s.cap_height, seed=s.seed,
-                    mix=s.mix, batch=rank)
+    s = shard_workload(WORKLOADS[args.workload], rank)
     x = s.inputs()
     ctx = v3c.Context(local_rank, flags=v3c.FLAG_TIMING)
     stream = torch.cuda.current_stream()
@@ -219,12 +236,7 @@ def run_v3c(args):
     ms = e0.elapsed_time(e1) / args.steps
     launches = ctx.kernel_launches() - l0
     stats = ctx.stage_stats(reset=True)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
 
     value = world * s.lde_elems() / (ms * 1e-3) / 1e9
 
@@ -245,13 +257,7 @@ def run_v3c(args):
     for _ in range(args.steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
     e2e_value = world * s.lde_elems() / e2e_s / 1e9
 
     # roofline of the dominant kernel (leaf hash), timed by events on its stream
@@ -379,12 +385,20 @@ def run_serving(args):
     def src(i, req):
         return pool[(req.shape.log_n, req.shape.c, i % 2)]
 
-    def summarize(lat, t_first, t_last, elems):
+    warm = 5.0 if args.duration > 5.0 else 0.0
+
+    def summarize(lat, done):
+        """lat: latencies of requests that arrived after the warm-up; done:
+        (completion time since the trace start, elements) of every request.
+        Throughput counts the elements completed after the warm-up over the
+        time from the end of the warm-up to the last completion."""
         lat = sorted(lat)
         q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None  # noqa: E731
+        t_end = max((t for t, _ in done), default=warm)
+        elems = sum(e for t, e in done if t >= warm)
         return {"requests": len(lat), "p50_ms": q(0.50) * 1e3 if lat else None,
                 "p99_ms": q(0.99) * 1e3 if lat else None,
-                "Gelem/s": elems / max(t_last - t_first, 1e-9) / 1e9}
+                "Gelem/s": elems / max(t_end - warm, 1e-9) / 1e9}
 
     ctx = v3c.Context(0, hbm_budget_bytes=150 << 30, max_inflight=args.inflight)
     # warm plans and graphs for the three shapes
@@ -394,8 +408,9 @@ def run_serving(args):
     torch.cuda.synchronize()
     ctx.serve_start(max_batch=args.max_batch)
     pending = {}
-    lat, done_elems, t_first, t_last = [], 0, None, None
+    lat, done = [], []
     t0 = time.perf_counter()
+    t0_lib = None   # the library's clock at the trace start
     i = 0
     while i < len(trace) or pending:
         now = time.perf_counter() - t0
@@ -414,23 +429,22 @@ def run_serving(args):
             if st != v3c.V3C_OK:
                 raise RuntimeError(f"request failed with status {st}")
             ctx.release(tk)
-            if req.t_arrive >= 5.0 or args.duration <= 5.0:
+            if t0_lib is None:
+                t0_lib = times[0] - req.t_arrive
+            done.append((times[3] - t0_lib, req.shape.lde_elems()))
+            if req.t_arrive >= warm:
                 lat.append(times[3] - times[0])
-                done_elems += req.shape.lde_elems()
-                t_first = times[0] if t_first is None else min(t_first, times[0])
-                t_last = times[3] if t_last is None else max(t_last, times[3])
         time.sleep(0.0002)
     wall = time.perf_counter() - t0
     ctx.serve_stop()
-    served = summarize(lat, t_first or 0, t_last or 1, done_elems)
+    served = summarize(lat, done)
     served["wall_s"] = wall
 
     # Serial path: one commit at a time, in arrival order, from the same pinned
     # inputs; latency = done - arrival.
     stream = torch.cuda.current_stream()
-    lat_s, elems_s = [], 0
+    lat_s, done_s = [], []
     t0 = time.perf_counter()
-    t_first_s = None
     for k, req in enumerate(trace):
         now = time.perf_counter() - t0
         if req.t_arrive > now:
@@ -439,11 +453,10 @@ def run_serving(args):
         ctx.cap(cid)
         ctx.release(cid)
         t_done = time.perf_counter() - t0
-        if req.t_arrive >= 5.0 or args.duration <= 5.0:
+        done_s.append((t_done, req.shape.lde_elems()))
+        if req.t_arrive >= warm:
             lat_s.append(t_done - req.t_arrive)
-            elems_s += req.shape.lde_elems()
-            t_first_s = req.t_arrive if t_first_s is None else t_first_s
-    serial = summarize(lat_s, t_first_s or 0, time.perf_counter() - t0, elems_s)
+    serial = summarize(lat_s, done_s)
     ctx.close()
     mean_elems = sum(r.shape.lde_elems() for r in trace) / max(len(trace), 1)
     out = {"metric": METRIC, "unit": "Gelem/s", "value": served["Gelem/s"], "higher_is_better": True,

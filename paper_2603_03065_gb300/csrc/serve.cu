@@ -147,7 +147,7 @@ bool admit_and_launch(Server* S)
         std::vector<u64> ids(batch.size());
         std::lock_guard<std::mutex> g(ctx_mutex(S->ctx));
         st = commit_locked(S->ctx, descs.data(), (u32)descs.size(), ids.data(), slot->stream, slot->arena,
-                           slot->arena_words, batch.data());
+                           slot->arena_words, batch.data(), /*allow_graph=*/false);  // mixes rarely repeat
         if (!st && cudaEventRecord(slot->done, slot->stream) != cudaSuccess) st = V3C_ECUDA;
     }
     double t2 = now_s();

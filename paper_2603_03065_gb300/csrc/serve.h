@@ -58,7 +58,8 @@ struct Server {
 
 namespace detail {
 v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64* ids, cudaStream_t s,
-                         u64* arena_override, size_t arena_words, const u64* preassigned_ids);
+                         u64* arena_override, size_t arena_words, const u64* preassigned_ids,
+                         bool allow_graph = true);
 v3c_status lock_and_select(v3c_ctx* ctx);
 std::mutex& ctx_mutex(v3c_ctx* ctx);
 u64 ctx_next_id(v3c_ctx* ctx);

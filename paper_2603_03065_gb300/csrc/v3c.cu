@@ -82,6 +82,7 @@ struct GraphSet {
     uint32_t next = 0;
 };
 constexpr uint32_t kGraphRing = 3;
+constexpr size_t kMaxGraphSets = 64;
 
 struct UploadSlot {
     void* h = nullptr;
@@ -129,6 +130,7 @@ struct v3c_ctx {
     cudaStream_t release_stream = nullptr;  // orders frees of resident objects
     // CUDA graphs of batch signatures, and the autotuner's per-shape choices
     std::unordered_map<std::string, GraphSet> graphs;
+    std::unordered_map<std::string, int> graph_seen;
     cudaStream_t capture_stream = nullptr;
     std::atomic<u64> graph_replays{0};
     std::map<std::pair<u32, u32>, TuneEntry> tuned;
@@ -489,10 +491,16 @@ v3c_status launch_batch_graph(v3c_ctx* ctx, Batch& b, cudaStream_t s)
     Tiles t = ctx->tiles;
     if (b.h_threads) t.h_threads = b.h_threads;
     b.finalize(t);
+    std::string key = batch_signature(b, t);
+    // A signature is captured on its second appearance (one-off batch mixes
+    // launch directly), and at most kMaxGraphSets signatures are kept.
+    auto seen = ctx->graph_seen.find(key);
+    bool repeat = seen != ctx->graph_seen.end();
+    if (!repeat && ctx->graph_seen.size() < 4 * kMaxGraphSets) ctx->graph_seen.emplace(key, 1);
+    if (!repeat || (!ctx->graphs.count(key) && ctx->graphs.size() >= kMaxGraphSets)) return launch_batch(ctx, b, s);
     std::vector<char> blob;
     std::vector<size_t> off;
     build_blob(b, blob, off);
-    std::string key = batch_signature(b, t);
     GraphSet& gs = ctx->graphs[key];
     if (gs.inst.empty()) gs.inst.resize(kGraphRing);
     GraphInst& gi = gs.inst[gs.next++ % kGraphRing];
@@ -775,6 +783,16 @@ v3c_status v3c_create(int device, const v3c_config* cfg, v3c_ctx** out)
         cudaMemGetInfo(&fr, &tot);
         ctx->cfg.hbm_budget_bytes = (uint64_t)(fr * 0.9);
     }
+    // Resident objects come from the device's default stream-ordered pool.
+    // Keep freed blocks in this process's pool instead of returning them to
+    // the driver at every synchronisation, so a commit/release cycle reuses
+    // the same memory.  The pool belongs to this process.
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
     if (cudaMalloc(&ctx->d_flag, 16) != cudaSuccess) {
         delete ctx;
         return V3C_ENOMEM;
@@ -892,7 +910,7 @@ namespace detail {
 // inputs in the arena, and launches the batch.  Caller holds ctx->mu and
 // has selected the device.  Shared by v3c_commit and the serving loop.
 v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64* ids, cudaStream_t s,
-                         u64* arena_override, size_t arena_words, const u64* preassigned_ids)
+                         u64* arena_override, size_t arena_words, const u64* preassigned_ids, bool allow_graph)
 {
     size_t need = 0, scratch = 0, staged = 0;
     for (u32 i = 0; i < nb; i++) {
@@ -1013,7 +1031,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
     b.h_threads = h_threads;
     // Replay a captured graph of this batch signature unless graphs are off
     // or per-stage timing (events around each launch) is requested.
-    if (ctx->cfg.flags & (V3C_FLAG_NO_GRAPH | V3C_FLAG_TIMING)) st = launch_batch(ctx, b, s);
+    if (!allow_graph || (ctx->cfg.flags & (V3C_FLAG_NO_GRAPH | V3C_FLAG_TIMING))) st = launch_batch(ctx, b, s);
     else st = launch_batch_graph(ctx, b, s);
     if (st) {
         rollback(nb);
