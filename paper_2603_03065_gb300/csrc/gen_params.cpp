@@ -398,6 +398,31 @@ int main(int argc, char** argv)
                     (unsigned)(v & 0x3FFFFF), (unsigned)((v >> 22) & 0x3FFFFF), (unsigned)(v >> 44));
         }
     fprintf(f, "}\n");
+    // Round constants for the split MDS (21-bit limbs a = bits 0-20,
+    // b = 21-41, c = 42-63), rounds 0..29 plus a zero row 30.  Per round:
+    // [a_i + a_(i+6)] (6), [a_i - a_(i+6) mod 2^32] (6), the same for b
+    // (12), then c_i (12).
+    fprintf(f, "#define V3C_RC_SPLIT_INIT {");
+    for (int r = 0; r <= kRounds; r++) {
+        uint32_t la[kW], lb[kW], lc[kW];
+        for (int i = 0; i < kW; i++) {
+            uint64_t v = r < kRounds ? rc[r][i] : 0;
+            la[i] = (uint32_t)(v & 0x1FFFFF);
+            lb[i] = (uint32_t)((v >> 21) & 0x1FFFFF);
+            lc[i] = (uint32_t)(v >> 42);
+        }
+        uint32_t row[36];
+        for (int i = 0; i < 6; i++) {
+            row[i] = la[i] + la[i + 6];
+            row[6 + i] = la[i] - la[i + 6];
+            row[12 + i] = lb[i] + lb[i + 6];
+            row[18 + i] = lb[i] - lb[i + 6];
+        }
+        for (int i = 0; i < kW; i++) row[24 + i] = lc[i];
+        for (int k = 0; k < 36; k++)
+            fprintf(f, "%s%s%uu", (r || k) ? ", " : "", k % 12 == 0 ? "\\\n  " : "", (unsigned)row[k]);
+    }
+    fprintf(f, "}\n");
     fclose(f);
     return 0;
 }

@@ -60,7 +60,7 @@ u32 leaf_items(const TreeJob& j, const Tiles& t)
 
 // One thread per row: sponge over the first `width` entries in chunks of 8
 // (overwrite mode), digest = lanes 0..3.
-__global__ void __launch_bounds__(128, 6) k_leaf_hash(const TreeJob* __restrict__ jobs, StageList L)
+__global__ void __launch_bounds__(128, 8) k_leaf_hash(const TreeJob* __restrict__ jobs, StageList L)
 {
     for (u32 item = blockIdx.x; item < L.total; item += gridDim.x) {
         u32 jid = find_job_t(L.first, L.njobs, item);

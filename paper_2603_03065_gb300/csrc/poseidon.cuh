@@ -39,6 +39,8 @@ __constant__ u64 c_fast_d0[11 * 11] = V3C_FAST_D0_INIT;
 __constant__ u64 c_rc_full[8 * 12] = V3C_FAST_RC_FULL_INIT;
 // Round constants as 22-bit limbs [round 0..30][lane][3]; row 30 is zero.
 __constant__ u32 c_rc_limbs[31 * 12 * 3] = V3C_RC_LIMBS_INIT;
+// Round constants for the split MDS [round 0..30][36] (see gen_params.cpp).
+__constant__ u32 c_rc_split[31 * 36] = V3C_RC_SPLIT_INIT;
 
 __host__ __device__ constexpr u32 mds_coef(int k)
 {
@@ -47,7 +49,10 @@ __host__ __device__ constexpr u32 mds_coef(int k)
 }
 
 enum MulKind { MUL_INTRINSIC = 0, MUL_PTX = 1, MUL_WIDE = 2 };
-enum MdsKind { MDS_WIDE = 0, MDS_LIMB = 1 };
+// MDS_SPLIT: 21-bit limbs; the two low limb vectors use the block form of
+// the circulant (two 6x6 products instead of one 12x12), the top limb the
+// direct product (see mds_split).
+enum MdsKind { MDS_WIDE = 0, MDS_LIMB = 1, MDS_SPLIT = 2 };
 
 // FOLD2: the limb sums are recombined with 32x32->64 multiply-adds and one
 // carry chain instead of shifts and compares.  ARCM: the round constants of
@@ -100,9 +105,10 @@ __device__ __forceinline__ u64 limb_fold3(u32 A, u32 B, u32 Cc)
     return r;
 }
 // The configuration the library's kernels use (fastest measured on GB300:
-// PTX 64x64 products, 22-bit-limb MDS, round constants merged into the MDS
-// accumulators, PTX carry-chain fold and reduction, plain round order).
-typedef Cfg<MUL_PTX, MDS_LIMB, false, false, false, true, true, true> Default;
+// split MDS on 21-bit limbs, round constants merged into the MDS
+// accumulators, PTX carry-chain reduction, compiler 64x64 products, plain
+// round order).
+typedef Cfg<MUL_INTRINSIC, MDS_SPLIT, false, false, false, true, false, true> Default;
 
 struct U128 {
     u64 lo, hi;
@@ -249,6 +255,95 @@ __device__ __forceinline__ u64 limb_fold2(u32 A, u32 B, u32 Cc)
     return (u64)c * 0xFFFFFFFFu + r;
 }
 
+// A + B 2^21 + C 2^42 (A, B, C < 2^32) to [0, 2^64): w0 = A + (B << 21)
+// carries c0; w1 = (B >> 11) + (C << 10 mod 2^32) + c0 carries c1; the
+// multiple of 2^64 is h = (C >> 22) + c1 < 2^11, folded as h EPS.  The last
+// step carries at most once, and after a carry the sum is below 2^43.
+__device__ __forceinline__ u64 limb_fold21(u32 A, u32 B, u32 Cc)
+{
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 t, u, v, w0, w1, hh, h, u0, u1, r0, r1, c;\n\t"
+        "shl.b32 t, %2, 21;\n\t"
+        "add.cc.u32 w0, %1, t;\n\t"
+        "shr.b32 u, %2, 11;\n\t"
+        "shl.b32 v, %3, 10;\n\t"
+        "addc.cc.u32 w1, u, v;\n\t"
+        "shr.b32 hh, %3, 22;\n\t"
+        "addc.u32 h, hh, 0;\n\t"
+        "sub.cc.u32 u0, 0, h;\n\t"
+        "subc.u32 u1, h, 0;\n\t"
+        "add.cc.u32 r0, w0, u0;\n\t"
+        "addc.cc.u32 r1, w1, u1;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "sub.cc.u32 r0, r0, c;\n\t"
+        "subc.u32 r1, r1, 0;\n\t"
+        "add.u32 r1, r1, c;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "r"(A), "r"(B), "r"(Cc));
+    return r;
+}
+
+// Block form of the circulant: with x = (x_top, x_bot) in halves of 6,
+// M = [[A, B], [B, A]], so y_top + y_bot = (A + B)(x_top + x_bot) and
+// y_top - y_bot = (A - B)(x_top - x_bot).  A + B is the 6x6 circulant of
+// s_k = m_k + m_(k+6); A - B has entries m[(j-i) mod 12] - m[(j-i+6) mod 12].
+__host__ __device__ constexpr u32 split_s(int k) { return mds_coef(k) + mds_coef(k + 6); }
+__host__ __device__ constexpr u32 split_d(int i, int j)
+{
+    return mds_coef(((j - i) % 12 + 12) % 12) - mds_coef(((j - i + 6) % 12 + 12) % 12);  // mod 2^32
+}
+
+// y = M x + rc for one vector of 21-bit limbs.  Bounds: u < 2^22, so
+// P <= 6 * 126 * (2^22 - 2) + 2^22 < 2^32; |v| < 2^21 and |Q| < 2^30; the true
+// P + Q and P - Q are 2 y in [0, 2^32), so the 32-bit sums are exact and the
+// halving is a logical shift.  init = [P inits (6), Q inits (6)].
+__device__ __forceinline__ void split6(const u32 (&x)[12], const u32* init, u32 (&y)[12])
+{
+    u32 u[6], v[6];
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        u[j] = x[j] + x[j + 6];
+        v[j] = x[j] - x[j + 6];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        u32 P = init[i], Q = init[6 + i];
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            P += u[j] * split_s((j - i + 6) % 6);
+            Q += v[j] * split_d(i, j);
+        }
+        y[i] = (P + Q) >> 1;
+        y[i + 6] = (P - Q) >> 1;
+    }
+}
+
+// s <- M s (+ the next round's constants, from init) with 21-bit limbs.
+__device__ __forceinline__ void mds_split(u64 (&s)[12], const u32* init)
+{
+    u32 a[12], b[12], c[12];
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+        a[j] = (u32)s[j] & 0x1FFFFFu;
+        b[j] = (u32)(s[j] >> 21) & 0x1FFFFFu;
+        c[j] = (u32)(s[j] >> 42);
+    }
+    u32 ya[12], yb[12];
+    split6(a, init, ya);
+    split6(b, init + 12, yb);
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        // The 22-bit top limb: direct product; 12 * 63 * (2^22 - 1) + 2^22 < 2^32.
+        u32 Cc = init[24 + i];
+#pragma unroll
+        for (int j = 0; j < 12; j++) Cc += c[j] * mds_coef((j - i + 12) % 12);
+        s[i] = limb_fold21(ya[i], yb[i], Cc);
+    }
+}
+
 // s <- M s, M[i][j] = m[(j - i) mod 12].  With C::ARCM the accumulators start
 // from the limbs `init` (the next round's constants), so the output is
 // M s + RC.
@@ -256,6 +351,10 @@ template <class C>
 __device__ __forceinline__ void mds(u64 (&s)[12], const u32* init = nullptr)
 {
     u64 out[12];
+    if (C::MDS == MDS_SPLIT) {
+        mds_split(s, init);
+        return;
+    }
     if (C::MDS == MDS_LIMB) {
         u32 a[12], b[12], c[12];
 #pragma unroll
@@ -323,7 +422,7 @@ __device__ __forceinline__ void permute_plain(u64 (&s)[12])
             } else {
                 s[0] = sbox<C>(s[0]);
             }
-            mds<C>(s, c_rc_limbs + (r + 1) * 36);
+            mds<C>(s, (C::MDS == MDS_SPLIT ? c_rc_split : c_rc_limbs) + (r + 1) * 36);
         }
         return;
     }
