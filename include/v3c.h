@@ -264,7 +264,7 @@ v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz);
  * Its work space is one file-scope device array of V3C_NOALLOC_SCRATCH_BYTES.
  * Every GPU that loads the library holds that array until the process exits.
  * It needs 8 * (64 + T + c * (n + N)) bytes.  T is the shape's table size,
- * at most 2n + N + 2^14 words.  The c * (n + N) term is 0 when
+ * at most 2n + 2^14 words.  The c * (n + N) term is 0 when
  * n <= 2^(13 - rate_bits).
  * A larger shape returns V3C_EINVAL before anything is enqueued; for example
  * 135 x 2^14 rows at rate 3 is too large.  The caller still passes and owns

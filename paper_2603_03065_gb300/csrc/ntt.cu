@@ -36,13 +36,17 @@ void plan_split(u32 log_n, u32 r, u32& log_n1, u32& log_n2)
 
 static inline size_t half_or_one(u32 log_l) { return log_l ? (size_t)1 << (log_l - 1) : 1; }
 
+// Powers of w_N in three 512-entry tables: w_N^e for any e < 2^27 is
+// pw[e mod 2^9] * pw[512 + (e >> 9) mod 2^9] * pw[1024 + (e >> 18)].
+constexpr size_t kPowWords = 3 * 512;
+
 size_t plan_table_words(u32 log_n, u32 r)
 {
     u32 l1, l2;
     plan_split(log_n, r, l1, l2);
     size_t n = (size_t)1 << log_n, N = n << r;
     size_t w = n;                          // scale
-    if (l1) w += n + N;                    // twa, twb
+    if (l1) w += n + kPowWords;            // twa, pw_N
     w += half_or_one(l1) * 2 + half_or_one(l2) + half_or_one(l2 + r);
     return w;
 }
@@ -64,7 +68,7 @@ static u64 hinv(u64 a) { return hpow(a, gl::P - 2); }
 struct TableArgs {
     u64* twa;
     u64* scale;
-    u64* twb;
+    u64* pw_N;
     u64* rinv_n1;
     u64* rinv_n2;
     u64* rfwd_M;
@@ -88,10 +92,10 @@ __global__ void k_plan_tables(TableArgs a)
             u64 k1 = i >> a.log_n2, t = i & (n2 - 1);
             u64 j = k1 + (u64)n1 * gl::bitrev((u32)t, a.log_n2);
             a.scale[i] = gl::mul(gl::pow(7, j), a.n_inv);
-        } else if (e < a.seg[2]) {  // twb[k1][q]
+        } else if (e < a.seg[2]) {  // pw_N[level][j] = w_N^(j * 2^(9 level))
             u64 i = e - a.seg[1];
-            u64 k1 = i >> a.log_M, q = i & (((u64)1 << a.log_M) - 1);
-            a.twb[i] = gl::pow(a.w_N, (k1 * q) & N_mask);
+            u64 level = i >> 9, j = i & 511;
+            a.pw_N[i] = gl::pow(a.w_N, (j << (9 * level)) & N_mask);
         } else if (e < a.seg[3]) {
             u64 i = e - a.seg[2];
             a.rinv_n1[i] = gl::pow(a.w_n1_inv, i);
@@ -123,8 +127,8 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
     cur += l1 ? n : 0;
     a.scale = cur;
     cur += n;
-    a.twb = l1 ? cur : nullptr;
-    cur += l1 ? N : 0;
+    a.pw_N = l1 ? cur : nullptr;
+    cur += l1 ? kPowWords : 0;
     a.rinv_n1 = cur;
     cur += half_or_one(l1);
     a.rinv_n2 = cur;
@@ -135,7 +139,7 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
     cur += half_or_one(l1);
     a.seg[0] = l1 ? n : 0;
     a.seg[1] = a.seg[0] + n;
-    a.seg[2] = a.seg[1] + (l1 ? N : 0);
+    a.seg[2] = a.seg[1] + (l1 ? kPowWords : 0);
     a.seg[3] = a.seg[2] + half_or_one(l1);
     a.seg[4] = a.seg[3] + half_or_one(l2);
     a.seg[5] = a.seg[4] + half_or_one(p.log_M);
@@ -154,7 +158,7 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
     a.log_N = p.log_N;
     p.twa = a.twa;
     p.scale = a.scale;
-    p.twb = a.twb;
+    p.pw_N = a.pw_N;
     p.rinv_n1 = a.rinv_n1;
     p.rinv_n2 = a.rinv_n2;
     p.rfwd_M = a.rfwd_M;
@@ -369,6 +373,13 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
 
 u32 stage_b_items(const LdeJob& j) { return j.c << j.plan.log_n1; }
 
+// w_N^e for e < 2^27 from the three power tables of the plan.
+__device__ __forceinline__ u64 pow_wN(const u64* __restrict__ pw, u64 e)
+{
+    u64 r = gl::mul(__ldg(pw + (e & 511)), __ldg(pw + 512 + ((e >> 9) & 511)));
+    return gl::mul(r, __ldg(pw + 1024 + (e >> 18)));
+}
+
 size_t stage_b_smem(const LdeJob& j)
 {
     size_t n2 = (size_t)1 << j.plan.log_n2, M = (size_t)1 << j.plan.log_M;
@@ -415,10 +426,15 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
             // stage C reads one contiguous run per column.
             u64* Z = J.Z + ((size_t)col << J.plan.log_N);
             const u32 Q = J.c_q, lQ = __ffs(Q) - 1;
-            const u64* tb = J.plan.twb + ((size_t)k1 << lM);
+            // Twiddle w_N^(k1 q) for q = tid + i * blockDim: start at
+            // w_N^(k1 tid) and step by w_N^(k1 blockDim), exact in F_p.
+            const u64 N_mask = ((u64)1 << J.plan.log_N) - 1;
+            u64 tw = pow_wN(J.plan.pw_N, ((u64)k1 * threadIdx.x) & N_mask);
+            const u64 step = pow_wN(J.plan.pw_N, ((u64)k1 * blockDim.x) & N_mask);
             for (u32 q = threadIdx.x; q < M; q += blockDim.x) {
                 size_t idx = ((size_t)(q >> lQ) << (l1 + lQ)) + ((size_t)k1 << lQ) + (q & (Q - 1));
-                __stcs(Z + idx, gl::mul(data[sw(q)], tb[q]));
+                __stcs(Z + idx, gl::mul(data[sw(q)], tw));
+                tw = gl::mul(tw, step);
             }
         } else {
             // n1 = 1: this CTA holds the whole column; write committed rows.
