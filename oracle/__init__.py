@@ -70,6 +70,10 @@ def lib():
                 "orc_merkle_verify": (i32, [_u64p, u32, u32, u32, u64, _u64p, _u64p]),
                 "orc_commit": (i32, [_u64p, u32, u32, u32, u32, _u64p, u32, _u64p, _u64p, i32]),
                 "orc_domain_log2": (u32, [u64]),
+                "orc_fri_combine": (i32, [_u64p, u32, u32, u64, u64, u64, i32, _u64p, i32]),
+                "orc_fri_fold_coset": (u64, [_u64p, u32, u64, u32, u64, u64]),
+                "orc_fri_fold": (i32, [_u64p, u32, u64, u32, u64, _u64p, i32]),
+                "orc_fri_interpolate": (i32, [_u64p, u32, u64, _u64p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -264,3 +268,120 @@ def commit(cols, rate_bits: int, cap_height: int, threads: int | None = None):
 
 def domain_log2(G: int) -> int:
     return lib().orc_domain_log2(G)
+
+
+# --- FRI commit phase ------------------------------------------------------
+# The combine / fold / interpolate arithmetic is in oracle.c; below is only the
+# round schedule and the bookkeeping of layers, trees and openings.
+GENERATOR = 7
+
+
+def fri_combine(ldes, widths, alpha: int, threads: int | None = None) -> np.ndarray:
+    """f_0[t] = sum over the committed matrices, in order, of alpha^e row_t[i],
+    with e running on from one matrix to the next."""
+    f = None
+    e0 = 0
+    for m, c in zip(ldes, widths):
+        a = _u64(m)
+        nrows, ld = a.shape
+        if f is None:
+            f = np.zeros(nrows, np.uint64)
+        assert lib().orc_fri_combine(_p(a), ld, c, nrows, alpha, e0, 1, _p(f),
+                                     threads or default_threads()) == 0
+        e0 += c
+    return f
+
+
+def fri_fold(f, shift: int, arity_bits: int, beta: int, threads: int | None = None) -> np.ndarray:
+    a = _u64(f)
+    logm = a.size.bit_length() - 1
+    out = np.empty(a.size >> arity_bits, np.uint64)
+    assert lib().orc_fri_fold(_p(a), logm, shift, arity_bits, beta, _p(out),
+                              threads or default_threads()) == 0
+    return out
+
+
+def fri_fold_coset(vals, logm: int, shift: int, arity_bits: int, beta: int, w: int) -> int:
+    return int(lib().orc_fri_fold_coset(_p(_u64(vals)), logm, shift, arity_bits, beta, w))
+
+
+def fri_interpolate(f, shift: int) -> np.ndarray:
+    a = _u64(f)
+    out = np.empty_like(a)
+    assert lib().orc_fri_interpolate(_p(a), a.size.bit_length() - 1, shift, _p(out)) == 0
+    return out
+
+
+def fri_arities(log_N: int, arity_bits: int, final_log: int) -> list[int]:
+    """Arity exponent of each round: arity_bits while the layer stays at or
+    above 2^final_log, then whatever remains."""
+    out, m = [], log_N
+    while m > final_log:
+        a = min(arity_bits, m - final_log)
+        out.append(a)
+        m -= a
+    return out
+
+
+def fri_commit(ldes, widths, alpha: int, betas, arity_bits: int, final_log: int, cap_height: int,
+               threads: int | None = None) -> dict:
+    """Commit phase: layer k (k < R) is committed as a Merkle tree whose leaf w
+    is the coset [w 2^a_k, (w+1) 2^a_k) of the layer; the last layer is sent as
+    polynomial coefficients."""
+    f = fri_combine(ldes, widths, alpha, threads)
+    log_N = f.size.bit_length() - 1
+    ar = fri_arities(log_N, arity_bits, final_log)
+    assert len(betas) >= len(ar)
+    layers, trees, caps, shifts, heights = [f], [], [], [GENERATOR], []
+    for k, a in enumerate(ar):
+        cur = layers[-1]
+        logL = (cur.size.bit_length() - 1) - a
+        h = min(cap_height, logL)
+        tree, cap = merkle(cur.reshape(-1, 1 << a), 1 << a, h, threads)
+        trees.append(tree)
+        caps.append(cap)
+        heights.append(h)
+        layers.append(fri_fold(cur, shifts[-1], a, betas[k], threads))
+        shifts.append(pow_(shifts[-1], 1 << a))
+    final = fri_interpolate(layers[-1], shifts[-1])
+    return {"layers": layers, "trees": trees, "caps": caps, "shifts": shifts, "arities": ar,
+            "heights": heights, "final": final, "betas": [int(b) for b in betas[: len(ar)]]}
+
+
+def fri_query(st: dict, t0: int) -> list[tuple[np.ndarray, np.ndarray]]:
+    """Openings of query position t0 (in layer 0): per round, the coset values
+    holding the query's position and their Merkle path."""
+    out, t = [], t0
+    for k, a in enumerate(st["arities"]):
+        cur = st["layers"][k]
+        logL = (cur.size.bit_length() - 1) - a
+        leaf = t >> a
+        vals = cur[leaf << a: (leaf + 1) << a].copy()
+        path = merkle_path(st["trees"][k], logL, st["heights"][k], leaf)
+        out.append((vals, path))
+        t = leaf
+    return out
+
+
+def fri_verify_query(caps, heights, arities, betas, final, log_N: int, t0: int, f0_value: int,
+                     openings) -> bool:
+    """Verifier side of one query: the opened cosets authenticate against the
+    layer caps, hold the running value at the query position, and fold into
+    the next layer's value; the last value equals the final polynomial at the
+    query's point."""
+    t, shift, logm, value = t0, GENERATOR, log_N, int(f0_value)
+    for k, a in enumerate(arities):
+        vals, path = openings[k]
+        logL = logm - a
+        leaf = t >> a
+        if int(vals[t & ((1 << a) - 1)]) != value:
+            return False
+        if not merkle_verify(vals, 1 << a, logL, heights[k], leaf, path, caps[k]):
+            return False
+        value = fri_fold_coset(vals, logm, shift, a, int(betas[k]), leaf)
+        t, logm, shift = leaf, logL, pow_(shift, 1 << a)
+    x = mul(shift, pow_(root_of_unity(logm), bitrev(t, logm)))
+    acc = 0
+    for c in reversed([int(v) for v in final]):
+        acc = add(mul(acc, x), c)
+    return acc == value

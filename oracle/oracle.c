@@ -633,3 +633,115 @@ uint32_t orc_domain_log2(uint64_t G)
     while (((uint64_t)1 << k) < G) k++;
     return k;
 }
+
+/* ------------------------------------------------------------------ */
+/* FRI commit phase.  The paper's prover uses the default Plonky2 FRI    */
+/* setup (Sec. 5, evaluation environment) but prints no FRI formula; the */
+/* steps below are the textbook FRI commit phase (Ben-Sasson, Bentov,    */
+/* Horesh, Riabzev, ICALP 2018) on the bit-reversed codeword:            */
+/*   combine  f_0(x_t) = sum_i alpha^i row_t[i];                         */
+/*   fold     f = sum_{i < 2^a} X^i f_i(X^{2^a})  ->  sum_i beta^i f_i;  */
+/*   final    coefficients of the last layer's polynomial.               */
+/* A layer of size m sits on the coset s * <w_m>; position t holds the   */
+/* value at x_t = s * w_m^{bitrev_{log m}(t)}.                           */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const u64* rows;
+    uint32_t ld, c;
+    u64 alpha, a0; /* a0 = alpha^e0 */
+    int acc;
+    u64* out;
+} combine_ctx;
+static void combine_body(void* vctx, size_t t)
+{
+    combine_ctx* C = (combine_ctx*)vctx;
+    const u64* row = C->rows + t * C->ld;
+    u64 s = 0, w = C->a0;
+    for (uint32_t i = 0; i < C->c; i++) {
+        s = orc_add(s, orc_mul(w, row[i]));
+        w = orc_mul(w, C->alpha);
+    }
+    C->out[t] = C->acc ? orc_add(C->out[t], s) : s;
+}
+
+/* out[t] (+)= sum_{i<c} alpha^(e0 + i) * rows[t][i] for t < nrows. */
+int orc_fri_combine(const u64* rows, uint32_t ld, uint32_t c, uint64_t nrows, u64 alpha, uint64_t e0,
+                    int acc, u64* out, int threads)
+{
+    combine_ctx C = {rows, ld, c, alpha, orc_pow(alpha, e0), acc, out};
+    parallel_for(nrows, threads, combine_body, &C);
+    return 0;
+}
+
+/* Fold of one coset: output position w of a layer of 2^logm values on
+ * shift * <w_m>.  The coset holds positions w*2^a + v (v < 2^a), whose
+ * points x_v all square a times to y_w.  With f(x_v) = sum_i x_v^i f_i(y_w),
+ * the sum over the coset of f(x_v) x_v^{-i} is 2^a f_i(y_w), so
+ *   f_i(y_w) = 2^{-a} sum_v f(x_v) x_v^{-i},  result = sum_i beta^i f_i(y_w).
+ * vals[v] = f(x_v). */
+u64 orc_fri_fold_coset(const u64* vals, uint32_t logm, u64 shift, uint32_t a, u64 beta, uint64_t w)
+{
+    uint32_t A = 1u << a;
+    u64 w_m = orc_root_of_unity(logm), inv_arity = orc_inv((u64)A);
+    u64 xinv[256], xpow[256]; /* x_v^{-1} and x_v^{-i} */
+    for (uint32_t v = 0; v < A; v++) {
+        xinv[v] = orc_inv(orc_mul(shift, orc_pow(w_m, bitrev((u64)w * A + v, logm))));
+        xpow[v] = 1;
+    }
+    u64 res = 0, bpow = 1;
+    for (uint32_t i = 0; i < A; i++) {
+        u64 fi = 0;
+        for (uint32_t v = 0; v < A; v++) {
+            fi = orc_add(fi, orc_mul(vals[v], xpow[v]));
+            xpow[v] = orc_mul(xpow[v], xinv[v]);
+        }
+        fi = orc_mul(fi, inv_arity);
+        res = orc_add(res, orc_mul(bpow, fi));
+        bpow = orc_mul(bpow, beta);
+    }
+    return res;
+}
+
+typedef struct {
+    const u64* f;
+    uint32_t logm, a;
+    u64 shift, beta;
+    u64* out;
+} fold_ctx;
+static void fold_body(void* vctx, size_t w)
+{
+    fold_ctx* F = (fold_ctx*)vctx;
+    F->out[w] = orc_fri_fold_coset(F->f + (w << F->a), F->logm, F->shift, F->a, F->beta, w);
+}
+
+/* One FRI fold of arity 2^a: f has 2^logm values on shift * <w_{2^logm}> in
+ * bit-reversed order; out gets 2^(logm - a) values on shift^(2^a) * <...>,
+ * also bit-reversed. */
+int orc_fri_fold(const u64* f, uint32_t logm, u64 shift, uint32_t a, u64 beta, u64* out, int threads)
+{
+    if (a == 0 || a > 8 || a > logm) return -1;
+    fold_ctx F = {f, logm, a, shift, beta, out};
+    parallel_for((size_t)1 << (logm - a), threads, fold_body, &F);
+    return 0;
+}
+
+/* Coefficients c_i of the polynomial of degree < m whose value at
+ * x_t = shift * w_m^{bitrev(t)} is f[t]: by the inverse DFT definition,
+ * c_i = m^{-1} shift^{-i} sum_j E_j w_m^{-ij} with E_j = f[bitrev(j)]. */
+int orc_fri_interpolate(const u64* f, uint32_t logm, u64 shift, u64* coeffs)
+{
+    size_t m = (size_t)1 << logm;
+    u64 winv = orc_inv(orc_root_of_unity(logm)), minv = orc_inv((u64)m % ORC_P), sinv = orc_inv(shift);
+    u64 spow = minv;
+    for (size_t i = 0; i < m; i++) {
+        u64 s = 0, wi = orc_pow(winv, i), wij = 1;
+        for (size_t j = 0; j < m; j++) {
+            s = orc_add(s, orc_mul(f[bitrev(j, logm)], wij));
+            wij = orc_mul(wij, wi);
+        }
+        coeffs[i] = orc_mul(s, spow);
+        spow = orc_mul(spow, sinv);
+    }
+    return 0;
+}
