@@ -55,11 +55,24 @@ INPUT_HOST_COPY, INPUT_DEVICE, INPUT_HOST_BORROW = 0, 1, 2
 
 
 FLAG_TIMING = 2
-STAGES = ("lde_a", "lde_b", "lde_c", "leaf_hash", "merkle")
+STAGES = ("lde_a", "lde_b", "lde_c", "leaf_hash", "merkle", "fri_combine", "fri_fold", "open")
 
 
 class StageStats(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_uint64 * 5)]
+    _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("launches", ctypes.c_uint64 * len(STAGES))]
+
+
+FRI_MAX_ROUNDS = 25
+
+
+class FriCfg(ctypes.Structure):
+    _fields_ = [("arity_bits", _u32), ("final_log", _u32), ("cap_height", _u32)]
+
+
+class FriInfo(ctypes.Structure):
+    _fields_ = [("rounds", _u32), ("rounds_done", _u32), ("log_N", _u32), ("n_columns", _u32),
+                ("arity_bits", _u32 * FRI_MAX_ROUNDS), ("log_size", _u32 * (FRI_MAX_ROUNDS + 1)),
+                ("cap_height", _u32 * FRI_MAX_ROUNDS), ("query_words", _u64), ("bytes", _u64)]
 
 
 class ReqTimes(ctypes.Structure):
@@ -91,6 +104,15 @@ SIGNATURES = {
     "v3c_stage_stats": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_int]),
     "v3c_lde_noalloc": (ctypes.c_int, [_vp, _u32, _u32, _u32, _vp, _u32, _vp]),
     "v3c_int_peak": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    # include/v3c_fri.h
+    "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
+    "v3c_fri_fold": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _vp]),
+    "v3c_fri_info": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(FriInfo)]),
+    "v3c_fri_cap": (ctypes.c_int, [_vp, _u64, _u32, _u64p]),
+    "v3c_fri_final": (ctypes.c_int, [_vp, _u64, _u64p]),
+    "v3c_fri_query": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _u64p]),
+    "v3c_fri_release": (ctypes.c_int, [_vp, _u64]),
+    "v3c_open_batch": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _u64p, _u64p]),
 }
 
 _lib = None
@@ -337,6 +359,69 @@ class Context:
 
     def serve_stop(self):
         self._check(self.lib.v3c_serve_stop(self.h))
+
+    # --------------------------------------------------------------- openings
+    def open_batch(self, cid: int, leaves, c: int, rows: bool = True, paths: bool = True):
+        """Rows [nq][c] and paths [nq][log_N - h][4] of many leaves in one call."""
+        b = self.buffers(cid)
+        k = b["log_rows"] - b["cap_height"]
+        idx = np.ascontiguousarray(leaves, dtype=np.uint64)
+        nq = idx.size
+        r = np.zeros((nq, c), np.uint64) if rows else None
+        pth = np.zeros((nq, k, 4), np.uint64) if paths else None
+        self._check(self.lib.v3c_open_batch(self.h, cid, idx.ctypes.data_as(_u64p), nq,
+                                            r.ctypes.data_as(_u64p) if rows else None,
+                                            pth.ctypes.data_as(_u64p) if paths and k else None))
+        return r, pth
+
+    # --------------------------------------------------------------- FRI
+    def fri_begin(self, cids, alpha: int, arity_bits: int = 4, final_log: int = 5, cap_height: int = 4,
+                  betas=(), stream=None) -> int:
+        ids = np.ascontiguousarray(cids, dtype=np.uint64)
+        bs = np.ascontiguousarray(betas, dtype=np.uint64)
+        cfg = FriCfg(arity_bits, final_log, cap_height)
+        out = _u64()
+        self._check(self.lib.v3c_fri_begin(self.h, ids.ctypes.data_as(_u64p), ids.size, alpha, ctypes.byref(cfg),
+                                           bs.ctypes.data_as(_u64p) if bs.size else None, bs.size,
+                                           ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def fri_fold(self, fid: int, betas, stream=None):
+        bs = np.ascontiguousarray(betas, dtype=np.uint64)
+        self._check(self.lib.v3c_fri_fold(self.h, fid, bs.ctypes.data_as(_u64p), bs.size, _stream(stream)))
+
+    def fri_info(self, fid: int) -> dict:
+        i = FriInfo()
+        self._check(self.lib.v3c_fri_info(self.h, fid, ctypes.byref(i)))
+        R = i.rounds
+        return {"rounds": R, "rounds_done": i.rounds_done, "log_N": i.log_N, "n_columns": i.n_columns,
+                "arities": list(i.arity_bits[:R]), "log_sizes": list(i.log_size[: R + 1]),
+                "heights": list(i.cap_height[:R]), "query_words": i.query_words, "bytes": i.bytes}
+
+    def fri_cap(self, fid: int, layer: int) -> np.ndarray:
+        info = self.fri_info(fid)
+        out = np.zeros((1 << info["heights"][layer]) * 4, np.uint64)
+        self._check(self.lib.v3c_fri_cap(self.h, fid, layer, out.ctypes.data_as(_u64p)))
+        return out.reshape(-1, 4)
+
+    def fri_final(self, fid: int) -> np.ndarray:
+        info = self.fri_info(fid)
+        out = np.zeros(1 << info["log_sizes"][-1], np.uint64)
+        self._check(self.lib.v3c_fri_final(self.h, fid, out.ctypes.data_as(_u64p)))
+        return out
+
+    def fri_query(self, fid: int, indices) -> np.ndarray:
+        """Raw opening records [nq][query_words]: per layer, the coset values
+        then the Merkle path."""
+        info = self.fri_info(fid)
+        idx = np.ascontiguousarray(indices, dtype=np.uint64)
+        out = np.zeros((idx.size, info["query_words"]), np.uint64)
+        self._check(self.lib.v3c_fri_query(self.h, fid, idx.ctypes.data_as(_u64p), idx.size,
+                                           out.ctypes.data_as(_u64p)))
+        return out
+
+    def fri_release(self, fid: int):
+        self._check(self.lib.v3c_fri_release(self.h, fid))
 
     # --------------------------------------------------------------- misc
     def kernel_launches(self) -> int:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libv3c.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["ntt.cu", "hash.cu", "v3c.cu", "serve.cu", "lde_noalloc.cu"]
+UNITS = ["ntt.cu", "hash.cu", "v3c.cu", "serve.cu", "lde_noalloc.cu", "fri.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 def _sources() -> list[str]:
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    out.append(os.path.join(INCLUDE, "v3c.h"))
+    out += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return out
 
 

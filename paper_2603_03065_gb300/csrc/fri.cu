@@ -1,0 +1,692 @@
+// FRI commit phase on resident commitments, and batched Merkle openings.
+//
+// The prover of the paper runs Plonky2 with its default FRI setup (Sec. 5,
+// evaluation environment); the commitments it opens are the Merkle trees of
+// Sec. 4.3, opened by the bits of the leaf index (Sec. 4.4, MerkleOpen).
+// The FRI steps are the textbook commit phase (Ben-Sasson et al., ICALP
+// 2018): a random linear combination of the committed columns, then folds
+// f -> sum_i beta^i f_i of f = sum_i X^i f_i(X^(2^a)), each layer committed
+// with the same Poseidon Merkle kernels as the LDE.
+//
+// GB300 mapping: the combination streams the whole resident LDE once (the
+// only HBM-heavy step) with one warp per 32 rows and 16-byte loads across
+// each row.  A fold reads each coset (2^a contiguous values) into registers
+// and applies a arity-2 steps there, one output per thread.  The layer
+// trees go through the batched leaf-hash and Merkle launches.  Openings are
+// one gather launch per call over every (query, word) pair.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../include/v3c_fri.h"
+#include "ctx.h"
+#include "gl.cuh"
+#include "internal.h"
+
+namespace v3c {
+
+using gl::u32;
+using gl::u64;
+
+struct FriState {
+    u64 id = 0;
+    u32 rounds = 0, done = 0, log_N = 0, ncols = 0;
+    u32 arity[V3C_FRI_MAX_ROUNDS] = {0};
+    u32 log_size[V3C_FRI_MAX_ROUNDS + 1] = {0};
+    u32 h[V3C_FRI_MAX_ROUNDS] = {0};
+    u64 shift[V3C_FRI_MAX_ROUNDS + 1] = {0};  // s_k
+    u64* mem = nullptr;
+    size_t bytes = 0;
+    u64* f[V3C_FRI_MAX_ROUNDS + 1] = {nullptr};
+    u64* tree[V3C_FRI_MAX_ROUNDS] = {nullptr};
+    u64* cap[V3C_FRI_MAX_ROUNDS] = {nullptr};
+    u64* final_coef = nullptr;
+    u64* pw_inv = nullptr;  // [3][512] powers of w_N^-1
+    u64* alpha_pw = nullptr;
+    u32 committed = 0;  // layers [0, committed) have trees
+    u64 query_words = 0;
+    cudaEvent_t ev = nullptr;
+};
+
+// ---------------------------------------------------------------- kernels
+
+// out[i] = alpha^i.
+__global__ void k_fri_powers(u64 alpha, u32 count, u64* out)
+{
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        out[i] = gl::pow(alpha, i);
+}
+
+// pw[512 l + j] = winv^((j << 9 l) mod N): w_N^-e for e < 2^27 is then the
+// product of pw[e mod 2^9], pw[512 + (e >> 9) mod 2^9], pw[1024 + (e >> 18)].
+__global__ void k_fri_root_tables(u64 winv, u32 log_N, u64* pw)
+{
+    u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 1536) return;
+    u64 e = ((u64)(i & 511) << (9 * (i >> 9))) & (((u64)1 << log_N) - 1);
+    pw[i] = gl::pow(winv, e);
+}
+
+__device__ __forceinline__ u64 pow3(const u64* __restrict__ pw, u64 e)
+{
+    u64 r = gl::mul(__ldg(pw + (e & 511)), __ldg(pw + 512 + ((e >> 9) & 511)));
+    return gl::mul(r, __ldg(pw + 1024 + (e >> 18)));
+}
+
+// f[t] (+)= sum_{i<c} pw[i] row_t[i].  A warp takes 32 consecutive rows; lane
+// l reads the column pairs (2l + 64j, 2l + 1 + 64j) of each row with 16-byte
+// loads (ld even, rows 16-byte aligned), the warp sums the lanes, and lane j
+// keeps row j's value for one coalesced store.
+__global__ void __launch_bounds__(256) k_fri_combine(const u64* __restrict__ rows, u32 ld, u32 c,
+                                                     const u64* __restrict__ pw, u64 nrows, int acc,
+                                                     u64* __restrict__ f)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 warp = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5;
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
+        const u32 cnt = (u32)min((u64)32, nrows - t0);
+        u64 mine = 0;
+        for (u32 j = 0; j < cnt; j++) {
+            const u64* row = rows + (t0 + j) * ld;
+            u64 s = 0;
+            for (u32 i = 2 * lane; i < c; i += 64) {
+                ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(row + i));
+                s = gl::add(s, gl::mul(v.x, __ldg(pw + i)));
+                if (i + 1 < c) s = gl::add(s, gl::mul(v.y, __ldg(pw + i + 1)));
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) s = gl::add(s, __shfl_xor_sync(0xffffffffu, s, o));
+            if (lane == j) mine = s;
+        }
+        if (lane < cnt) {
+            u64* d = f + t0 + lane;
+            *d = acc ? gl::add(*d, mine) : mine;
+        }
+    }
+}
+
+// Per-round fold constants.  Step m of a round pairs positions (2u, 2u+1) of
+// the intermediate layer; with u = w 2^b + v' (b = a-1-m) the point of
+// position 2u is x = s^(2^m) w_{2^(b+1)}^bitrev_b(v') (w_{N_k}^e)^(2^m),
+// e = bitrev_{log N_{k+1}}(w).  K holds beta^(2^m) (2 s^(2^m))^-1
+// w_{2^(b+1)}^-bitrev_b(v') for every (m, v'), steps in order.
+struct FoldArgs {
+    const u64* in;
+    u64* out;
+    const u64* pw_inv;
+    u32 log_out;    // log2 N_{k+1}
+    u32 exp_shift;  // log2 (N_0 / N_k)
+    u64 inv2;
+    u64 K[15];
+};
+
+// g(x^2) = (f(x) + f(-x)) / 2 + beta (f(x) - f(-x)) / (2x), applied a times
+// in registers to one coset of 2^a values.
+template <int A_BITS>
+__global__ void __launch_bounds__(256) k_fri_fold(FoldArgs p)
+{
+    constexpr int A = 1 << A_BITS;
+    const u64 nout = (u64)1 << p.log_out;
+    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nout; w += (u64)gridDim.x * blockDim.x) {
+        u64 v[A];
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(p.in + (w << A_BITS));
+#pragma unroll
+        for (int k = 0; k < A / 2; k++) {
+            ulonglong2 q = __ldg(src + k);
+            v[2 * k] = q.x;
+            v[2 * k + 1] = q.y;
+        }
+        u64 e = (u64)gl::bitrev((u32)w, p.log_out) << p.exp_shift;
+        u64 z = pow3(p.pw_inv, e);  // 1 / (w_{N_k}^e)
+        int kidx = 0;
+#pragma unroll
+        for (int m = 0; m < A_BITS; m++) {
+            const int half = A >> (m + 1);
+#pragma unroll
+            for (int u = 0; u < half; u++) {
+                u64 a0 = v[2 * u], a1 = v[2 * u + 1];
+                u64 t = gl::mul(p.K[kidx + u], z);
+                v[u] = gl::add(gl::mul(gl::add(a0, a1), p.inv2), gl::mul(gl::sub(a0, a1), t));
+            }
+            kidx += half;
+            z = gl::mul(z, z);
+        }
+        p.out[w] = v[0];
+    }
+}
+
+// c_i = m^-1 s^-i sum_j E_j w_m^-ij with E_j = f[bitrev(j)]: the inverse DFT
+// of the natural-order values, unshifted.  One CTA, m <= 1024.
+__global__ void __launch_bounds__(256) k_fri_final(const u64* __restrict__ f, u32 logm, u64 winv, u64 sinv,
+                                                   u64 minv, u64* __restrict__ out)
+{
+    __shared__ u64 E[1024];
+    const u32 m = 1u << logm;
+    for (u32 j = threadIdx.x; j < m; j += blockDim.x) E[j] = f[gl::bitrev(j, logm)];
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < m; i += blockDim.x) {
+        u64 wi = gl::pow(winv, i), wij = 1, acc = 0;
+        for (u32 j = 0; j < m; j++) {
+            acc = gl::add(acc, gl::mul(E[j], wij));
+            wij = gl::mul(wij, wi);
+        }
+        out[i] = gl::mul(acc, gl::mul(gl::pow(sinv, i), minv));
+    }
+}
+
+struct QueryLayer {
+    const u64* f;
+    const u64* tree;
+    u64 word0;  // first word of this layer in a query's record
+    u32 a, logL, h, tshift;  // arity bits, log2 leaves, cap height, sum of earlier arities
+};
+struct QueryArgs {
+    QueryLayer L[V3C_FRI_MAX_ROUNDS];
+    u32 R;
+    u32 nq;
+    u64 words;
+    const u64* idx;
+    u64* out;
+};
+
+// One thread per (query, word): the coset values of each layer's leaf, then
+// the leaf's siblings up to the cap (level j starts at word 8L - 8L/2^j).
+__global__ void k_fri_query(QueryArgs p)
+{
+    const u64 total = (u64)p.nq * p.words;
+    for (u64 g = blockIdx.x * (u64)blockDim.x + threadIdx.x; g < total; g += (u64)gridDim.x * blockDim.x) {
+        u64 q = g / p.words, o = g - q * p.words;
+        u32 k = 0;
+        while (k + 1 < p.R && p.L[k + 1].word0 <= o) k++;
+        const QueryLayer& L = p.L[k];
+        u64 off = o - L.word0;
+        u64 leaf = (p.idx[q] >> L.tshift) >> L.a;
+        u64 val;
+        if (off < ((u64)1 << L.a)) {
+            val = L.f[(leaf << L.a) + off];
+        } else {
+            off -= (u64)1 << L.a;
+            u32 lvl = (u32)(off >> 2), comp = (u32)(off & 3);
+            u64 eightL = (u64)8 << L.logL;
+            val = L.tree[(eightL - (eightL >> lvl)) + 4 * ((leaf >> lvl) ^ 1) + comp];
+        }
+        p.out[g] = val;
+    }
+}
+
+// Rows and authentication paths of a list of leaves of one commitment.
+__global__ void k_open_rows(const u64* __restrict__ lde, u32 ld, u32 c, const u64* __restrict__ tree, u32 log_N,
+                            u32 h, const u64* __restrict__ idx, u32 nq, u64* __restrict__ rows_out,
+                            u64* __restrict__ paths_out)
+{
+    const u32 plen = 4 * (log_N - h);
+    const u64 per = (u64)c + plen;
+    const u64 total = per * nq;
+    for (u64 g = blockIdx.x * (u64)blockDim.x + threadIdx.x; g < total; g += (u64)gridDim.x * blockDim.x) {
+        u64 q = g / per, o = g - q * per;
+        u64 t = idx[q];
+        if (o < c) {
+            if (rows_out) rows_out[q * c + o] = lde[t * ld + o];
+        } else if (paths_out) {
+            o -= c;
+            u32 lvl = (u32)(o >> 2), comp = (u32)(o & 3);
+            u64 eightN = (u64)8 << log_N;
+            paths_out[q * plen + o] = tree[(eightN - (eightN >> lvl)) + 4 * ((t >> lvl) ^ 1) + comp];
+        }
+    }
+}
+
+}  // namespace v3c
+
+using namespace v3c::detail;
+
+namespace {
+
+int grid_for(u64 work, int threads)
+{
+    u64 g = (work + threads - 1) / threads;
+    return (int)std::max<u64>(1, std::min<u64>(g, (u64)num_sms() * 16));
+}
+
+// Enqueues round k's fold: f_{k+1} from f_k with challenge beta.
+v3c_status launch_fold(v3c_ctx* ctx, FriState& st, u32 k, u64 beta, cudaStream_t s)
+{
+    const u32 a = st.arity[k];
+    FoldArgs p;
+    memset(&p, 0, sizeof p);
+    p.in = st.f[k];
+    p.out = st.f[k + 1];
+    p.pw_inv = st.pw_inv;
+    p.log_out = st.log_size[k + 1];
+    p.exp_shift = st.log_N - st.log_size[k];
+    p.inv2 = gl::h_inv(2);
+    int kidx = 0;
+    u64 bm = beta, sm = st.shift[k];
+    for (u32 m = 0; m < a; m++) {
+        const u32 b = a - 1 - m;
+        const u64 base = gl::h_mul(bm, gl::h_inv(gl::h_mul(2, sm)));
+        const u64 rinv = gl::h_inv(gl::h_root(b + 1));
+        for (u32 vp = 0; vp < (1u << b); vp++)
+            p.K[kidx + vp] = gl::h_mul(base, gl::h_pow(rinv, gl::bitrev(vp, b)));
+        kidx += 1 << b;
+        bm = gl::h_mul(bm, bm);
+        sm = gl::h_mul(sm, sm);
+    }
+    const int threads = 256;
+    const int grid = grid_for((u64)1 << p.log_out, threads);
+    StageTimer tm(ctx, 6, s);
+    switch (a) {
+    case 1: k_fri_fold<1><<<grid, threads, 0, s>>>(p); break;
+    case 2: k_fri_fold<2><<<grid, threads, 0, s>>>(p); break;
+    case 3: k_fri_fold<3><<<grid, threads, 0, s>>>(p); break;
+    default: k_fri_fold<4><<<grid, threads, 0, s>>>(p); break;
+    }
+    CK(cudaGetLastError());
+    tm.done();
+    ctx->launches++;
+    return V3C_OK;
+}
+
+v3c_status launch_final(v3c_ctx* ctx, FriState& st, cudaStream_t s)
+{
+    const u32 logm = st.log_size[st.rounds];
+    const u64 winv = gl::h_inv(gl::h_root(logm));
+    const u64 sinv = gl::h_inv(st.shift[st.rounds]);
+    const u64 minv = gl::h_inv((u64)1 << logm);
+    StageTimer tm(ctx, 6, s);
+    k_fri_final<<<1, 256, 0, s>>>(st.f[st.rounds], logm, winv, sinv, minv, st.final_coef);
+    CK(cudaGetLastError());
+    tm.done();
+    ctx->launches++;
+    return V3C_OK;
+}
+
+// Tree of every layer that exists and is below R but not committed yet, in
+// one batched leaf-hash / Merkle launch sequence.
+v3c_status commit_layers(v3c_ctx* ctx, FriState& st, cudaStream_t s)
+{
+    Batch b;
+    u32 upto = std::min(st.done + 1, st.rounds);
+    for (u32 k = st.committed; k < upto; k++) {
+        TreeJob t;
+        memset(&t, 0, sizeof t);
+        t.rows = st.f[k];
+        t.ld = t.width = 1u << st.arity[k];
+        t.log_N = st.log_size[k] - st.arity[k];
+        t.h = st.h[k];
+        t.tree = st.tree[k];
+        t.cap = st.cap[k];
+        t.vec_ok = ((uintptr_t)t.rows % 16 == 0) && (t.ld % 2 == 0);
+        b.tree.push_back(t);
+    }
+    if (b.tree.empty()) return V3C_OK;
+    v3c_status r = launch_batch(ctx, b, s);
+    if (r) return r;
+    st.committed = upto;
+    return V3C_OK;
+}
+
+// Applies the next n rounds, commits the new layers, and the final
+// coefficients once every round is done.  Caller holds ctx->mu.
+v3c_status advance(v3c_ctx* ctx, FriState& st, const uint64_t* betas, u32 n, cudaStream_t s)
+{
+    for (u32 i = 0; i < n; i++) {
+        if (betas[i] >= gl::P) return fail(ctx, V3C_EINVAL, "v3c_fri: beta %u not canonical", i);
+    }
+    for (u32 i = 0; i < n; i++) {
+        v3c_status r = launch_fold(ctx, st, st.done, betas[i], s);
+        if (r) return r;
+        st.done++;
+    }
+    v3c_status r = commit_layers(ctx, st, s);
+    if (r) return r;
+    if (st.done == st.rounds && n + (st.rounds == 0) > 0) {
+        r = launch_final(ctx, st, s);
+        if (r) return r;
+    }
+    CK(cudaEventRecord(st.ev, s));
+    return V3C_OK;
+}
+
+FriState* find_fri(v3c_ctx* ctx, v3c_fri_id id)
+{
+    auto it = ctx->fri.find(id);
+    return it == ctx->fri.end() ? nullptr : it->second;
+}
+
+cudaStream_t aux_stream(v3c_ctx* ctx)
+{
+    if (!ctx->release_stream) cudaStreamCreateWithFlags(&ctx->release_stream, cudaStreamNonBlocking);
+    return ctx->release_stream;
+}
+
+}  // namespace
+
+void fri_free_all(v3c_ctx* ctx)
+{
+    for (auto& kv : ctx->fri) {
+        FriState* st = kv.second;
+        if (st->mem) cudaFree(st->mem);
+        if (st->ev) cudaEventDestroy(st->ev);
+        delete st;
+    }
+    ctx->fri.clear();
+}
+
+extern "C" {
+
+v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids, uint64_t alpha,
+                         const v3c_fri_cfg* cfg, const uint64_t* h_betas, uint32_t n_betas, v3c_fri_id* out,
+                         void* stream)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (!ids || !n_ids || !cfg || !out || (n_betas && !h_betas))
+        return fail(ctx, V3C_EINVAL, "v3c_fri_begin: NULL argument or no commitments");
+    if (cfg->arity_bits < 1 || cfg->arity_bits > 4 || cfg->final_log > 10 || alpha >= gl::P)
+        return fail(ctx, V3C_EINVAL, "v3c_fri_begin: arity_bits %u, final_log %u or alpha out of range",
+                    cfg->arity_bits, cfg->final_log);
+    v3c_status r = use_device(ctx);
+    if (r) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    std::vector<Object> objs;
+    for (u32 i = 0; i < n_ids; i++) {
+        auto it = ctx->objects.find(ids[i]);
+        if (it == ctx->objects.end())
+            return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)ids[i]);
+        objs.push_back(it->second);
+    }
+    const u32 log_N = objs[0].log_n + objs[0].r;
+    u32 ncols = 0;
+    for (auto& o : objs) {
+        if (o.log_n + o.r != log_N) return fail(ctx, V3C_EINVAL, "v3c_fri_begin: commitments differ in row count");
+        ncols += o.c;
+    }
+    FriState* st = new FriState();
+    st->log_N = log_N;
+    st->ncols = ncols;
+    st->log_size[0] = log_N;
+    st->shift[0] = 7;
+    for (u32 m = log_N; m > cfg->final_log;) {
+        u32 a = std::min(cfg->arity_bits, m - cfg->final_log);
+        u32 k = st->rounds++;
+        st->arity[k] = a;
+        st->h[k] = std::min(cfg->cap_height, m - a);
+        m -= a;
+        st->log_size[k + 1] = m;
+        st->shift[k + 1] = gl::h_pow(st->shift[k], (u64)1 << a);
+    }
+    if (n_betas > st->rounds) {
+        delete st;
+        return fail(ctx, V3C_EINVAL, "v3c_fri_begin: %u betas for %u rounds", n_betas, st->rounds);
+    }
+    // One allocation: root tables, alpha powers, layers, trees, caps, final.
+    auto even = [](size_t w) { return (w + 1) & ~(size_t)1; };
+    size_t words = 1536 + even(ncols);
+    size_t off_f[V3C_FRI_MAX_ROUNDS + 1], off_t[V3C_FRI_MAX_ROUNDS], off_c[V3C_FRI_MAX_ROUNDS];
+    for (u32 k = 0; k <= st->rounds; k++) {
+        off_f[k] = words;
+        words += even((size_t)1 << st->log_size[k]);
+    }
+    st->query_words = 0;
+    for (u32 k = 0; k < st->rounds; k++) {
+        size_t L = (size_t)1 << (st->log_size[k] - st->arity[k]);
+        off_t[k] = words;
+        words += (2 * L - ((size_t)2 << st->h[k])) * 4;
+        off_c[k] = words;
+        words += (size_t)4 << st->h[k];
+        st->query_words += ((u64)1 << st->arity[k]) + 4 * (st->log_size[k] - st->arity[k] - st->h[k]);
+    }
+    size_t off_final = words;
+    words += even((size_t)1 << st->log_size[st->rounds]);
+    st->bytes = words * 8;
+    if (ctx->resident + st->bytes > ctx->cfg.hbm_budget_bytes) {
+        size_t need = st->bytes;
+        delete st;
+        return fail(ctx, V3C_ENOMEM, "v3c_fri_begin: %zu bytes over the HBM budget", need);
+    }
+    cudaError_t e = cudaMallocAsync((void**)&st->mem, st->bytes, s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (st->mem) cudaFreeAsync(st->mem, s);
+        delete st;
+        return fail(ctx, V3C_ENOMEM, "v3c_fri_begin: allocation failed: %s", cudaGetErrorString(e));
+    }
+    u64* base = st->mem;
+    st->pw_inv = base;
+    st->alpha_pw = base + 1536;
+    for (u32 k = 0; k <= st->rounds; k++) st->f[k] = base + off_f[k];
+    for (u32 k = 0; k < st->rounds; k++) {
+        st->tree[k] = base + off_t[k];
+        st->cap[k] = base + off_c[k];
+    }
+    st->final_coef = base + off_final;
+    auto bail = [&](v3c_status code) {
+        cudaFreeAsync(st->mem, s);
+        cudaEventDestroy(st->ev);
+        delete st;
+        return code;
+    };
+#define CKB(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return bail(fail(ctx, V3C_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)));     \
+    } while (0)
+    for (auto& o : objs) CKB(cudaStreamWaitEvent(s, o.done, 0));
+    k_fri_root_tables<<<6, 256, 0, s>>>(gl::h_inv(gl::h_root(log_N)), log_N, st->pw_inv);
+    CKB(cudaGetLastError());
+    k_fri_powers<<<grid_for(ncols, 256), 256, 0, s>>>(alpha, ncols, st->alpha_pw);
+    CKB(cudaGetLastError());
+    ctx->launches += 2;
+    u32 e0 = 0;
+    const u64 N = (u64)1 << log_N;
+    for (size_t i = 0; i < objs.size(); i++) {
+        const Object& o = objs[i];
+        int nb = 0;
+        CKB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fri_combine, 256, 0));
+        int grid = (int)std::min<u64>((u64)std::max(nb, 1) * num_sms(), (N / 32 + 7) / 8);
+        StageTimer tm(ctx, 5, s);
+        k_fri_combine<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + e0, N, i > 0, st->f[0]);
+        CKB(cudaGetLastError());
+        tm.done();
+        ctx->launches++;
+        e0 += o.c;
+    }
+#undef CKB
+    st->id = ctx->next_id++;
+    r = advance(ctx, *st, h_betas, n_betas, s);
+    if (r) return bail(r);
+    ctx->resident += st->bytes;
+    ctx->fri[st->id] = st;
+    *out = st->id;
+    return V3C_OK;
+}
+
+v3c_status v3c_fri_fold(v3c_ctx* ctx, v3c_fri_id fri, const uint64_t* h_betas, uint32_t n_betas, void* stream)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (n_betas && !h_betas) return fail(ctx, V3C_EINVAL, "v3c_fri_fold: NULL betas");
+    v3c_status r = use_device(ctx);
+    if (r) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    FriState* st = find_fri(ctx, fri);
+    if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
+    if (n_betas > st->rounds - st->done)
+        return fail(ctx, V3C_EINVAL, "v3c_fri_fold: %u betas, %u rounds left", n_betas, st->rounds - st->done);
+    if (!n_betas) return V3C_OK;
+    CK(cudaStreamWaitEvent(s, st->ev, 0));
+    return advance(ctx, *st, h_betas, n_betas, s);
+}
+
+v3c_status v3c_fri_info(v3c_ctx* ctx, v3c_fri_id fri, v3c_fri_info_t* out)
+{
+    if (!ctx || !out) return V3C_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    FriState* st = find_fri(ctx, fri);
+    if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
+    memset(out, 0, sizeof *out);
+    out->rounds = st->rounds;
+    out->rounds_done = st->done;
+    out->log_N = st->log_N;
+    out->n_columns = st->ncols;
+    for (u32 k = 0; k < st->rounds; k++) {
+        out->arity_bits[k] = st->arity[k];
+        out->cap_height[k] = st->h[k];
+    }
+    for (u32 k = 0; k <= st->rounds; k++) out->log_size[k] = st->log_size[k];
+    out->query_words = st->query_words;
+    out->bytes = st->bytes;
+    return V3C_OK;
+}
+
+v3c_status v3c_fri_cap(v3c_ctx* ctx, v3c_fri_id fri, uint32_t layer, uint64_t* h_cap)
+{
+    if (!ctx || !h_cap) return V3C_EINVAL;
+    v3c_status r = use_device(ctx);
+    if (r) return r;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    FriState* st = find_fri(ctx, fri);
+    if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
+    if (layer >= st->committed) return fail(ctx, V3C_EINVAL, "v3c_fri_cap: layer %u is not committed", layer);
+    CK(cudaEventSynchronize(st->ev));
+    CK(cudaMemcpy(h_cap, st->cap[layer], ((size_t)4 << st->h[layer]) * 8, cudaMemcpyDeviceToHost));
+    return V3C_OK;
+}
+
+v3c_status v3c_fri_final(v3c_ctx* ctx, v3c_fri_id fri, uint64_t* h_coeffs)
+{
+    if (!ctx || !h_coeffs) return V3C_EINVAL;
+    v3c_status r = use_device(ctx);
+    if (r) return r;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    FriState* st = find_fri(ctx, fri);
+    if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
+    if (st->done != st->rounds) return fail(ctx, V3C_EINVAL, "v3c_fri_final: %u of %u rounds done", st->done, st->rounds);
+    CK(cudaEventSynchronize(st->ev));
+    CK(cudaMemcpy(h_coeffs, st->final_coef, ((size_t)1 << st->log_size[st->rounds]) * 8, cudaMemcpyDeviceToHost));
+    return V3C_OK;
+}
+
+v3c_status v3c_fri_query(v3c_ctx* ctx, v3c_fri_id fri, const uint64_t* h_idx, uint32_t nq, uint64_t* h_out)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (nq && (!h_idx || !h_out)) return fail(ctx, V3C_EINVAL, "v3c_fri_query: NULL argument");
+    v3c_status r = use_device(ctx);
+    if (r) return r;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    FriState* st = find_fri(ctx, fri);
+    if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
+    if (st->done != st->rounds) return fail(ctx, V3C_EINVAL, "v3c_fri_query: %u of %u rounds done", st->done, st->rounds);
+    for (u32 q = 0; q < nq; q++)
+        if (h_idx[q] >> st->log_N) return fail(ctx, V3C_EINVAL, "v3c_fri_query: index %u out of range", q);
+    if (!nq || !st->rounds) return V3C_OK;
+    cudaStream_t s = aux_stream(ctx);
+    if (!s) return fail(ctx, V3C_ECUDA, "v3c_fri_query: no stream");
+    QueryArgs p;
+    memset(&p, 0, sizeof p);
+    u64 w0 = 0;
+    u32 tsh = 0;
+    for (u32 k = 0; k < st->rounds; k++) {
+        QueryLayer& L = p.L[k];
+        L.f = st->f[k];
+        L.tree = st->tree[k];
+        L.word0 = w0;
+        L.a = st->arity[k];
+        L.logL = st->log_size[k] - st->arity[k];
+        L.h = st->h[k];
+        L.tshift = tsh;
+        w0 += ((u64)1 << L.a) + 4 * (L.logL - L.h);
+        tsh += L.a;
+    }
+    p.R = st->rounds;
+    p.nq = nq;
+    p.words = st->query_words;
+    size_t out_words = (size_t)nq * st->query_words;
+    u64* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, (nq + out_words) * 8, s));
+    p.idx = d;
+    p.out = d + nq;
+    CK(cudaStreamWaitEvent(s, st->ev, 0));
+    cudaError_t e = cudaMemcpyAsync(d, h_idx, (size_t)nq * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        StageTimer tm(ctx, 7, s);
+        k_fri_query<<<grid_for(out_words, 256), 256, 0, s>>>(p);
+        e = cudaGetLastError();
+        tm.done();
+        ctx->launches++;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, p.out, out_words * 8, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, V3C_ECUDA, "v3c_fri_query: %s", cudaGetErrorString(e));
+    return V3C_OK;
+}
+
+v3c_status v3c_fri_release(v3c_ctx* ctx, v3c_fri_id fri)
+{
+    if (!ctx) return V3C_EINVAL;
+    v3c_status r = use_device(ctx);
+    if (r) return r;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    FriState* st = find_fri(ctx, fri);
+    if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
+    ctx->fri.erase(fri);
+    cudaStream_t s = aux_stream(ctx);
+    if (!s) return fail(ctx, V3C_ECUDA, "v3c_fri_release: no stream");
+    CK(cudaStreamWaitEvent(s, st->ev, 0));
+    CK(cudaFreeAsync(st->mem, s));
+    CK(cudaEventDestroy(st->ev));
+    ctx->resident -= st->bytes;
+    delete st;
+    return V3C_OK;
+}
+
+v3c_status v3c_open_batch(v3c_ctx* ctx, v3c_commit_id id, const uint64_t* h_leaves, uint32_t nq, uint64_t* h_rows,
+                          uint64_t* h_paths)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (nq && !h_leaves) return fail(ctx, V3C_EINVAL, "v3c_open_batch: NULL leaves");
+    v3c_status r = use_device(ctx);
+    if (r) return r;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->objects.find(id);
+    if (it == ctx->objects.end()) return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)id);
+    const Object o = it->second;
+    const u32 log_N = o.log_n + o.r;
+    for (u32 q = 0; q < nq; q++)
+        if (h_leaves[q] >> log_N) return fail(ctx, V3C_EINVAL, "v3c_open_batch: leaf %u out of range", q);
+    if (!nq || (!h_rows && !h_paths)) return V3C_OK;
+    cudaStream_t s = aux_stream(ctx);
+    if (!s) return fail(ctx, V3C_ECUDA, "v3c_open_batch: no stream");
+    const size_t plen = 4 * (size_t)(log_N - o.h);
+    const size_t rows_w = (size_t)nq * o.c, paths_w = (size_t)nq * plen;
+    u64* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, (nq + rows_w + paths_w) * 8, s));
+    u64* d_rows = d + nq;
+    u64* d_paths = d_rows + rows_w;
+    CK(cudaStreamWaitEvent(s, o.done, 0));
+    cudaError_t e = cudaMemcpyAsync(d, h_leaves, (size_t)nq * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        StageTimer tm(ctx, 7, s);
+        k_open_rows<<<grid_for(rows_w + paths_w, 256), 256, 0, s>>>(o.lde, o.ld, o.c, o.tree, log_N, o.h, d, nq,
+                                                                    d_rows, plen ? d_paths : nullptr);
+        e = cudaGetLastError();
+        tm.done();
+        ctx->launches++;
+    }
+    if (e == cudaSuccess && h_rows) e = cudaMemcpyAsync(h_rows, d_rows, rows_w * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_paths && plen)
+        e = cudaMemcpyAsync(h_paths, d_paths, paths_w * 8, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, V3C_ECUDA, "v3c_open_batch: %s", cudaGetErrorString(e));
+    return V3C_OK;
+}
+
+}  // extern "C"

@@ -128,6 +128,22 @@ __device__ __forceinline__ u64 pow(u64 a, u64 e)
     return r;
 }
 
+// Host-side arithmetic for the planners (per-round constants, tables).
+inline u64 h_mul(u64 a, u64 b) { return (u64)((unsigned __int128)a * b % P); }
+inline u64 h_pow(u64 a, u64 e)
+{
+    u64 r = 1;
+    while (e) {
+        if (e & 1) r = h_mul(r, a);
+        a = h_mul(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+inline u64 h_inv(u64 a) { return h_pow(a, P - 2); }
+// w_m = 7^((p-1)/m) for m = 2^log_m (7 generates the multiplicative group).
+inline u64 h_root(u32 log_m) { return h_pow(7, (P - 1) >> log_m); }
+
 __host__ __device__ __forceinline__ u32 bitrev(u32 x, u32 bits)
 {
 #ifdef __CUDA_ARCH__

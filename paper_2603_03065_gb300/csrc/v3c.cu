@@ -15,12 +15,13 @@
 #include <vector>
 
 #include "../../include/v3c.h"
+#include "ctx.h"
 #include "internal.h"
 #include "serve.h"
 
 namespace v3c {
 
-static thread_local int g_dev_cache = -1;
+thread_local int g_dev_cache = -1;
 
 int num_sms()
 {
@@ -61,94 +62,9 @@ double now_s()
 
 using namespace v3c;
 
-// ---------------------------------------------------------------- context
-
-struct PlanEntry {
-    Plan plan;
-    u64* mem = nullptr;
-};
-
-// One captured instance of a batch signature (see launch_batch_graph).
-struct GraphInst {
-    cudaGraphExec_t exec = nullptr;
-    void* h_blob = nullptr;
-    void* d_blob = nullptr;
-    size_t bytes = 0;
-    cudaEvent_t done = nullptr;
-    uint32_t kernels = 0;
-};
-struct GraphSet {
-    std::vector<GraphInst> inst;
-    uint32_t next = 0;
-};
-constexpr uint32_t kGraphRing = 3;
-constexpr size_t kMaxGraphSets = 64;
-
-struct UploadSlot {
-    void* h = nullptr;
-    void* d = nullptr;
-    size_t cap = 0;
-    cudaEvent_t ev = nullptr;
-};
-
-struct Arena {
-    u64* mem = nullptr;
-    size_t words = 0;
-    cudaEvent_t ev = nullptr;
-    cudaStream_t last = nullptr;
-    bool used = false;
-};
-
-struct Object {
-    u64 id = 0;
-    u64* lde = nullptr;
-    u64* tree = nullptr;
-    u64* cap = nullptr;
-    u32 c = 0, ld = 0, log_n = 0, r = 0, h = 0;
-    size_t bytes = 0;
-    cudaEvent_t done = nullptr;
-    cudaStream_t stream = nullptr;
-};
-
-struct v3c_ctx {
-    int device = 0;
-    v3c_config cfg{};
-    std::mutex mu;
-    std::map<std::pair<u32, u32>, PlanEntry> plans;
-    Arena arena;
-    std::vector<UploadSlot> ring;
-    u32 ring_next = 0;
-    std::unordered_map<u64, Object> objects;
-    u64 next_id = 1;
-    size_t resident = 0;
-    std::atomic<u64> launches{0};
-    std::mutex err_mu;
-    std::string err;
-    Tiles tiles;
-    u32* d_flag = nullptr;
-    serve::Server* server = nullptr;
-    cudaStream_t release_stream = nullptr;  // orders frees of resident objects
-    // CUDA graphs of batch signatures, and the autotuner's per-shape choices
-    std::unordered_map<std::string, GraphSet> graphs;
-    std::unordered_map<std::string, int> graph_seen;
-    cudaStream_t capture_stream = nullptr;
-    std::atomic<u64> graph_replays{0};
-    std::map<std::pair<u32, u32>, TuneEntry> tuned;
-    // per-stage timing (V3C_FLAG_TIMING)
-    std::mutex tmu;
-    struct Pending {
-        int stage;
-        cudaEvent_t a, b;
-    };
-    std::vector<Pending> pending;
-    std::vector<cudaEvent_t> ev_pool;
-    double stage_ms[V3C_NUM_STAGES] = {0};
-    uint64_t stage_n[V3C_NUM_STAGES] = {0};
-};
-
 static thread_local std::string g_err_copy;
 
-static v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...)
+v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...)
 {
     if (ctx) {
         char buf[512];
@@ -162,15 +78,8 @@ static v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...)
     return s;
 }
 
-#define CK(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess)                                                                     \
-            return fail(ctx, V3C_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
-                        __FILE__, __LINE__);                                                       \
-    } while (0)
 
-static v3c_status use_device(v3c_ctx* ctx)
+v3c_status use_device(v3c_ctx* ctx)
 {
     if (g_dev_cache != ctx->device) {
         CK(cudaSetDevice(ctx->device));
@@ -181,6 +90,19 @@ static v3c_status use_device(v3c_ctx* ctx)
 
 namespace v3c {
 namespace detail {
+
+cudaEvent_t pool_event(v3c_ctx* ctx)
+{
+    std::lock_guard<std::mutex> g(ctx->tmu);
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
 
 // Plan tables of a shape, built once and kept.  Caller holds ctx->mu.
 v3c_status get_plan(v3c_ctx* ctx, u32 log_n, u32 r, cudaStream_t s, Plan* out)
@@ -275,95 +197,7 @@ v3c_status upload_done(v3c_ctx* ctx, u32 slot, cudaStream_t s)
 
 static void job_tiles(LdeJob& j) { lde_job_tiles(j); }
 
-// A batch of LDE jobs and tree jobs, launched as one persistent launch per
-// stage.  Builds the upload blob (jobs + stage item lists).
-struct Batch {
-    std::vector<LdeJob> lde;
-    std::vector<TreeJob> tree;
-    std::vector<u32> fa, fb, fc, fl;
-    std::vector<std::vector<u32>> fm;
-    size_t smem_a = 0, smem_b = 0, smem_c = 0;
-    u32 max_top = 0;
-
-    void finalize(const Tiles& t)
-    {
-        fa.assign(1, 0);
-        fb.assign(1, 0);
-        fc.assign(1, 0);
-        for (auto& j : lde) {
-            fa.push_back(fa.back() + stage_a_items(j, t));
-            fb.push_back(fb.back() + stage_b_items(j));
-            fc.push_back(fc.back() + stage_c_items(j, t));
-            smem_a = std::max(smem_a, stage_a_smem(j, t));
-            smem_b = std::max(smem_b, stage_b_smem(j));
-            smem_c = std::max(smem_c, stage_c_smem(j, t));
-        }
-        fl.assign(1, 0);
-        max_top = 0;
-        for (auto& j : tree) {
-            fl.push_back(fl.back() + leaf_items(j, t));
-            max_top = std::max(max_top, j.log_N - j.h);
-        }
-        // Merkle launches: one per level while the level has enough nodes to
-        // fill the GPU with one compression per thread, then one launch that
-        // folds up to 8 levels per CTA in shared memory.
-        fm.clear();
-        mgroups.clear();
-        for (u32 lev0 = 0; lev0 < max_top;) {
-            u64 nodes = 0;
-            for (auto& j : tree)
-                if (j.log_N - j.h > lev0) nodes += (u64)1 << (j.log_N - lev0 - 1);
-            u32 nlev = nodes >= ((u64)1 << 17) ? 1 : 8;
-            std::vector<u32> f(1, 0);
-            for (auto& j : tree) f.push_back(f.back() + merkle_items(j, lev0, t));
-            fm.push_back(f);
-            mgroups.push_back({lev0, nlev});
-            lev0 += nlev;
-        }
-    }
-    std::vector<std::pair<u32, u32>> mgroups;  // (first level, levels) of each Merkle launch
-    u32 h_threads = 0;                          // leaf-hash CTA size (0 = context default)
-};
-
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-static cudaEvent_t pool_event(v3c_ctx* ctx)
-{
-    std::lock_guard<std::mutex> g(ctx->tmu);
-    if (!ctx->ev_pool.empty()) {
-        cudaEvent_t e = ctx->ev_pool.back();
-        ctx->ev_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-}
-
-// Brackets one stage launch with events on its stream when timing is on.
-struct StageTimer {
-    v3c_ctx* ctx;
-    int stage;
-    cudaStream_t s;
-    cudaEvent_t a = nullptr;
-    StageTimer(v3c_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str)
-    {
-        if ((ctx->cfg.flags & V3C_FLAG_TIMING) && st >= 0) {
-            a = pool_event(ctx);
-            if (a) cudaEventRecord(a, s);
-        }
-    }
-    void done()
-    {
-        if (!a) return;
-        cudaEvent_t b = pool_event(ctx);
-        if (!b) return;
-        cudaEventRecord(b, s);
-        std::lock_guard<std::mutex> g(ctx->tmu);
-        ctx->pending.push_back({stage, a, b});
-        a = nullptr;
-    }
-};
 
 // Job table + stage item lists of a batch, packed into one upload.
 // Layout: LdeJob[], TreeJob[], fa, fb, fc, fl, fm[...], 16-byte aligned parts.
@@ -807,6 +641,7 @@ v3c_status v3c_destroy(v3c_ctx* ctx)
     v3c_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    fri_free_all(ctx);
     for (auto& kv : ctx->objects) {
         cudaFree(kv.second.lde);
         cudaFree(kv.second.tree);

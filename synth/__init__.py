@@ -110,6 +110,14 @@ def columns(seed: int, c: int, log_n: int, batch: int = 0, mix: str = "trace") -
     return out
 
 
+def challenges(seed: int, count: int) -> list[int]:
+    """Verifier challenges (FRI alpha, betas, query positions are drawn by the
+    caller from these): the first ``count`` canonical nonzero draws of the
+    stream of (seed, batch 0xFFFFFFFF, column 0)."""
+    st = stream_state(seed, 0xFFFFFFFF, 0)
+    return [int(v) for v in _filtered(st, count, lambda d: (d < np.uint64(P)) & (d != np.uint64(0)))]
+
+
 def uniform_int(state: int, k: int) -> tuple[int, int]:
     """Unbiased integer in [0, k) by rejection from a SplitMix64 stream."""
     limit = ((1 << 64) // k) * k
