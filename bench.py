@@ -153,6 +153,8 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "fri_135x2_20":
+        return run_reference_fri(args)
     import oracle
 
     s = CPU_SAMPLE
@@ -175,6 +177,25 @@ def run_reference(args):
                          "sample": f"oracle commit of {s.c} x 2^{s.log_n} rows per step (bounded sample of the "
                                    f"{args.workload} workload's column mix)"},
         "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_fri(args):
+    s = FRI_CPU_SAMPLE
+    for _ in range(max(args.warmup - 1, 0)):
+        fri_cpu_baseline(s, 1)
+    base = fri_cpu_baseline(s, args.steps)
+    line = {
+        "impl": "reference", "metric": FRI_METRIC, "value": base["value"], "unit": "Gelem/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "fri_135x2_20", "columns": 135, "log_rows": 20, "rate_bits": 3,
+                   "arity_bits": FRI_CFG[0], "final_log": FRI_CFG[1], "layer_cap_height": FRI_CFG[2],
+                   "queries": FRI_QUERIES},
+        "cpu_baseline": {k: base[k] for k in ("kind", "cores", "value", "unit", "sample")},
+        "e2e": {"value": base["value"], "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
@@ -471,13 +492,183 @@ def run_serving(args):
     return 0
 
 
+FRI_METRIC = "FRI commit phase on the resident LDE: combined LDE elements Gelem/s"
+FRI_QUERIES = 28      # Plonky2's default number of query rounds
+FRI_CFG = (4, 5, 4)   # arity 2^4, final polynomial 2^5 values, cap height 4 per layer
+# DRAM traffic of one k_fri_combine launch on the 135 x 2^20 workload, from an
+# ncu capture of the same kernel.  Drop the entry when the kernel changes.
+FRI_COMBINE_TRAFFIC = {}
+
+
+def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
+    """The oracle's commit phase (combine, folds, layer trees, final
+    polynomial) and 28 query openings on the LDE of a bounded sample."""
+    import oracle
+
+    x = s.inputs()
+    threads = oracle.default_threads()
+    e = oracle.lde(x, s.rate_bits, threads=threads)
+    ch = synth.challenges(7, 32)
+    nr = len(oracle.fri_arities(s.log_N, FRI_CFG[0], FRI_CFG[1]))
+    idx = np.array(ch[-FRI_QUERIES:], dtype=np.uint64) % np.uint64(1 << s.log_N)
+
+    def one():
+        st = oracle.fri_commit([e], [s.c], ch[0], ch[1:1 + nr], *FRI_CFG, threads=threads)
+        for t in idx:
+            oracle.fri_query(st, int(t))
+
+    one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": s.lde_elems() / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
+            "sample": f"oracle FRI commit phase (arity 16, final 2^5, cap 4) + {FRI_QUERIES} query openings on "
+                      f"the LDE of {s.c} columns x 2^{s.log_n} rows, rate_bits {s.rate_bits}; {dt:.2f} s per step",
+            "ms_per_step": dt * 1e3}
+
+
+def run_fri(args):
+    """FRI commit phase on a resident commitment of the 135 x 2^20 trace
+    workload: combination of the 135 LDE columns with powers of alpha, folds
+    of arity 16 down to 2^5 values, every layer's Merkle tree, the final
+    coefficients; then 28 query openings and the 28 initial-row openings.
+    Not the default bench line; see the design doc."""
+    import torch
+
+    import paper_2603_03065_gb300 as v3c
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    s = shard_workload(synth.LARGE_135x2_20, rank)
+    ctx = v3c.Context(local_rank, flags=v3c.FLAG_TIMING)
+    stream = torch.cuda.current_stream()
+    cid = ctx.commit([(v3c.to_device_u64(s.inputs()), s.rate_bits, s.cap_height)], stream=stream)[0]
+    ch = synth.challenges(7 + rank, 64)
+    alpha = ch[0]
+    a, fl, h = FRI_CFG
+    fid = ctx.fri_begin([cid], alpha, a, fl, h)
+    info = ctx.fri_info(fid)
+    ctx.fri_release(fid)
+    nr = info["rounds"]
+    betas = ch[1:1 + nr]
+    idx = np.array(ch[-FRI_QUERIES:], dtype=np.uint64) % np.uint64(1 << s.log_N)
+
+    def commit_phase():
+        return ctx.fri_begin([cid], alpha, a, fl, h, betas=betas, stream=stream)
+
+    for _ in range(max(args.warmup, 1)):
+        ctx.fri_release(commit_phase())
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    ctx.stage_stats(reset=True)
+    l0 = ctx.kernel_launches()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.fri_release(commit_phase())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    launches = ctx.kernel_launches() - l0
+    stats = ctx.stage_stats(reset=True)
+    value = world * s.lde_elems() / (ms * 1e-3) / 1e9
+
+    # End to end through the public calls: commit phase, layer caps and final
+    # polynomial to the host, the query openings and the initial rows.
+    def step_e2e():
+        fid = commit_phase()
+        caps = [ctx.fri_cap(fid, k) for k in range(nr)]
+        fin = ctx.fri_final(fid)
+        recs = ctx.fri_query(fid, idx)
+        rows, paths = ctx.open_batch(cid, idx, s.c)
+        ctx.fri_release(fid)
+        return caps, fin, recs, rows, paths
+
+    out = step_e2e()
+    d2h = sum(c.nbytes for c in out[0]) + out[1].nbytes + out[2].nbytes + out[3].nbytes + out[4].nbytes
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+
+    comb_ms, comb_n = stats["fri_combine"]
+    comb_per = comb_ms / max(comb_n, 1)
+    N = 1 << s.log_N
+    comb_bytes = N * s.ld * 8 + N * 8   # every LDE row once (pad column included), f_0 written
+    achieved = comb_bytes / (comb_per * 1e-3) / 1e9
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    stage_ms = {k: (v[0] / v[1], int(v[1])) for k, v in stats.items() if v[1]}
+    if rank == 0:
+        line = {
+            "metric": FRI_METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "fri_135x2_20", "columns": s.c, "log_rows": s.log_n,
+                       "rate_bits": s.rate_bits, "lde_rows": N, "arity_bits": a, "final_log": fl,
+                       "layer_cap_height": h, "rounds": nr, "queries": FRI_QUERIES,
+                       "l2": "inputs larger than L2 (no flush needed)"},
+            "e2e": {"value": world * s.lde_elems() / e2e_s / 1e9, "unit": "Gelem/s",
+                    "h2d_bytes_per_step": int(2 * idx.nbytes + 8 * len(betas)), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": {"bound": "hbm", "kernel": "k_fri_combine", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": FRI_COMBINE_TRAFFIC.get("fri_135x2_20"),
+                         "bytes_per_launch": comb_bytes, "ms_per_launch": comb_per, "peak_source": "measured"},
+            "stages_ms_per_launch": stage_ms,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = fri_cpu_baseline(FRI_CPU_SAMPLE)
+        print(json.dumps(line))
+    ctx.release(cid)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+FRI_CPU_SAMPLE = synth.Shape(c=135, log_n=16, rate_bits=3, cap_height=4, seed=0)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["v3c", "reference"], default="v3c")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven_64", "serve_poisson"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven_64", "serve_poisson", "fri_135x2_20"],
                     default="large_135x2_20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--int-peak", action="store_true", help="also run the integer-pipe microbenchmark")
@@ -492,6 +683,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve_poisson":
         return run_serving(args)
+    if args.workload == "fri_135x2_20":
+        return run_fri(args)
     return run_v3c(args)
 
 

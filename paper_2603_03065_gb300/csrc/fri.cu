@@ -9,9 +9,10 @@
 // with the same Poseidon Merkle kernels as the LDE.
 //
 // GB300 mapping: the combination streams the whole resident LDE once (the
-// only HBM-heavy step) with one warp per 32 rows and 16-byte loads across
-// each row.  A fold reads each coset (2^a contiguous values) into registers
-// and applies a arity-2 steps there, one output per thread.  The layer
+// only HBM-heavy step), one thread per row, 64-byte runs per load group and
+// an unreduced 192-bit sum per row.  A fold reads each coset (2^a
+// contiguous values) into registers and applies a arity-2 steps there, one
+// output per thread.  The layer
 // trees go through the batched leaf-hash and Merkle launches.  Openings are
 // one gather launch per call over every (query, word) pair.
 #include <cuda_runtime.h>
@@ -75,36 +76,63 @@ __device__ __forceinline__ u64 pow3(const u64* __restrict__ pw, u64 e)
     return gl::mul(r, __ldg(pw + 1024 + (e >> 18)));
 }
 
-// f[t] (+)= sum_{i<c} pw[i] row_t[i].  A warp takes 32 consecutive rows; lane
-// l reads the column pairs (2l + 64j, 2l + 1 + 64j) of each row with 16-byte
-// loads (ld even, rows 16-byte aligned), the warp sums the lanes, and lane j
-// keeps row j's value for one coalesced store.
+// (lo, mid, hi) += a * b: a 64x64 -> 128-bit product added into a 192-bit
+// accumulator whose top word counts the carries (at most one per product).
+__device__ __forceinline__ void mac192(u64& lo, u64& mid, u32& hi, u64 a, u64 b)
+{
+    asm("{\n\t"
+        ".reg .u64 pl, ph;\n\t"
+        "mul.lo.u64 pl, %3, %4;\n\t"
+        "mul.hi.u64 ph, %3, %4;\n\t"
+        "add.cc.u64 %0, %0, pl;\n\t"
+        "addc.cc.u64 %1, %1, ph;\n\t"
+        "addc.u32 %2, %2, 0;\n\t"
+        "}"
+        : "+l"(lo), "+l"(mid), "+r"(hi)
+        : "l"(a), "l"(b));
+}
+
+// The accumulator's value lo + mid 2^64 + hi 2^128 mod p.  With 2^64 = 2^32 - 1
+// and 2^128 = (2^32 - 1)^2 = 2^64 - 2^33 + 1 = -2^32 (mod p), it is
+// reduce(lo + mid 2^64) - hi 2^32, and hi 2^32 < 2^63 < p for hi < 2^31.
+__device__ __forceinline__ u64 fold192(u64 lo, u64 mid, u32 hi)
+{
+    return gl::sub(gl::canon(gl::reduce128_ptx(lo, mid)), (u64)hi << 32);
+}
+
+// f[t] (+)= sum_{i<c} pw[i] row_t[i].  One thread per row: 16-byte loads of
+// column pairs, four pairs (one 64-byte run, two whole sectors) per
+// iteration, products summed unreduced and reduced once per row.  The
+// powers pw[i] are the same for every thread of a warp (broadcast loads).
+// Rows are 16-byte aligned (ld even); c < 2^31.
 __global__ void __launch_bounds__(256) k_fri_combine(const u64* __restrict__ rows, u32 ld, u32 c,
                                                      const u64* __restrict__ pw, u64 nrows, int acc,
                                                      u64* __restrict__ f)
 {
-    const u32 lane = threadIdx.x & 31;
-    const u64 warp = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5;
-    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-    for (u64 t0 = warp * 32; t0 < nrows; t0 += nwarps * 32) {
-        const u32 cnt = (u32)min((u64)32, nrows - t0);
-        u64 mine = 0;
-        for (u32 j = 0; j < cnt; j++) {
-            const u64* row = rows + (t0 + j) * ld;
-            u64 s = 0;
-            for (u32 i = 2 * lane; i < c; i += 64) {
-                ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(row + i));
-                s = gl::add(s, gl::mul(v.x, __ldg(pw + i)));
-                if (i + 1 < c) s = gl::add(s, gl::mul(v.y, __ldg(pw + i + 1)));
-            }
+    const u32 pairs = c >> 1;
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < nrows; t += (u64)gridDim.x * blockDim.x) {
+        const ulonglong2* row = reinterpret_cast<const ulonglong2*>(rows + t * ld);
+        u64 lo = 0, mid = 0;
+        u32 hi = 0;
+        u32 k = 0;
+        for (; k + 4 <= pairs; k += 4) {
+            ulonglong2 v[4];
 #pragma unroll
-            for (int o = 16; o; o >>= 1) s = gl::add(s, __shfl_xor_sync(0xffffffffu, s, o));
-            if (lane == j) mine = s;
+            for (int j = 0; j < 4; j++) v[j] = __ldg(row + k + j);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                mac192(lo, mid, hi, v[j].x, __ldg(pw + 2 * (k + j)));
+                mac192(lo, mid, hi, v[j].y, __ldg(pw + 2 * (k + j) + 1));
+            }
         }
-        if (lane < cnt) {
-            u64* d = f + t0 + lane;
-            *d = acc ? gl::add(*d, mine) : mine;
+        for (; k < pairs; k++) {
+            ulonglong2 v = __ldg(row + k);
+            mac192(lo, mid, hi, v.x, __ldg(pw + 2 * k));
+            mac192(lo, mid, hi, v.y, __ldg(pw + 2 * k + 1));
         }
+        if (c & 1) mac192(lo, mid, hi, __ldg(rows + t * ld + c - 1), __ldg(pw + c - 1));
+        u64 r = fold192(lo, mid, hi);
+        f[t] = acc ? gl::add(f[t], r) : r;
     }
 }
 
@@ -489,7 +517,7 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
         const Object& o = objs[i];
         int nb = 0;
         CKB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fri_combine, 256, 0));
-        int grid = (int)std::min<u64>((u64)std::max(nb, 1) * num_sms(), (N / 32 + 7) / 8);
+        int grid = (int)std::min<u64>((u64)std::max(nb, 1) * num_sms(), (N + 255) / 256);
         StageTimer tm(ctx, 5, s);
         k_fri_combine<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + e0, N, i > 0, st->f[0]);
         CKB(cudaGetLastError());
