@@ -74,6 +74,9 @@ def lib():
                 "orc_fri_fold_coset": (u64, [_u64p, u32, u64, u32, u64, u64]),
                 "orc_fri_fold": (i32, [_u64p, u32, u64, u32, u64, _u64p, i32]),
                 "orc_fri_interpolate": (i32, [_u64p, u32, u64, _u64p]),
+                "orc_snapshot_slot_leaves": (i32, [_u64p, u32, u32, u32, _u64p, i32]),
+                "orc_snapshot_commit": (i32, [_u64p, u32, u32, u32, _u64p, u32, _u64p, u32, u32, _u64p, _u64p,
+                                              _u64p, _u64p, i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -385,3 +388,30 @@ def fri_verify_query(caps, heights, arities, betas, final, log_N: int, t0: int, 
     for c in reversed([int(v) for v in final]):
         acc = add(mul(acc, x), c)
     return acc == value
+
+
+# --- snapshot commitment (Sec. 4.3) ----------------------------------------
+def snapshot_slot_leaves(records, log_nlist: int, log_n: int, threads: int | None = None) -> np.ndarray:
+    r = _u64(records)
+    N = 1 << (log_nlist + log_n)
+    M = r.shape[1] - 2
+    out = np.empty((N, 4), np.uint64)
+    assert lib().orc_snapshot_slot_leaves(_p(r), 1 << log_nlist, 1 << log_n, M, _p(out),
+                                          threads or default_threads()) == 0
+    return out
+
+
+def snapshot_commit(records, mu, codebooks, log_nlist: int, log_n: int, threads: int | None = None) -> dict:
+    """Returns list roots [nlist][4], centroid digests [nlist][4], root_mk, root_cb."""
+    r, m, cb = _u64(records), _u64(mu), _u64(codebooks)
+    nlist = 1 << log_nlist
+    M = r.shape[1] - 2
+    D = m.shape[1]
+    Mc, K, d = cb.shape
+    roots = np.empty((nlist, 4), np.uint64)
+    cent = np.empty((nlist, 4), np.uint64)
+    mk = np.empty(4, np.uint64)
+    cbr = np.empty(4, np.uint64)
+    assert lib().orc_snapshot_commit(_p(r), log_nlist, log_n, M, _p(m), D, _p(cb), K, d, _p(roots), _p(cent),
+                                     _p(mk), _p(cbr), threads or default_threads()) == 0
+    return {"list_roots": roots, "centroid_digests": cent, "root_mk": mk, "root_cb": cbr}

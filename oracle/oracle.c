@@ -745,3 +745,116 @@ int orc_fri_interpolate(const u64* f, uint32_t logm, u64 shift, u64* coeffs)
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Snapshot commitment (Sec. 4.3, "Snapshot Commitments"):             */
+/*   hash_{i,j} = Hash(i, j, f_{i,j}, item_{i,j}, v_{i,j}^(0..M-1)),     */
+/*   root_i     = MerkleTree(hash_{i,0}, ..., hash_{i,n-1}),            */
+/*   hash_i     = Hash(i, mu_i[0..D), root_i),                          */
+/*   root_mk    = MerkleTree(hash_0, ..., hash_{nlist-1}),              */
+/*   root_cb    = Hash(C_{0,0}, ..., C_{M-1,K-1}) (each C_{m,k} in F^d). */
+/* Hash is the Poseidon sponge above; MerkleTree takes the digests as   */
+/* its leaves and compresses pairs up to one root.  A slot record is     */
+/* stored as [f, item, v^(0), ..., v^(M-1)] (2 + M field elements).      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const u64* rec;
+    uint32_t n, M;
+    u64* out;
+} slot_ctx;
+static void slot_body(void* vctx, size_t t)
+{
+    slot_ctx* S = (slot_ctx*)vctx;
+    u64 in[2 + 2 + 256];
+    in[0] = (u64)(t / S->n); /* i */
+    in[1] = (u64)(t % S->n); /* j */
+    memcpy(in + 2, S->rec + t * (2 + (size_t)S->M), (2 + (size_t)S->M) * sizeof(u64));
+    orc_hash(in, 4 + S->M, S->out + 4 * t);
+}
+
+typedef struct {
+    const u64* mu;
+    const u64* roots;
+    uint32_t D;
+    u64* out;
+    u64* buf;
+} cent_ctx;
+static void cent_body(void* vctx, size_t i)
+{
+    cent_ctx* C = (cent_ctx*)vctx;
+    size_t L = 1 + (size_t)C->D + 4;
+    u64* in = (u64*)malloc(L * sizeof(u64));
+    in[0] = (u64)i;
+    memcpy(in + 1, C->mu + i * C->D, (size_t)C->D * sizeof(u64));
+    memcpy(in + 1 + C->D, C->roots + 4 * i, 4 * sizeof(u64));
+    orc_hash(in, (uint32_t)L, C->out + 4 * i);
+    free(in);
+}
+
+/* Root of the Merkle tree whose 2^log_leaves leaves are the given digests. */
+static int digest_tree_root(const u64* leaves, uint32_t log_leaves, u64* root, int threads)
+{
+    size_t cnt = (size_t)1 << log_leaves;
+    u64* level = (u64*)malloc(cnt * 4 * sizeof(u64));
+    if (!level) return -1;
+    memcpy(level, leaves, cnt * 4 * sizeof(u64));
+    while (cnt > 1) {
+        u64* next = (u64*)malloc((cnt / 2) * 4 * sizeof(u64));
+        if (!next) {
+            free(level);
+            return -1;
+        }
+        orc_merkle_level(level, cnt / 2, next, threads);
+        free(level);
+        level = next;
+        cnt /= 2;
+    }
+    memcpy(root, level, 4 * sizeof(u64));
+    free(level);
+    return 0;
+}
+
+typedef struct {
+    const u64* leaves;
+    uint32_t log_n;
+    u64* roots;
+    int failed;
+} list_ctx;
+/* root_i of one list: its own tree, built serially (lists run in parallel). */
+static void list_body(void* vctx, size_t i)
+{
+    list_ctx* L = (list_ctx*)vctx;
+    if (digest_tree_root(L->leaves + (i << L->log_n) * 4, L->log_n, L->roots + 4 * i, 1)) L->failed = 1;
+}
+
+/* Slot leaf digests [nlist * n][4] (list-major). */
+int orc_snapshot_slot_leaves(const u64* records, uint32_t nlist, uint32_t n, uint32_t M, u64* out, int threads)
+{
+    if (!params() || M > 256) return -1;
+    slot_ctx S = {records, n, M, out};
+    parallel_for((size_t)nlist * n, threads, slot_body, &S);
+    return 0;
+}
+
+/* list_roots [nlist][4], centroid digests [nlist][4], root_mk [4], root_cb [4].
+ * nlist and n are powers of two. */
+int orc_snapshot_commit(const u64* records, uint32_t log_nlist, uint32_t log_n, uint32_t M, const u64* mu,
+                        uint32_t D, const u64* codebooks, uint32_t K, uint32_t d, u64* list_roots,
+                        u64* cent_digests, u64* root_mk, u64* root_cb, int threads)
+{
+    if (!params() || M > 256) return -1;
+    size_t nlist = (size_t)1 << log_nlist, n = (size_t)1 << log_n;
+    u64* leaves = (u64*)malloc(nlist * n * 4 * sizeof(u64));
+    if (!leaves) return -1;
+    orc_snapshot_slot_leaves(records, (uint32_t)nlist, (uint32_t)n, M, leaves, threads);
+    list_ctx Lc = {leaves, log_n, list_roots, 0};
+    parallel_for(nlist, threads, list_body, &Lc);
+    free(leaves);
+    if (Lc.failed) return -1;
+    cent_ctx C = {mu, list_roots, D, cent_digests, NULL};
+    parallel_for(nlist, threads, cent_body, &C);
+    if (digest_tree_root(cent_digests, log_nlist, root_mk, threads)) return -1;
+    orc_hash(codebooks, M * K * d, root_cb);
+    return 0;
+}

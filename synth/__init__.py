@@ -212,3 +212,36 @@ def poisson_trace(rate: float = 200.0, duration: float = 60.0, seed: int = 5) ->
         out.append(Request(t, Shape(c=c, log_n=log_n, rate_bits=3, cap_height=4, batch=i, seed=seed)))
         i += 1
     return out
+
+
+# --- IVF-PQ snapshots --------------------------------------------------------
+# A fixed-shape IVF-PQ snapshot: nlist lists of n slots, each slot a record
+# [f, item, v^(0), ..., v^(M-1)]; centroids mu [nlist][D]; PQ codebooks
+# [M][K][d], d = D / M.  Coordinates are 16-bit fixed point, the encoding
+# round((2^16 - 1) v / v_max) of real coordinates in [-v_max, v_max],
+# embedded in F_p (a negative x as p + x).  Padding slots (f = 0) hold zeros.
+SNAP_SIFT1M = dict(log_nlist=13, log_n=8, D=128, M=8, K=256, valid=1e6 / (1 << 21))
+SNAP_MSMARCO = dict(log_nlist=13, log_n=11, D=384, M=8, K=256, valid=8.8e6 / (1 << 24))
+
+
+def _fixed_point(state: int, count: int) -> np.ndarray:
+    span = np.uint64(2 * 65535 + 1)
+    u = draws(state, 0, count) % span           # x + 65535, x in [-65535, 65535]
+    neg = u < np.uint64(65535)
+    return np.where(neg, np.uint64(P - 65535) + u, u - np.uint64(65535))
+
+
+def snapshot(seed: int, log_nlist: int, log_n: int, D: int, M: int = 8, K: int = 256, valid: float = 0.5):
+    """(records [nlist * n][2 + M], mu [nlist][D], codebooks [M][K][D / M])."""
+    N = 1 << (log_nlist + log_n)
+    base = 0xFFFF0000
+    f = (draws(stream_state(seed, base, 0), 0, N) & np.uint64(0xFFFF)) < np.uint64(int(valid * 65536))
+    item = draws(stream_state(seed, base, 1), 0, N) & np.uint64(0xFFFFFFFF)
+    codes = (draws(stream_state(seed, base, 2), 0, N * M) & np.uint64(K - 1)).reshape(N, M)
+    rec = np.zeros((N, 2 + M), np.uint64)
+    rec[:, 0] = f.astype(np.uint64)
+    rec[:, 1] = np.where(f, item, 0)
+    rec[:, 2:] = np.where(f[:, None], codes, 0)
+    mu = _fixed_point(stream_state(seed, base, 3), (1 << log_nlist) * D).reshape(1 << log_nlist, D)
+    cb = _fixed_point(stream_state(seed, base, 4), M * K * (D // M)).reshape(M, K, D // M)
+    return rec, mu, cb
