@@ -75,6 +75,8 @@ def lib():
                 "orc_fri_fold": (i32, [_u64p, u32, u64, u32, u64, _u64p, i32]),
                 "orc_fri_interpolate": (i32, [_u64p, u32, u64, _u64p]),
                 "orc_snapshot_slot_leaves": (i32, [_u64p, u32, u32, u32, _u64p, i32]),
+                "orc_snapshot_list_root": (i32, [_u64p, u64, u32, u32, _u64p]),
+                "orc_snapshot_centroid_digest": (None, [u64, _u64p, u32, _u64p, _u64p]),
                 "orc_snapshot_commit": (i32, [_u64p, u32, u32, u32, _u64p, u32, _u64p, u32, u32, _u64p, _u64p,
                                               _u64p, _u64p, i32]),
             }
@@ -415,3 +417,18 @@ def snapshot_commit(records, mu, codebooks, log_nlist: int, log_n: int, threads:
     assert lib().orc_snapshot_commit(_p(r), log_nlist, log_n, M, _p(m), D, _p(cb), K, d, _p(roots), _p(cent),
                                      _p(mk), _p(cbr), threads or default_threads()) == 0
     return {"list_roots": roots, "centroid_digests": cent, "root_mk": mk, "root_cb": cbr}
+
+
+def snapshot_list_root(list_records, i: int, log_n: int) -> np.ndarray:
+    """root_i from the n records of list i alone."""
+    r = _u64(list_records)
+    out = np.empty(4, np.uint64)
+    assert lib().orc_snapshot_list_root(_p(r), i, log_n, r.shape[1] - 2, _p(out)) == 0
+    return out
+
+
+def snapshot_centroid_digest(i: int, mu_i, root_i) -> np.ndarray:
+    m, rt = _u64(mu_i), _u64(root_i)
+    out = np.empty(4, np.uint64)
+    lib().orc_snapshot_centroid_digest(i, _p(m), m.size, _p(rt), _p(out))
+    return out

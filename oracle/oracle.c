@@ -858,3 +858,33 @@ int orc_snapshot_commit(const u64* records, uint32_t log_nlist, uint32_t log_n, 
     orc_hash(codebooks, M * K * d, root_cb);
     return 0;
 }
+
+/* root_i of one list from its n = 2^log_n records, for list index i. */
+int orc_snapshot_list_root(const u64* list_records, uint64_t i, uint32_t log_n, uint32_t M, u64* root)
+{
+    if (!params() || M > 256) return -1;
+    size_t n = (size_t)1 << log_n;
+    u64* leaves = (u64*)malloc(n * 4 * sizeof(u64));
+    if (!leaves) return -1;
+    u64 in[2 + 2 + 256];
+    for (size_t j = 0; j < n; j++) {
+        in[0] = i;
+        in[1] = (u64)j;
+        memcpy(in + 2, list_records + j * (2 + (size_t)M), (2 + (size_t)M) * sizeof(u64));
+        orc_hash(in, 4 + M, leaves + 4 * j);
+    }
+    int rc = digest_tree_root(leaves, log_n, root, 1);
+    free(leaves);
+    return rc;
+}
+
+/* hash_i = Hash(i, mu_i, root_i). */
+void orc_snapshot_centroid_digest(uint64_t i, const u64* mu_i, uint32_t D, const u64* root_i, u64* out)
+{
+    u64* in = (u64*)malloc((1 + (size_t)D + 4) * sizeof(u64));
+    in[0] = i;
+    memcpy(in + 1, mu_i, (size_t)D * sizeof(u64));
+    memcpy(in + 1 + D, root_i, 4 * sizeof(u64));
+    orc_hash(in, 1 + D + 4, out);
+    free(in);
+}

@@ -75,6 +75,11 @@ class FriInfo(ctypes.Structure):
                 ("cap_height", _u32 * FRI_MAX_ROUNDS), ("query_words", _u64), ("bytes", _u64)]
 
 
+class SnapshotDesc(ctypes.Structure):
+    _fields_ = [("records", _vp), ("centroids", _vp), ("codebooks", _vp), ("on_device", ctypes.c_int32),
+                ("log_nlist", _u32), ("log_n", _u32), ("M", _u32), ("D", _u32), ("K", _u32), ("d", _u32)]
+
+
 class ReqTimes(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
                 ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
@@ -113,6 +118,12 @@ SIGNATURES = {
     "v3c_fri_query": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _u64p]),
     "v3c_fri_release": (ctypes.c_int, [_vp, _u64]),
     "v3c_open_batch": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _u64p, _u64p]),
+    # include/v3c_snapshot.h
+    "v3c_snapshot_commit": (ctypes.c_int, [_vp, ctypes.POINTER(SnapshotDesc), _u64p, _vp]),
+    "v3c_snapshot_roots": (ctypes.c_int, [_vp, _u64, _u64p, _u64p]),
+    "v3c_snapshot_list_roots": (ctypes.c_int, [_vp, _u64, _u64p]),
+    "v3c_snapshot_open_lists": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(_u32), _u32, _u64p]),
+    "v3c_snapshot_release": (ctypes.c_int, [_vp, _u64]),
 }
 
 _lib = None
@@ -422,6 +433,46 @@ class Context:
 
     def fri_release(self, fid: int):
         self._check(self.lib.v3c_fri_release(self.h, fid))
+
+    # --------------------------------------------------------------- snapshots
+    def snapshot_commit(self, records, centroids, codebooks, log_nlist: int, log_n: int, stream=None) -> int:
+        """records [nlist*n][2+M], centroids [nlist][D], codebooks [M][K][d]: all
+        uint64 numpy arrays (host, copied) or all int64 CUDA tensors (device)."""
+        on_dev = not isinstance(records, np.ndarray)
+        if on_dev:
+            ptrs = [records.data_ptr(), centroids.data_ptr(), codebooks.data_ptr()]
+            M, D = records.shape[1] - 2, centroids.shape[1]
+            _, K, d = codebooks.shape
+        else:
+            keep = [np.ascontiguousarray(a, dtype=np.uint64) for a in (records, centroids, codebooks)]
+            ptrs = [a.ctypes.data for a in keep]
+            M, D = keep[0].shape[1] - 2, keep[1].shape[1]
+            _, K, d = keep[2].shape
+        desc = SnapshotDesc(ptrs[0], ptrs[1], ptrs[2], INPUT_DEVICE if on_dev else INPUT_HOST_COPY, log_nlist, log_n,
+                            M, D, K, d)
+        out = _u64()
+        self._check(self.lib.v3c_snapshot_commit(self.h, ctypes.byref(desc), ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def snapshot_roots(self, sid: int) -> tuple[np.ndarray, np.ndarray]:
+        mk, cb = np.zeros(4, np.uint64), np.zeros(4, np.uint64)
+        self._check(self.lib.v3c_snapshot_roots(self.h, sid, mk.ctypes.data_as(_u64p), cb.ctypes.data_as(_u64p)))
+        return mk, cb
+
+    def snapshot_list_roots(self, sid: int, log_nlist: int) -> np.ndarray:
+        out = np.zeros((1 << log_nlist, 4), np.uint64)
+        self._check(self.lib.v3c_snapshot_list_roots(self.h, sid, out.ctypes.data_as(_u64p)))
+        return out
+
+    def snapshot_open_lists(self, sid: int, lists, log_nlist: int) -> np.ndarray:
+        idx = np.ascontiguousarray(lists, dtype=np.uint32)
+        out = np.zeros((idx.size, log_nlist, 4), np.uint64)
+        self._check(self.lib.v3c_snapshot_open_lists(self.h, sid, idx.ctypes.data_as(ctypes.POINTER(_u32)), idx.size,
+                                                     out.ctypes.data_as(_u64p)))
+        return out
+
+    def snapshot_release(self, sid: int):
+        self._check(self.lib.v3c_snapshot_release(self.h, sid))
 
     # --------------------------------------------------------------- misc
     def kernel_launches(self) -> int:

@@ -18,6 +18,7 @@ namespace serve {
 struct Server;
 }
 struct FriState;
+struct SnapState;
 extern thread_local int g_dev_cache;
 }  // namespace v3c
 
@@ -89,7 +90,8 @@ struct v3c_ctx {
     Tiles tiles;
     u32* d_flag = nullptr;
     serve::Server* server = nullptr;
-    std::unordered_map<u64, FriState*> fri;  // FRI commit-phase states (fri.cu)
+    std::unordered_map<u64, FriState*> fri;      // FRI commit-phase states (fri.cu)
+    std::unordered_map<u64, SnapState*> snaps;   // snapshot commitments (snapshot.cu)
     cudaStream_t release_stream = nullptr;  // orders frees of resident objects
     // CUDA graphs of batch signatures, and the autotuner's per-shape choices
     std::unordered_map<std::string, GraphSet> graphs;
@@ -116,6 +118,8 @@ v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...);
 v3c_status use_device(v3c_ctx* ctx);
 // Frees every FRI state of the context (fri.cu).
 void fri_free_all(v3c_ctx* ctx);
+// Frees every snapshot object of the context (snapshot.cu).
+void snap_free_all(v3c_ctx* ctx);
 
 #define CK(call)                                                                                   \
     do {                                                                                           \
@@ -176,6 +180,7 @@ struct Batch {
     }
     std::vector<std::pair<u32, u32>> mgroups;  // (first level, levels) of each Merkle launch
     u32 h_threads = 0;                          // leaf-hash CTA size (0 = context default)
+    bool leaves_ready = false;                  // level 0 of every tree is already written: no leaf hash
 };
 
 

@@ -262,11 +262,13 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
                    list(4, b.fc, nl), 0);
         if (st) return st;
     }
-    if (nt) {
+    if (nt && !b.leaves_ready) {
         st = stage(3, [](const Batch&, const Tiles& t, StageList l, const LdeJob*, const TreeJob* dt, size_t,
                          cudaStream_t s) { return launch_leaf_hash(dt, l, t, 0, s); },
                    list(5, b.fl, nt), 0);
         if (st) return st;
+    }
+    if (nt) {
         for (size_t g = 0; g < b.fm.size(); g++) {
             st = stage(4, [](const Batch& b, const Tiles& t, StageList l, const LdeJob*, const TreeJob* dt,
                              size_t g, cudaStream_t s) {
@@ -305,8 +307,8 @@ static std::string batch_signature(const Batch& b, const Tiles& t)
 {
     std::string k;
     char buf[96];
-    snprintf(buf, sizeof buf, "t%u.%u.%u.%u.%u|", t.a_threads, t.b_threads, t.c_threads, b.h_threads ? b.h_threads : t.h_threads,
-             t.m_threads);
+    snprintf(buf, sizeof buf, "t%u.%u.%u.%u.%u.%d|", t.a_threads, t.b_threads, t.c_threads,
+             b.h_threads ? b.h_threads : t.h_threads, t.m_threads, (int)b.leaves_ready);
     k += buf;
     for (auto& j : b.lde) {
         snprintf(buf, sizeof buf, "L%u.%u.%u.%u.%u.%u.%u.%u.%u|", j.c, j.ld, j.plan.log_n, j.plan.r, j.vec_ok, j.a_cols,
@@ -642,6 +644,7 @@ v3c_status v3c_destroy(v3c_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     fri_free_all(ctx);
+    snap_free_all(ctx);
     for (auto& kv : ctx->objects) {
         cudaFree(kv.second.lde);
         cudaFree(kv.second.tree);

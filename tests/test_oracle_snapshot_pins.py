@@ -42,6 +42,15 @@ def test_snapshot_matches_the_composed_equations():
     assert np.array_equal(st["root_cb"], cbr)
 
 
+def test_per_list_helpers_agree_with_the_whole_commit():
+    rec, mu, cb = synth.snapshot(16, 3, 3, 8, 2, 4)
+    st = oracle.snapshot_commit(rec, mu, cb, 3, 3)
+    for i in range(8):
+        root = oracle.snapshot_list_root(rec[i * 8:(i + 1) * 8], i, 3)
+        assert np.array_equal(root, st["list_roots"][i])
+        assert np.array_equal(oracle.snapshot_centroid_digest(i, mu[i], root), st["centroid_digests"][i])
+
+
 def test_single_list_and_single_slot_edges():
     # nlist = 1: root_mk is hash_0 itself; n = 1: root_i is the slot digest.
     rec, mu, cb = synth.snapshot(12, 0, 3, 8, 2, 4)
