@@ -76,6 +76,8 @@ def lib():
                 "orc_fri_interpolate": (i32, [_u64p, u32, u64, _u64p]),
                 "orc_snapshot_slot_leaves": (i32, [_u64p, u32, u32, u32, _u64p, i32]),
                 "orc_snapshot_list_root": (i32, [_u64p, u64, u32, u32, _u64p]),
+                "orc_compress_tuple": (u64, [_u64p, u32, u64]),
+                "orc_seteq_partial_products": (i32, [_u64p, _u64p, u64, u32, u64, u64, _u64p]),
                 "orc_snapshot_centroid_digest": (None, [u64, _u64p, u32, _u64p, _u64p]),
                 "orc_snapshot_commit": (i32, [_u64p, u32, u32, u32, _u64p, u32, _u64p, u32, u32, _u64p, _u64p,
                                               _u64p, _u64p, i32]),
@@ -432,3 +434,19 @@ def snapshot_centroid_digest(i: int, mu_i, root_i) -> np.ndarray:
     out = np.empty(4, np.uint64)
     lib().orc_snapshot_centroid_digest(i, _p(m), m.size, _p(rt), _p(out))
     return out
+
+
+# --- multiset equality (Sec. 4.5) -------------------------------------------
+def compress_tuple(x, beta: int) -> int:
+    a = _u64(x)
+    return int(lib().orc_compress_tuple(_p(a), a.size, beta))
+
+
+def seteq_partial_products(X, Y, alpha: int, beta: int):
+    """Z [L + 1] with Z_0 = 1, Z_{i+1} = Z_i (alpha - x_i) / (alpha - y_i) over
+    compressed tuples; None if some alpha - y_i is zero."""
+    a, b = _u64(X), _u64(Y)
+    L, T = a.shape
+    z = np.empty(L + 1, np.uint64)
+    rc = lib().orc_seteq_partial_products(_p(a), _p(b), L, T, alpha, beta, _p(z))
+    return None if rc else z

@@ -888,3 +888,36 @@ void orc_snapshot_centroid_digest(uint64_t i, const u64* mu_i, uint32_t D, const
     orc_hash(in, 1 + D + 4, out);
     free(in);
 }
+
+/* ------------------------------------------------------------------ */
+/* Multiset equality gadget (Sec. 4.5, set-oriented gadgets).          */
+/*   Compress(x; beta) = sum_k x_k beta^k over a tuple of T components; */
+/*   SetEq(X, Y): prod_i (alpha - x_i) = prod_i (alpha - y_i).           */
+/* The prover's grand-product column (the partial products of a        */
+/* PLONK-style permutation argument) is                                 */
+/*   Z_0 = 1,  Z_{i+1} = Z_i (alpha - x_i) / (alpha - y_i),             */
+/* so Z_L = 1 exactly when the two products agree.  Returns 1 (and      */
+/* leaves z undefined) if some alpha - y_i is zero.                      */
+/* ------------------------------------------------------------------ */
+
+u64 orc_compress_tuple(const u64* x, uint32_t T, u64 beta)
+{
+    u64 s = 0, bp = 1;
+    for (uint32_t k = 0; k < T; k++) {
+        s = orc_add(s, orc_mul(x[k], bp));
+        bp = orc_mul(bp, beta);
+    }
+    return s;
+}
+
+int orc_seteq_partial_products(const u64* X, const u64* Y, uint64_t L, uint32_t T, u64 alpha, u64 beta, u64* z)
+{
+    z[0] = 1;
+    for (uint64_t i = 0; i < L; i++) {
+        u64 num = orc_sub(alpha, orc_compress_tuple(X + i * T, T, beta));
+        u64 den = orc_sub(alpha, orc_compress_tuple(Y + i * T, T, beta));
+        if (den == 0) return 1;
+        z[i + 1] = orc_mul(z[i], orc_mul(num, orc_inv(den)));
+    }
+    return 0;
+}
