@@ -55,7 +55,8 @@ INPUT_HOST_COPY, INPUT_DEVICE, INPUT_HOST_BORROW = 0, 1, 2
 
 
 FLAG_TIMING = 2
-STAGES = ("lde_a", "lde_b", "lde_c", "leaf_hash", "merkle", "fri_combine", "fri_fold", "open")
+STAGES = ("lde_a", "lde_b", "lde_c", "leaf_hash", "merkle", "fri_combine", "fri_fold", "open", "seteq",
+          "snapshot_slots")
 
 
 class StageStats(ctypes.Structure):
@@ -78,6 +79,11 @@ class FriInfo(ctypes.Structure):
 class SnapshotDesc(ctypes.Structure):
     _fields_ = [("records", _vp), ("centroids", _vp), ("codebooks", _vp), ("on_device", ctypes.c_int32),
                 ("log_nlist", _u32), ("log_n", _u32), ("M", _u32), ("D", _u32), ("K", _u32), ("d", _u32)]
+
+
+class SeteqDesc(ctypes.Structure):
+    _fields_ = [("x", _vp), ("y", _vp), ("z", _vp), ("L", _u64), ("T", _u32), ("pad", _u32), ("alpha", _u64),
+                ("beta", _u64)]
 
 
 class ReqTimes(ctypes.Structure):
@@ -124,6 +130,8 @@ SIGNATURES = {
     "v3c_snapshot_list_roots": (ctypes.c_int, [_vp, _u64, _u64p]),
     "v3c_snapshot_open_lists": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(_u32), _u32, _u64p]),
     "v3c_snapshot_release": (ctypes.c_int, [_vp, _u64]),
+    # include/v3c_seteq.h
+    "v3c_seteq": (ctypes.c_int, [_vp, ctypes.POINTER(SeteqDesc), _u32, ctypes.POINTER(_u32), _vp]),
 }
 
 _lib = None
@@ -473,6 +481,19 @@ class Context:
 
     def snapshot_release(self, sid: int):
         self._check(self.lib.v3c_snapshot_release(self.h, sid))
+
+    # --------------------------------------------------------------- SetEq
+    def seteq(self, instances, wait: bool = True, stream=None):
+        """instances: list of (x [L][T], y [L][T], z [L+1], alpha, beta), int64
+        CUDA tensors.  Returns per-instance statuses (0 ok, 1 alpha equals a
+        compressed y) when wait, else None."""
+        descs = (SeteqDesc * len(instances))()
+        for i, (x, y, z, alpha, beta) in enumerate(instances):
+            L, T = x.shape
+            descs[i] = SeteqDesc(x.data_ptr(), y.data_ptr(), z.data_ptr(), L, T, 0, alpha, beta)
+        st = (_u32 * len(instances))() if wait else None
+        self._check(self.lib.v3c_seteq(self.h, descs, len(instances), st, _stream(stream)))
+        return list(st) if wait else None
 
     # --------------------------------------------------------------- misc
     def kernel_launches(self) -> int:

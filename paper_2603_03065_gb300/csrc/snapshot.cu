@@ -253,7 +253,7 @@ v3c_status v3c_snapshot_commit(v3c_ctx* ctx, const v3c_snapshot_desc* d, v3c_sna
     ctx->launches++;
     // Slot digests: level 0 of the slot tree, or the list roots when n = 1.
     {
-        StageTimer tm(ctx, 3, s);
+        StageTimer tm(ctx, 9, s);
         k_snap_slots<<<sgrid(N, 128), 128, 0, s>>>(rec, d->M, d->log_n, N, d->log_n ? slot_tree : st->list_roots);
         CKS(cudaGetLastError());
         tm.done();

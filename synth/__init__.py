@@ -245,3 +245,25 @@ def snapshot(seed: int, log_nlist: int, log_n: int, D: int, M: int = 8, K: int =
     mu = _fixed_point(stream_state(seed, base, 3), (1 << log_nlist) * D).reshape(1 << log_nlist, D)
     cb = _fixed_point(stream_state(seed, base, 4), M * K * (D // M)).reshape(M, K, D // M)
     return rec, mu, cb
+
+
+# --- multiset-equality instances -------------------------------------------
+# SetEq over the candidate tuples of the multiset-based query circuit: X holds
+# L tuples (list, slot, distance, item) of the scan budget N_sel, Y the same
+# tuples in another order (a valid permutation witness), or with one tuple
+# altered when equal=False.  Distances are 32-bit fixed point.
+SETEQ_MSMARCO = dict(instances=64, log_L=17, T=4)   # N_sel = 2^24 / 128 per query, 64 queries
+
+
+def seteq_instance(seed: int, L: int, T: int = 4, equal: bool = True, batch: int = 0):
+    base = 0xFFFE0000
+    cols = []
+    for k in range(T):
+        d = draws(stream_state(seed, base + batch, k), 0, L)
+        cols.append(d & np.uint64(0xFFFFFFFF if k >= 2 else 0x1FFF))
+    X = np.stack(cols, axis=1).astype(np.uint64)
+    order = np.argsort(draws(stream_state(seed, base + batch, T), 0, L), kind="stable")
+    Y = X[order].copy()
+    if not equal:
+        Y[L // 2, T - 1] ^= np.uint64(1)
+    return X, Y

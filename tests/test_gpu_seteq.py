@@ -1,0 +1,110 @@
+"""SetEq grand-product columns (Sec. 4.5) on the GPU against the CPU oracle.
+
+Bit-exact over whole columns: single instances whose lengths straddle the
+2048-element tiles (1, 7, 2047, 2048, 2049, 2^16 + 3), tuple widths 1 to 32,
+a batch of uneven instances in one call, the 64 x 2^17 batched workload (two
+instances compared in full, every instance closing to 1), unequal multisets,
+and the degenerate challenge (alpha equal to a compressed y).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+P = oracle.P
+
+
+@pytest.fixture(scope="module")
+def v3c():
+    from paper_2603_03065_gb300 import build
+
+    build.build()
+    import paper_2603_03065_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(v3c):
+    c = v3c.Context(0)
+    yield c
+    c.close()
+
+
+def run(v3c, ctx, cases):
+    import torch
+
+    inst, host = [], []
+    for X, Y, alpha, beta in cases:
+        z = torch.empty(X.shape[0] + 1, dtype=torch.int64, device="cuda")
+        inst.append((v3c.to_device_u64(X), v3c.to_device_u64(Y), z, alpha, beta))
+        host.append((X, Y, alpha, beta))
+    st = ctx.seteq(inst)
+    torch.cuda.synchronize()
+    return st, [v3c.to_host_u64(i[2]) for i in inst]
+
+
+@pytest.mark.parametrize("L,T", [(1, 1), (7, 3), (2047, 4), (2048, 1), (2049, 2), (5000, 32), ((1 << 16) + 3, 4)])
+def test_seteq_matches_oracle(v3c, ctx, L, T):
+    X, Y = synth.seteq_instance(L + T, L, T, equal=(L % 2 == 1))
+    ch = synth.challenges(L, 2)
+    st, (z,) = run(v3c, ctx, [(X, Y, ch[0], ch[1])])
+    want = oracle.seteq_partial_products(X, Y, ch[0], ch[1])
+    assert st == [0]
+    assert np.array_equal(z, want)
+    if L % 2 == 1:
+        assert int(z[-1]) == 1
+
+
+def test_seteq_batch_of_uneven_instances(v3c, ctx):
+    cases = []
+    for b, (L, T) in enumerate([(3, 1), (4096, 4), (10000, 2), (1, 5), (2500, 4), (65, 7)]):
+        X, Y = synth.seteq_instance(90, L, T, equal=b % 2 == 0, batch=b)
+        ch = synth.challenges(90 + b, 2)
+        cases.append((X, Y, ch[0], ch[1]))
+    st, zs = run(v3c, ctx, cases)
+    assert st == [0] * len(cases)
+    for (X, Y, a, bta), z in zip(cases, zs):
+        assert np.array_equal(z, oracle.seteq_partial_products(X, Y, a, bta))
+
+
+def test_seteq_64_queries_x_2_17(v3c, ctx):
+    p = synth.SETEQ_MSMARCO
+    L = 1 << p["log_L"]
+    cases = []
+    for q in range(p["instances"]):
+        X, Y = synth.seteq_instance(7, L, p["T"], batch=q)
+        ch = synth.challenges(1000 + q, 2)
+        cases.append((X, Y, ch[0], ch[1]))
+    st, zs = run(v3c, ctx, cases)
+    assert st == [0] * len(cases)
+    assert all(int(z[-1]) == 1 and int(z[0]) == 1 for z in zs)
+    for q in (0, len(cases) - 1):
+        X, Y, a, b = cases[q]
+        assert np.array_equal(zs[q], oracle.seteq_partial_products(X, Y, a, b))
+
+
+def test_seteq_degenerate_alpha(v3c, ctx):
+    X, Y = synth.seteq_instance(5, 3000, 2)
+    beta = 12345
+    alpha = oracle.compress_tuple(Y[1234], beta)  # alpha - y_1234 = 0
+    ok_X, ok_Y = synth.seteq_instance(6, 100, 2)
+    st, zs = run(v3c, ctx, [(X, Y, alpha, beta), (ok_X, ok_Y, 99, beta)])
+    assert st == [1, 0]
+    assert not zs[0].any()
+    assert oracle.seteq_partial_products(X, Y, alpha, beta) is None
+    assert np.array_equal(zs[1], oracle.seteq_partial_products(ok_X, ok_Y, 99, beta))
+
+
+def test_seteq_rejects_bad_arguments(v3c, ctx):
+    import torch
+
+    x = torch.zeros((4, 33), dtype=torch.int64, device="cuda")
+    z = torch.zeros(5, dtype=torch.int64, device="cuda")
+    with pytest.raises(v3c.V3CError):
+        ctx.seteq([(x, x, z, 1, 1)])  # T = 33
+    x = torch.zeros((4, 2), dtype=torch.int64, device="cuda")
+    with pytest.raises(v3c.V3CError):
+        ctx.seteq([(x, x, z, P, 1)])  # alpha not canonical
