@@ -155,6 +155,8 @@ def run_reference(args):
         return 0
     if args.workload == "fri_135x2_20":
         return run_reference_fri(args)
+    if args.workload in ("snapshot_msmarco", "seteq_64x2_17"):
+        return run_reference_other(args)
     import oracle
 
     s = CPU_SAMPLE
@@ -196,6 +198,24 @@ def run_reference_fri(args):
                    "queries": FRI_QUERIES},
         "cpu_baseline": {k: base[k] for k in ("kind", "cores", "value", "unit", "sample")},
         "e2e": {"value": base["value"], "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_other(args):
+    snap = args.workload == "snapshot_msmarco"
+    for _ in range(max(args.warmup - 1, 0)):
+        (snapshot_cpu_baseline if snap else seteq_cpu_baseline)(1)
+    base = (snapshot_cpu_baseline if snap else seteq_cpu_baseline)(args.steps)
+    line = {
+        "impl": "reference", "metric": "snapshot commitment (root_mk, root_cb) Mslot/s" if snap else
+        "SetEq grand-product columns Gtuple/s", "value": base["value"], "unit": base["unit"], "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {k: base[k] for k in ("kind", "cores", "value", "unit", "sample")},
+        "e2e": {"value": base["value"], "unit": base["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
@@ -651,6 +671,200 @@ def run_fri(args):
     return 0
 
 
+def timed_region(ctx, step, steps: int, warmup: int, local_rank: int, stream):
+    """W untimed steps, then K steps between CUDA events on the stream, with
+    clocks sampled and the library's launches and stage times counted."""
+    import torch
+
+    for _ in range(max(warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    ctx.stage_stats(reset=True)
+    l0 = ctx.kernel_launches()
+    clocks.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stats = ctx.stage_stats(reset=True)
+    return (e0.elapsed_time(e1) / steps, clk, ctx.kernel_launches() - l0,
+            {k: (v[0] / v[1], int(v[1])) for k, v in stats.items() if v[1]})
+
+
+SNAP_CPU_SAMPLE = dict(log_nlist=10, log_n=8, D=384, M=8, K=256)   # 2^18 slots, MS MARCO dimensions
+
+
+def snapshot_cpu_baseline(steps: int = 1) -> dict:
+    import oracle
+
+    p = SNAP_CPU_SAMPLE
+    rec, mu, cb = synth.snapshot(31, p["log_nlist"], p["log_n"], p["D"], p["M"], p["K"])
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.snapshot_commit(rec, mu, cb, p["log_nlist"], p["log_n"], threads=threads)
+    dt = (time.perf_counter() - t0) / steps
+    slots = 1 << (p["log_nlist"] + p["log_n"])
+    return {"value": slots / dt / 1e6, "unit": "Mslot/s", "cores": threads, "kind": "oracle", "ms_per_step": dt * 1e3,
+            "sample": f"oracle snapshot commitment of 2^{p['log_nlist']} lists x 2^{p['log_n']} slots, D {p['D']}, "
+                      f"M {p['M']}, K {p['K']}; {dt:.2f} s per commitment"}
+
+
+def run_snapshot(args):
+    """Snapshot commitment of the MS MARCO high-accuracy layout (8192 lists x
+    2048 slots = 2^24 slots, D = 384, M = 8, K = 256) from device-resident
+    records, centroids and codebooks; roots read back each step.  Not the
+    default bench line; see the design doc."""
+    import torch
+
+    import paper_2603_03065_gb300 as v3c
+
+    torch.cuda.set_device(0)
+    p = synth.SNAP_MSMARCO
+    ln, lnn = p["log_nlist"], p["log_n"]
+    rec, mu, cb = synth.snapshot(24, ln, lnn, p["D"], p["M"], p["K"], valid=p["valid"])
+    ctx = v3c.Context(0, flags=v3c.FLAG_TIMING)
+    stream = torch.cuda.current_stream()
+    d = [v3c.to_device_u64(a) for a in (rec, mu, cb)]
+
+    def step():
+        ctx.snapshot_release(ctx.snapshot_commit(*d, ln, lnn, stream=stream))
+
+    ms, clk, launches, stage_ms = timed_region(ctx, step, args.steps, args.warmup, 0, stream)
+    N = 1 << (ln + lnn)
+    value = N / (ms * 1e-3) / 1e6
+
+    def step_e2e():
+        sid = ctx.snapshot_commit(rec, mu, cb, ln, lnn, stream=stream)
+        roots = ctx.snapshot_roots(sid)
+        ctx.snapshot_release(sid)
+        return roots
+
+    step_e2e()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    slot_ms = stage_ms["snapshot_slots"][0]
+    perms = N * -(-(4 + p["M"]) // 8)
+    achieved = W_PER_PERM * perms / (slot_ms * 1e-3) / 1e12
+    peak = SMS * WIDE_MUL_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    line = {
+        "metric": "snapshot commitment (root_mk, root_cb) Mslot/s", "value": value, "unit": "Mslot/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "snapshot_msmarco", "lists": 1 << ln, "slots_per_list": 1 << lnn, "D": p["D"],
+                   "M": p["M"], "K": p["K"], "valid_fraction": p["valid"],
+                   "l2": "inputs larger than L2 (no flush needed)"},
+        "e2e": {"value": N / e2e_s / 1e6, "unit": "Mslot/s", "ms_per_step": e2e_s * 1e3,
+                "h2d_bytes_per_step": int(rec.nbytes + mu.nbytes + cb.nbytes), "d2h_bytes_per_step": 64},
+        "gpu_launches": int(launches), "clocks": clk,
+        "roofline": {"bound": "alu", "kernel": "k_snap_slots", "achieved": achieved, "peak": peak,
+                     "unit": "T wide-mul/s", "frac": achieved / peak, "traffic": None,
+                     "work_per_launch": W_PER_PERM * perms, "ms_per_launch": slot_ms},
+        "stages_ms_per_launch": stage_ms,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = snapshot_cpu_baseline()
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def seteq_cpu_baseline(steps: int = 1) -> dict:
+    import oracle
+
+    p = synth.SETEQ_MSMARCO
+    L, n = 1 << p["log_L"], 8
+    cases = [synth.seteq_instance(7, L, p["T"], batch=q) for q in range(n)]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for q, (X, Y) in enumerate(cases):
+            oracle.seteq_partial_products(X, Y, 1000 + q, 77 + q)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": n * L / dt / 1e9, "unit": "Gtuple/s", "cores": 1, "kind": "oracle", "ms_per_step": dt * 1e3,
+            "sample": f"oracle SetEq columns of {n} of the 64 instances (2^{p['log_L']} tuples of width {p['T']}), "
+                      f"one core; {dt:.2f} s"}
+
+
+def run_seteq(args):
+    """SetEq grand-product columns of 64 instances x 2^17 tuples of width 4
+    (the multiset checks of 64 queries at the MS MARCO scan budget) in one
+    call, device-resident.  Not the default bench line; see the design doc."""
+    import torch
+
+    import paper_2603_03065_gb300 as v3c
+
+    torch.cuda.set_device(0)
+    p = synth.SETEQ_MSMARCO
+    L, n, T = 1 << p["log_L"], p["instances"], p["T"]
+    ctx = v3c.Context(0, flags=v3c.FLAG_TIMING)
+    stream = torch.cuda.current_stream()
+    host, inst = [], []
+    for q in range(n):
+        X, Y = synth.seteq_instance(7, L, T, batch=q)
+        ch = synth.challenges(1000 + q, 2)
+        host.append((X, Y))
+        z = torch.empty(L + 1, dtype=torch.int64, device="cuda")
+        inst.append((v3c.to_device_u64(X), v3c.to_device_u64(Y), z, ch[0], ch[1]))
+
+    def step():
+        ctx.seteq(inst, wait=False, stream=stream)
+
+    ms, clk, launches, stage_ms = timed_region(ctx, step, args.steps, args.warmup, 0, stream)
+    value = n * L / (ms * 1e-3) / 1e9
+    # end to end: inputs from pinned host memory, every column back to the host
+    pinned = [(torch.from_numpy(X.view(np.int64)).pin_memory(), torch.from_numpy(Y.view(np.int64)).pin_memory())
+              for X, Y in host]
+    zh = [torch.empty(L + 1, dtype=torch.int64).pin_memory() for _ in range(n)]
+
+    def step_e2e():
+        for (xp, yp), (xd, yd, _, _, _) in zip(pinned, inst):
+            xd.copy_(xp, non_blocking=True)
+            yd.copy_(yp, non_blocking=True)
+        st = ctx.seteq(inst, wait=True, stream=stream)
+        for z, (_, _, zd, _, _) in zip(zh, inst):
+            z.copy_(zd, non_blocking=True)
+        torch.cuda.synchronize()
+        return st
+
+    step_e2e()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    seq_ms = stage_ms["seteq"][0]
+    alg_bytes = n * (2 * L * T * 8 + (L + 1) * 8)
+    achieved = alg_bytes / (seq_ms * 1e-3) / 1e9
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    line = {
+        "metric": "SetEq grand-product columns Gtuple/s", "value": value, "unit": "Gtuple/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "seteq_64x2_17", "instances": n, "tuples": L, "tuple_width": T,
+                   "l2": "inputs larger than L2 (no flush needed)"},
+        "e2e": {"value": n * L / e2e_s / 1e9, "unit": "Gtuple/s", "ms_per_step": e2e_s * 1e3,
+                "h2d_bytes_per_step": int(n * 2 * L * T * 8), "d2h_bytes_per_step": int(n * (L + 1) * 8)},
+        "gpu_launches": int(launches), "clocks": clk,
+        "roofline": {"bound": "hbm", "kernel": "k_seteq_reduce+k_seteq_carries+k_seteq_apply",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "bytes_per_launch": alg_bytes, "ms_per_launch": seq_ms, "peak_source": "measured",
+                     "note": "algorithmic bytes: X and Y read once, Z written once; the kernels read X and Y twice"},
+        "stages_ms_per_launch": stage_ms,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = seteq_cpu_baseline()
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -668,7 +882,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["v3c", "reference"], default="v3c")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven_64", "serve_poisson", "fri_135x2_20"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven_64", "serve_poisson", "fri_135x2_20",
+                                                               "snapshot_msmarco", "seteq_64x2_17"],
                     default="large_135x2_20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--int-peak", action="store_true", help="also run the integer-pipe microbenchmark")
@@ -685,6 +900,10 @@ def main():
         return run_serving(args)
     if args.workload == "fri_135x2_20":
         return run_fri(args)
+    if args.workload == "snapshot_msmarco":
+        return run_snapshot(args)
+    if args.workload == "seteq_64x2_17":
+        return run_seteq(args)
     return run_v3c(args)
 
 

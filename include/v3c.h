@@ -238,9 +238,9 @@ uint64_t v3c_kernel_launches(v3c_ctx* ctx);
  * leaf hash, 4 = Merkle levels, 5 = FRI batch combination, 6 = FRI folds and
  * final coefficients, 7 = opening gathers (v3c_fri_query, v3c_open_batch,
  * v3c_snapshot_open_lists), 8 = SetEq grand products (three launches as one
- * stage), 9 = snapshot slot digests. */
+ * stage), 9 = snapshot slot digests, 10 = snapshot codebook digest. */
 #define V3C_FLAG_TIMING 0x2u
-#define V3C_NUM_STAGES 10
+#define V3C_NUM_STAGES 11
 typedef struct {
     double ms[V3C_NUM_STAGES];
     uint64_t launches[V3C_NUM_STAGES];

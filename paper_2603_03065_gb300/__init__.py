@@ -56,7 +56,7 @@ INPUT_HOST_COPY, INPUT_DEVICE, INPUT_HOST_BORROW = 0, 1, 2
 
 FLAG_TIMING = 2
 STAGES = ("lde_a", "lde_b", "lde_c", "leaf_hash", "merkle", "fri_combine", "fri_fold", "open", "seteq",
-          "snapshot_slots")
+          "snapshot_slots", "snapshot_codebook")
 
 
 class StageStats(ctypes.Structure):

@@ -95,10 +95,73 @@ __global__ void __launch_bounds__(128) k_snap_centroids(const u64* __restrict__ 
     }
 }
 
-// root_cb = Hash of the flattened codebooks: one thread, one sponge.
-__global__ void k_snap_codebook(const u64* __restrict__ cb, u32 count, u64* __restrict__ out)
+// root_cb = Hash of the flattened codebooks.  The sponge is sequential
+// (count / 8 permutations, each on the previous state), so its time is the
+// latency of one permutation times their number.  One warp shares each
+// permutation: lane l < 12 holds state word s_l.  A round adds the round
+// constant, applies the S-box (every lane in a full round, lane 0 in a
+// partial one), and forms its MDS row
+//   s'_l = sum_j m[(j - l) mod 12] s_j
+// from the other lanes' words, gathered by shuffles.  The products by
+// m < 2^6 are summed unreduced in 128 bits and reduced once per round.
+// Words stay non-canonical (in [0, 2^64), congruent mod p) until the digest.
+__constant__ u32 c_mds_row[12] = V3C_MDS_ROW_INIT;
+
+// x^7 on non-canonical values (inputs and output in [0, 2^64)).
+__device__ __forceinline__ u64 sbox7_nc(u64 x)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) sponge_digest(count, [&](u32 e) -> u64 { return __ldg(cb + e); }, out);
+    u64 x2 = gl::mul_nc(x, x);
+    u64 x3 = gl::mul_nc(x2, x);
+    u64 x4 = gl::mul_nc(x2, x2);
+    return gl::mul_nc(x3, x4);
+}
+
+__global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb, u32 count, u64* __restrict__ out)
+{
+    const u32 l = threadIdx.x;
+    const bool own = l < 12;
+    u32 m[12];  // m[j] = row[(j - l) mod 12]: this lane's MDS row
+#pragma unroll
+    for (int j = 0; j < 12; j++) m[j] = c_mds_row[(j + 12 - (own ? l : 0)) % 12];
+    u64 x = 0;  // s_l, non-canonical in [0, 2^64) between rounds
+    if (count <= 4) {
+        if (l < count) x = __ldg(cb + l);
+    } else {
+        u64 next = l < 8 && l < count ? __ldg(cb + l) : 0;
+        for (u32 st = 0; st < count; st += 8) {
+            const u32 len = min(8u, count - st);
+            if (l < len) x = next;  // overwrite lanes 0 .. len-1
+            if (st + 8 < count)     // prefetch the next chunk during the permutation
+                next = l < 8 && st + 8 + l < count ? __ldg(cb + st + 8 + l) : 0;
+            for (int r = 0; r < 30; r++) {
+                const bool full = r < 4 || r >= 26;
+                const u64 rc = pos::c_rc[r][own ? l : 0];  // always an in-bounds read
+                x = gl::add_nc_small(x, own ? rc : 0);
+                // Every lane computes x^7 without branching.  In a partial round
+                // only lane 0's word takes it: the other 11 gathered words are
+                // the pre-S-box ones, so their products overlap the S-box chain.
+                const u64 y = sbox7_nc(x);
+                const u64 v = full ? y : x;
+                // Three independent 128-bit sums (j mod 3) shorten the dependency chain.
+                u64 lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+                for (int j = 11; j >= 0; j--) {
+                    u64 sj = __shfl_sync(0xffffffffu, j == 0 ? y : v, j);
+                    u64 p0 = (u64)(u32)sj * m[j], p1 = (sj >> 32) * m[j];  // sj m = p0 + p1 2^32
+                    u64 add_lo = p0 + (p1 << 32);
+                    u64 c0 = add_lo < p0;
+                    lo[j % 3] += add_lo;
+                    hi[j % 3] += (p1 >> 32) + c0 + (lo[j % 3] < add_lo);
+                }
+                u64 a = lo[0] + lo[1];
+                u64 h = hi[0] + hi[1] + (a < lo[0]);
+                u64 b = a + lo[2];
+                h += hi[2] + (b < a);
+                x = gl::reduce128_ptx(b, h);
+            }
+        }
+    }
+    if (l < 4) out[l] = gl::canon(x);
 }
 
 // Top-level paths: for query q and word o < 4 log_nlist, sibling digest of
@@ -247,8 +310,12 @@ v3c_status v3c_snapshot_commit(v3c_ctx* ctx, const v3c_snapshot_desc* d, v3c_sna
     CKS(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
     CKS(cudaEventRecord(fork, s));
     CKS(cudaStreamWaitEvent(side, fork, 0));
-    k_snap_codebook<<<1, 32, 0, side>>>(cb, (u32)cbw, st->root_cb);
-    CKS(cudaGetLastError());
+    {
+        StageTimer tm(ctx, 10, side);
+        k_snap_codebook<<<1, 32, 0, side>>>(cb, (u32)cbw, st->root_cb);
+        CKS(cudaGetLastError());
+        tm.done();
+    }
     CKS(cudaEventRecord(join, side));
     ctx->launches++;
     // Slot digests: level 0 of the slot tree, or the list roots when n = 1.
