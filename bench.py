@@ -53,8 +53,8 @@ SMS = 152
 WIDE_MUL_PER_SM_CLK = 32
 SM_MAX_MHZ = 2070.0
 # DRAM traffic of one leaf-hash launch on this workload, from an ncu capture
-# of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum,
-# profiles/launches_large_135x2_20.md).  Drop an entry when the kernel changes.
+# of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum, one
+# capture of the bench's own command).  Drop an entry when the kernel changes.
 LEAF_HASH_TRAFFIC = {"large_135x2_20": 9.785e9}
 # The CPU-baseline / reference-arm sample: the full commit of the same column
 # mix at fewer rows.
@@ -345,7 +345,7 @@ def run_batched(args):
     """64 uneven column-batches (seed 3): one v3c_commit over all of them
     (one persistent launch per stage, replayed from a CUDA graph) against 64
     one-batch commits (per-batch launches), on the same device-resident
-    inputs.  Not the default bench line; see the design doc."""
+    inputs.  Not the default bench line."""
     import torch
 
     import paper_2603_03065_gb300 as v3c
@@ -408,7 +408,7 @@ def run_serving(args):
     (borrowed, copied at admission), each released as soon as it is done.
     Reports p50/p99 submit->done latency after a 5 s warm-up and Gelem/s, and
     the same trace through the serial one-at-a-time commit path.  Not the
-    default bench line; see the design doc."""
+    default bench line."""
     import torch
 
     import paper_2603_03065_gb300 as v3c
@@ -517,7 +517,7 @@ FRI_QUERIES = 28      # Plonky2's default number of query rounds
 FRI_CFG = (4, 5, 4)   # arity 2^4, final polynomial 2^5 values, cap height 4 per layer
 # DRAM traffic of one k_fri_combine launch on the 135 x 2^20 workload, from an
 # ncu capture of the same kernel.  Drop the entry when the kernel changes.
-FRI_COMBINE_TRAFFIC = {}
+FRI_COMBINE_TRAFFIC = {"fri_135x2_20": 9.724e9}
 
 
 def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
@@ -553,7 +553,7 @@ def run_fri(args):
     workload: combination of the 135 LDE columns with powers of alpha, folds
     of arity 16 down to 2^5 values, every layer's Merkle tree, the final
     coefficients; then 28 query openings and the 28 initial-row openings.
-    Not the default bench line; see the design doc."""
+    Not the default bench line."""
     import torch
 
     import paper_2603_03065_gb300 as v3c
@@ -720,7 +720,7 @@ def run_snapshot(args):
     """Snapshot commitment of the MS MARCO high-accuracy layout (8192 lists x
     2048 slots = 2^24 slots, D = 384, M = 8, K = 256) from device-resident
     records, centroids and codebooks; roots read back each step.  Not the
-    default bench line; see the design doc."""
+    default bench line."""
     import torch
 
     import paper_2603_03065_gb300 as v3c
@@ -796,7 +796,7 @@ def seteq_cpu_baseline(steps: int = 1) -> dict:
 def run_seteq(args):
     """SetEq grand-product columns of 64 instances x 2^17 tuples of width 4
     (the multiset checks of 64 queries at the MS MARCO scan budget) in one
-    call, device-resident.  Not the default bench line; see the design doc."""
+    call, device-resident.  Not the default bench line."""
     import torch
 
     import paper_2603_03065_gb300 as v3c

@@ -10,7 +10,9 @@
 // inverse of the full denominator product (the instance's only inversion).
 // (3) Every tile recomputes its elements, scans them with warp shuffles and
 // one shared-memory step per CTA, and writes
-// Z_i = N_{<i} * D_{>=i} * D_all^-1.
+// Z_i = N_{<i} * D_{>=i} * D_all^-1.  Loads and stores are coalesced: the
+// order-free product of phase 1 takes strided elements, and phase 3
+// transposes through shared memory.
 // Each launch streams X and Y once (phase 1 and 3) or touches only tile
 // products (phase 2).
 #include <cuda_runtime.h>
@@ -111,19 +113,21 @@ __device__ __forceinline__ u64 block_exclusive(u64 v, u64* sh)
     return r;
 }
 
-// Phase 1: tile products of the numerators and denominators.
+// Phase 1: tile products of the numerators and denominators.  A product
+// does not depend on order, so thread t takes elements t + 256 k: the warp's
+// loads of one tuple component are then one contiguous run.
 __global__ void __launch_bounds__(kSeqThreads) k_seteq_reduce(const SeqJob* __restrict__ jobs, u32 njobs, u32 ntiles)
 {
     __shared__ u64 sh[32];
     for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const SeqJob& J = jobs[seq_find(jobs, njobs, tile)];
         const u32 lt = tile - J.tile0;
-        const u64 base = (u64)lt * kSeqTile + (u64)threadIdx.x * kSeqPer;
+        const u64 base = (u64)lt * kSeqTile + threadIdx.x;
         u64 pn = 1, pd = 1;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
             u64 n, d;
-            seq_terms(J, base + k, n, d);
+            seq_terms(J, base + (u64)k * kSeqThreads, n, d);
             pn = gl::mul(pn, n);
             pd = gl::mul(pd, d);
         }
@@ -179,19 +183,40 @@ __global__ void __launch_bounds__(1024) k_seteq_carries(const SeqJob* __restrict
 }
 
 // Phase 3: Z_i = N_{<i} D_{>=i} D^-1 for every element of every tile, and
-// Z_L = N_{<L} D^-1 from the thread that holds element L - 1.
+// Z_L = N_{<L} D^-1 from the thread that holds element L - 1.  Terms are
+// computed with coalesced loads (thread t, elements t + 256 k), transposed
+// through shared memory so that thread t scans the contiguous elements
+// 8t .. 8t+7, and Z goes back through shared memory for coalesced stores.
+// Shared words are padded by one per 8 (index i + i/8): the 8-word stride of
+// the contiguous reads becomes 9, an odd number of 8-byte words, so a warp's
+// accesses fall in distinct bank pairs.
+__device__ __forceinline__ u32 seq_pad(u32 i) { return i + (i >> 3); }
+
 __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __restrict__ jobs, u32 njobs, u32 ntiles)
 {
     __shared__ u64 sh[32];
+    __shared__ u64 s_num[kSeqTile + kSeqTile / 8];
+    __shared__ u64 s_den[kSeqTile + kSeqTile / 8];
+    const u32 t = threadIdx.x;
     for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const SeqJob& J = jobs[seq_find(jobs, njobs, tile)];
         const u32 lt = tile - J.tile0;
-        const u64 base = (u64)lt * kSeqTile + (u64)threadIdx.x * kSeqPer;
+        const u64 tbase = (u64)lt * kSeqTile;
+#pragma unroll
+        for (u32 k = 0; k < kSeqPer; k++) {
+            const u32 i = t + k * kSeqThreads;
+            u64 n, d;
+            seq_terms(J, tbase + i, n, d);
+            s_num[seq_pad(i)] = n;
+            s_den[seq_pad(i)] = d;
+        }
+        __syncthreads();
         u64 num[kSeqPer], den[kSeqPer];
         u64 pn = 1, pd = 1;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
-            seq_terms(J, base + k, num[k], den[k]);
+            num[k] = s_num[seq_pad(kSeqPer * t + k)];
+            den[k] = s_den[seq_pad(kSeqPer * t + k)];
             pn = gl::mul(pn, num[k]);
             pd = gl::mul(pd, den[k]);
         }
@@ -205,13 +230,20 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __res
             S = gl::mul(S, den[k]);
             suf[k] = S;
         }
+        const u64 ebase = tbase + (u64)kSeqPer * t;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
-            const u64 e = base + k;
-            if (e < J.L) J.z[e] = gl::mul(gl::mul(N, suf[k]), inv);
+            s_num[seq_pad(kSeqPer * t + k)] = gl::mul(gl::mul(N, suf[k]), inv);  // every read above is done
             N = gl::mul(N, num[k]);
-            if (e + 1 == J.L) J.z[J.L] = gl::mul(N, inv);
+            if (ebase + k + 1 == J.L) J.z[J.L] = gl::mul(N, inv);
         }
+        __syncthreads();
+#pragma unroll
+        for (u32 k = 0; k < kSeqPer; k++) {
+            const u32 i = t + k * kSeqThreads;
+            if (tbase + i < J.L) J.z[tbase + i] = s_num[seq_pad(i)];
+        }
+        __syncthreads();
     }
 }
 
