@@ -317,6 +317,19 @@ __device__ __forceinline__ u32 find_job(const u32* first, u32 njobs, u32 item)
     return lo;
 }
 
+// Asynchronous 8-byte global -> shared copies (cp.async, L1 bypassed for the
+// streamed operand).  A thread issues all copies of its tile, then waits
+// once, so the tile's loads are in flight together instead of a few at a time.
+__device__ __forceinline__ void cp_async8(u64* smem_dst, const u64* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------- stage A
 
 u32 stage_a_items(const LdeJob& j, const Tiles&)
@@ -354,8 +367,9 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
         }
         for (u32 e = threadIdx.x; e < (T2 << l1); e += blockDim.x) {
             u32 u = e & (T2 - 1), i1 = e >> lT2;
-            data[sw((u << l1) + i1)] = __ldcs(x + i20 + u + ((size_t)i1 << l2));
+            cp_async8(data + sw((u << l1) + i1), x + i20 + u + ((size_t)i1 << l2));
         }
+        cp_async_wait_all();
         __syncthreads();
         dft_dif(data, T2, l1, tw, J.kcap);
         u64* Y = J.Y + ((size_t)col << J.plan.log_n);
@@ -499,12 +513,14 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
             u32 w = e >> (l1 + lQ), rem = e & (per - 1);
             u32 v = rem & (Q - 1), k1 = rem >> lQ;
             u32 col = kStageCCols * cg + w;
-            u64 val = 0;
+            u64* dst = data + sw(((w * Q + v) << l1) + k1);
             if (col < J.c)
-                val = __ldcg(J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQz)) +
-                             ((size_t)k1 << lQz) + qoff + v);
-            data[sw(((w * Q + v) << l1) + k1)] = val;
+                cp_async8(dst, J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQz)) +
+                                   ((size_t)k1 << lQz) + qoff + v);
+            else
+                *dst = 0;
         }
+        cp_async_wait_all();
         __syncthreads();
         dft_dif(data, kStageCCols * Q, l1, tw, J.kcap);
         const u32 c0 = kStageCCols * cg;
