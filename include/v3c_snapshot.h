@@ -49,8 +49,11 @@ typedef struct {
 /* Builds the commitment on `stream` (a cudaStream_t) and returns a resident
  * snapshot object.  The codebook digest, a single sequential sponge, runs on
  * a second stream alongside the tree levels and is joined back before the
- * call's work on `stream` completes.  Host inputs are copied before the
- * call returns. */
+ * call's work on `stream` completes.  The context keeps a device copy of the
+ * last committed codebooks and their digest: a commit whose codebooks are
+ * equal word for word (compared on the device) reuses the digest, so
+ * successive snapshot versions with unchanged codebooks skip the sponge.
+ * Host inputs are copied before the call returns. */
 v3c_status v3c_snapshot_commit(v3c_ctx* ctx, const v3c_snapshot_desc* desc, v3c_snapshot_id* out, void* stream);
 
 /* root_mk and root_cb (4 words each; either may be NULL).  Waits for the build. */

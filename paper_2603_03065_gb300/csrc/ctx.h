@@ -19,6 +19,7 @@ struct Server;
 }
 struct FriState;
 struct SnapState;
+struct SnapCbCache;
 extern thread_local int g_dev_cache;
 }  // namespace v3c
 
@@ -92,6 +93,7 @@ struct v3c_ctx {
     serve::Server* server = nullptr;
     std::unordered_map<u64, FriState*> fri;      // FRI commit-phase states (fri.cu)
     std::unordered_map<u64, SnapState*> snaps;   // snapshot commitments (snapshot.cu)
+    SnapCbCache* snap_cb = nullptr;              // codebook-digest cache (snapshot.cu)
     cudaStream_t release_stream = nullptr;  // orders frees of resident objects
     // CUDA graphs of batch signatures, and the autotuner's per-shape choices
     std::unordered_map<std::string, GraphSet> graphs;

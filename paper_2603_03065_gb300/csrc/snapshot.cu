@@ -9,8 +9,9 @@
 // that tree at height log2(nlist), and the batched Merkle-level launches of
 // the polynomial commitment build every list tree at once.  One thread per
 // list binds the centroid; the top-level tree reuses the same launches.
-// The codebook digest is one sequential sponge (M K d / 8 permutations in
-// one thread): it runs on a side stream, overlapped with the trees.
+// The codebook digest is one sequential sponge (M K d / 8 permutations): it
+// runs on a side stream, overlapped with the trees, and is reused when a
+// later commit's codebooks are equal word for word (checked on the device).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +39,17 @@ struct SnapState {
     u64* top_tree = nullptr;    // level-major, levels 0 .. log_nlist - 1 (level 0 = centroid digests)
     u64* root_mk = nullptr;     // [4]
     u64* root_cb = nullptr;     // [4]
+    cudaEvent_t ev = nullptr;
+};
+
+// The context's codebook-digest cache: the last committed codebooks and their
+// digest.  PQ codebooks are static once trained (Sec. 4.3), so successive
+// snapshot versions usually share them; a commit compares its codebooks
+// with the cached copy on the device and reuses the digest only if every
+// word is equal.  Layout of mem: [diff flag, digest (4), codebooks (count)].
+struct SnapCbCache {
+    u64* mem = nullptr;
+    u32 count = 0;
     cudaEvent_t ev = nullptr;
 };
 
@@ -116,9 +128,16 @@ __device__ __forceinline__ u64 sbox7_nc(u64 x)
     return gl::mul_nc(x3, x4);
 }
 
-__global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb, u32 count, u64* __restrict__ out)
+// With `same` non-null, *same == 0 means the codebooks equal the cached ones
+// (k_snap_cb_compare) and the cached digest is copied instead.
+__global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb, u32 count, u64* __restrict__ out,
+                                                     const u64* __restrict__ same, const u64* __restrict__ cached)
 {
     const u32 l = threadIdx.x;
+    if (same && *same == 0) {
+        if (l < 4) out[l] = cached[l];
+        return;
+    }
     const bool own = l < 12;
     u32 m[12];  // m[j] = row[(j - l) mod 12]: this lane's MDS row
 #pragma unroll
@@ -162,6 +181,14 @@ __global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb
         }
     }
     if (l < 4) out[l] = gl::canon(x);
+}
+
+// *diff = 1 if a[i] != b[i] for some i < count (diff cleared beforehand).
+__global__ void k_snap_cb_compare(const u64* __restrict__ a, const u64* __restrict__ b, u32 count, u64* diff)
+{
+    bool d = false;
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) d |= a[i] != b[i];
+    if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) *diff = 1;
 }
 
 // Top-level paths: for query q and word o < 4 log_nlist, sibling digest of
@@ -219,6 +246,12 @@ void snap_free_all(v3c_ctx* ctx)
         delete kv.second;
     }
     ctx->snaps.clear();
+    if (ctx->snap_cb) {
+        if (ctx->snap_cb->mem) cudaFree(ctx->snap_cb->mem);
+        if (ctx->snap_cb->ev) cudaEventDestroy(ctx->snap_cb->ev);
+        delete ctx->snap_cb;
+        ctx->snap_cb = nullptr;
+    }
 }
 
 extern "C" {
@@ -311,13 +344,41 @@ v3c_status v3c_snapshot_commit(v3c_ctx* ctx, const v3c_snapshot_desc* d, v3c_sna
     CKS(cudaEventRecord(fork, s));
     CKS(cudaStreamWaitEvent(side, fork, 0));
     {
+        SnapCbCache*& cc = ctx->snap_cb;
+        if (!cc) cc = new SnapCbCache();
+        const bool usable = cc->mem && cc->count == (u32)cbw;
         StageTimer tm(ctx, 10, side);
-        k_snap_codebook<<<1, 32, 0, side>>>(cb, (u32)cbw, st->root_cb);
+        if (usable) {
+            CKS(cudaStreamWaitEvent(side, cc->ev, 0));
+            CKS(cudaMemsetAsync(cc->mem, 0, 8, side));
+            k_snap_cb_compare<<<sgrid(cbw, 256), 256, 0, side>>>(cc->mem + 5, cb, (u32)cbw, cc->mem);
+            CKS(cudaGetLastError());
+            k_snap_codebook<<<1, 32, 0, side>>>(cb, (u32)cbw, st->root_cb, cc->mem, cc->mem + 1);
+            ctx->launches += 2;
+        } else {
+            k_snap_codebook<<<1, 32, 0, side>>>(cb, (u32)cbw, st->root_cb, nullptr, nullptr);
+            ctx->launches++;
+        }
         CKS(cudaGetLastError());
         tm.done();
+        // Refresh the cache with this commit's codebooks and digest.
+        // The cache counts as filled (count set) only once its copies are queued.
+        if (!usable) {
+            cc->count = 0;
+            if (cc->mem) {
+                CKS(cudaStreamWaitEvent(side, cc->ev, 0));
+                CKS(cudaFreeAsync(cc->mem, side));
+                cc->mem = nullptr;
+            }
+            CKS(cudaMallocAsync((void**)&cc->mem, (5 + cbw) * 8, side));
+            if (!cc->ev) CKS(cudaEventCreateWithFlags(&cc->ev, cudaEventDisableTiming));
+        }
+        CKS(cudaMemcpyAsync(cc->mem + 1, st->root_cb, 32, cudaMemcpyDeviceToDevice, side));
+        CKS(cudaMemcpyAsync(cc->mem + 5, cb, cbw * 8, cudaMemcpyDeviceToDevice, side));
+        CKS(cudaEventRecord(cc->ev, side));
+        cc->count = (u32)cbw;
     }
     CKS(cudaEventRecord(join, side));
-    ctx->launches++;
     // Slot digests: level 0 of the slot tree, or the list roots when n = 1.
     {
         StageTimer tm(ctx, 9, s);

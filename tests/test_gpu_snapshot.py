@@ -100,6 +100,24 @@ def test_snapshot_msmarco_high_acc_sampled(v3c, ctx):
     ctx.snapshot_release(sid)
 
 
+def test_snapshot_codebook_digest_cache(v3c):
+    # The context reuses root_cb only for codebooks equal word for word: a
+    # stale digest would show up as a mismatch against the oracle here.
+    with v3c.Context(0) as c:
+        rec, mu, cb = synth.snapshot(40, 3, 3, 16, 4, 8)
+        rec2, mu2, _ = synth.snapshot(41, 3, 3, 16, 4, 8)
+        cb_changed = cb.copy()
+        cb_changed[3, 5, 2] = (int(cb_changed[3, 5, 2]) + 1) % oracle.P
+        _, _, cb_other = synth.snapshot(42, 3, 3, 16, 4, 4)  # another shape: K = 4
+        seq = [(rec, mu, cb), (rec2, mu2, cb), (rec, mu, cb_changed), (rec2, mu2, cb_other), (rec, mu, cb)]
+        for r, m, k in seq:
+            sid = c.snapshot_commit(v3c.to_device_u64(r), v3c.to_device_u64(m), v3c.to_device_u64(k), 3, 3)
+            mk, cbr = c.snapshot_roots(sid)
+            assert np.array_equal(cbr, oracle.hash_(k.reshape(-1)))
+            assert np.array_equal(mk, oracle.snapshot_commit(r, m, k, 3, 3)["root_mk"])
+            c.snapshot_release(sid)
+
+
 def test_snapshot_errors(v3c, ctx):
     rec, mu, cb = synth.snapshot(8, 2, 2, 8, 2, 4)
     with pytest.raises(v3c.V3CError):
