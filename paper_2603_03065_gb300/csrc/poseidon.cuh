@@ -61,7 +61,7 @@ enum MdsKind { MDS_WIDE = 0, MDS_LIMB = 1, MDS_SPLIT = 2 };
 // FOLD3 / RED: the limb fold and the 128-bit reduction written as PTX
 // carry chains (no compares or selects).
 template <int MUL_, int MDS_, bool SQR_, bool FAST_, bool FOLD2_ = false, bool ARCM_ = false,
-          bool FOLD3_ = false, bool RED_ = false>
+          bool FOLD3_ = false, bool RED_ = false, bool SHIFT_ = false>
 struct Cfg {
     static constexpr int MUL = MUL_;
     static constexpr int MDS = MDS_;
@@ -71,6 +71,7 @@ struct Cfg {
     static constexpr bool ARCM = ARCM_;
     static constexpr bool FOLD3 = FOLD3_;
     static constexpr bool RED = RED_;
+    static constexpr bool SHIFT = SHIFT_;
 };
 
 // A + B 2^22 + C 2^44 (A, B, C < 2^32) to [0, 2^64) with carry chains:
@@ -286,6 +287,51 @@ __device__ __forceinline__ u64 limb_fold21(u32 A, u32 B, u32 Cc)
     return r;
 }
 
+
+// acc + x K for a constant K (mod 2^32; K is a compile-time constant once the
+// MDS loops are unrolled).  With shift set, constants with at most two set
+// bits, or of the form 2^a - 2^b, are built from shifts and adds (integer ALU
+// pipe) instead of one multiply-add (the IMAD pipe, which the permutation
+// otherwise saturates).  Negative K subtracts.
+// Bit counts of 0 <= a < 256 with fixed-bound loops, so that they fold to
+// constants after the MDS loops are unrolled.
+__host__ __device__ __forceinline__ constexpr int cpop(int a)
+{
+    int n = 0;
+    for (int b = 0; b < 8; b++) n += (a >> b) & 1;
+    return n;
+}
+__host__ __device__ __forceinline__ constexpr int chi(int a)
+{
+    int h = 0;
+    for (int b = 0; b < 8; b++)
+        if ((a >> b) & 1) h = b;
+    return h;
+}
+__host__ __device__ __forceinline__ constexpr int clo(int a)
+{
+    int l = 0;
+    for (int b = 7; b >= 0; b--)
+        if ((a >> b) & 1) l = b;
+    return l;
+}
+
+__device__ __forceinline__ u32 mac_const(u32 acc, u32 x, int K, bool shift)
+{
+    const int A = K < 0 ? -K : K;
+    const int pc = cpop(A), hi = chi(A), lo = clo(A);
+    const bool sub_form = pc > 2 && ((1 << (hi + 1)) - (1 << lo)) == A;
+    if (!shift || A == 0 || (pc > 2 && !sub_form)) return acc + x * (u32)K;
+    u32 t;
+    if (pc == 1)
+        t = x << lo;
+    else if (pc == 2)
+        t = (x << hi) + (x << lo);
+    else
+        t = (x << (hi + 1)) - (x << lo);
+    return K < 0 ? acc - t : acc + t;
+}
+
 // Block form of the circulant: with x = (x_top, x_bot) in halves of 6,
 // M = [[A, B], [B, A]], so y_top + y_bot = (A + B)(x_top + x_bot) and
 // y_top - y_bot = (A - B)(x_top - x_bot).  A + B is the 6x6 circulant of
@@ -300,6 +346,7 @@ __host__ __device__ constexpr u32 split_d(int i, int j)
 // P <= 6 * 126 * (2^22 - 2) + 2^22 < 2^32; |v| < 2^21 and |Q| < 2^30; the true
 // P + Q and P - Q are 2 y in [0, 2^32), so the 32-bit sums are exact and the
 // halving is a logical shift.  init = [P inits (6), Q inits (6)].
+template <class C>
 __device__ __forceinline__ void split6(const u32 (&x)[12], const u32* init, u32 (&y)[12])
 {
     u32 u[6], v[6];
@@ -313,8 +360,8 @@ __device__ __forceinline__ void split6(const u32 (&x)[12], const u32* init, u32 
         u32 P = init[i], Q = init[6 + i];
 #pragma unroll
         for (int j = 0; j < 6; j++) {
-            P += u[j] * split_s((j - i + 6) % 6);
-            Q += v[j] * split_d(i, j);
+            P = mac_const(P, u[j], (int)split_s((j - i + 6) % 6), C::SHIFT);
+            Q = mac_const(Q, v[j], (int)split_d(i, j), C::SHIFT);
         }
         y[i] = (P + Q) >> 1;
         y[i + 6] = (P - Q) >> 1;
@@ -322,6 +369,7 @@ __device__ __forceinline__ void split6(const u32 (&x)[12], const u32* init, u32 
 }
 
 // s <- M s (+ the next round's constants, from init) with 21-bit limbs.
+template <class C>
 __device__ __forceinline__ void mds_split(u64 (&s)[12], const u32* init)
 {
     u32 a[12], b[12], c[12];
@@ -332,14 +380,14 @@ __device__ __forceinline__ void mds_split(u64 (&s)[12], const u32* init)
         c[j] = (u32)(s[j] >> 42);
     }
     u32 ya[12], yb[12];
-    split6(a, init, ya);
-    split6(b, init + 12, yb);
+    split6<C>(a, init, ya);
+    split6<C>(b, init + 12, yb);
 #pragma unroll
     for (int i = 0; i < 12; i++) {
         // The 22-bit top limb: direct product; 12 * 63 * (2^22 - 1) + 2^22 < 2^32.
         u32 Cc = init[24 + i];
 #pragma unroll
-        for (int j = 0; j < 12; j++) Cc += c[j] * mds_coef((j - i + 12) % 12);
+        for (int j = 0; j < 12; j++) Cc = mac_const(Cc, c[j], (int)mds_coef((j - i + 12) % 12), C::SHIFT);
         s[i] = limb_fold21(ya[i], yb[i], Cc);
     }
 }
@@ -352,7 +400,7 @@ __device__ __forceinline__ void mds(u64 (&s)[12], const u32* init = nullptr)
 {
     u64 out[12];
     if (C::MDS == MDS_SPLIT) {
-        mds_split(s, init);
+        mds_split<C>(s, init);
         return;
     }
     if (C::MDS == MDS_LIMB) {
