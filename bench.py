@@ -114,7 +114,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
@@ -125,12 +125,17 @@ class ClockSampler:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for name, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(pw) if pw else None}
 
 
 def cpu_baseline(steps: int = 1) -> dict:
@@ -294,11 +299,14 @@ def run_v3c(args):
     step_e2e()
     torch.cuda.synchronize()
     barrier()
+    e2e_clocks = ClockSampler(local_rank)
+    e2e_clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step_e2e()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e_clk = e2e_clocks.stop()
     e2e_value = world * s.lde_elems() / e2e_s / 1e9
 
     # roofline of the dominant kernel (leaf hash), timed by events on its stream
@@ -318,7 +326,8 @@ def run_v3c(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(args.workload, s),
             "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": int(x.nbytes),
-                    "d2h_bytes_per_step": int(32 << s.cap_height), "ms_per_step": e2e_s * 1e3},
+                    "d2h_bytes_per_step": int(32 << s.cap_height), "ms_per_step": e2e_s * 1e3,
+                    "clocks": e2e_clk},
             "gpu_launches": int(launches),
             "clocks": clk,
             "roofline": {"bound": "alu", "kernel": "k_leaf_hash", "achieved": achieved, "peak": peak,

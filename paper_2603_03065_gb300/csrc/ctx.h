@@ -25,6 +25,9 @@ extern thread_local int g_dev_cache;
 
 using namespace v3c;
 
+// Column chunks per large host input on the direct commit path.
+constexpr v3c::u32 kCopyChunks = 4;
+
 // ---------------------------------------------------------------- context
 
 struct PlanEntry {
@@ -95,6 +98,10 @@ struct v3c_ctx {
     std::unordered_map<u64, SnapState*> snaps;   // snapshot commitments (snapshot.cu)
     SnapCbCache* snap_cb = nullptr;              // codebook-digest cache (snapshot.cu)
     cudaStream_t release_stream = nullptr;  // orders frees of resident objects
+    // Chunked input copies of large host inputs (commit_locked).
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_fork = nullptr;
+    std::vector<cudaEvent_t> copy_events;
     // CUDA graphs of batch signatures, and the autotuner's per-shape choices
     std::unordered_map<std::string, GraphSet> graphs;
     std::unordered_map<std::string, int> graph_seen;
@@ -166,6 +173,17 @@ struct Batch {
         // Merkle launches: one per level while the level has enough nodes to
         // fill the GPU with one compression per thread, then one launch that
         // folds up to 8 levels per CTA in shared memory.
+        fac.clear();
+        fbc.clear();
+        for (auto& g : chunks) {
+            std::vector<u32> a(1, 0), b(1, 0);
+            for (u32 k = g.first; k < g.first + g.second; k++) {
+                a.push_back(a.back() + stage_a_items(lde[k], t));
+                b.push_back(b.back() + stage_b_items(lde[k]));
+            }
+            fac.push_back(a);
+            fbc.push_back(b);
+        }
         fm.clear();
         mgroups.clear();
         for (u32 lev0 = 0; lev0 < max_top;) {
@@ -183,6 +201,12 @@ struct Batch {
     std::vector<std::pair<u32, u32>> mgroups;  // (first level, levels) of each Merkle launch
     u32 h_threads = 0;                          // leaf-hash CTA size (0 = context default)
     bool leaves_ready = false;                  // level 0 of every tree is already written: no leaf hash
+    // Column chunks whose inputs arrive by separate copies: stages A and B
+    // run per chunk, each after its copy's event; stage C and the trees run
+    // once over all jobs.  Empty: one launch per stage over all jobs.
+    std::vector<std::pair<u32, u32>> chunks;    // (first LDE job, job count)
+    std::vector<cudaEvent_t> chunk_ready;       // one per chunk, recorded after its copy
+    std::vector<std::vector<u32>> fac, fbc;     // per-chunk stage A / B item prefixes
 };
 
 

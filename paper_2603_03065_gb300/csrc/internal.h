@@ -43,7 +43,7 @@ struct LdeJob {
     u32 c_q;       // Z block: q values per block (power of two, <= M)
     u32 c_qc;      // stage C: q values per CTA (power of two, <= c_q)
     u32 kcap;      // largest radix exponent of the in-register DFT passes (1..4)
-    u32 pad;
+    u32 wcols;     // columns writable from lde: ld for a whole matrix, fewer for a column chunk
 };
 
 // Tile choice of one (log_n, rate_bits) shape, from the autotuner.

@@ -103,6 +103,7 @@ extern "C" v3c_status v3c_lde_noalloc(const uint64_t* d_cols, uint32_t c, uint32
     j.x = d_cols;
     j.c = c;
     j.ld = ld;
+    j.wcols = ld;
     j.lde = d_lde;
     j.vec_ok = ((uintptr_t)d_lde % 16 == 0) && (ld % 2 == 0);
     if (l1) {

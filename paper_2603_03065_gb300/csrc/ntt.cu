@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
             }
         } else {
             // n1 = 1: this CTA holds the whole column; write committed rows.
-            const bool pad = (col + 1 == J.c) && (J.c & 1) && J.c < J.ld;
+            const bool pad = (col + 1 == J.c) && (J.c & 1) && J.c < J.wcols;
             for (u32 e = threadIdx.x; e < M; e += blockDim.x) {
                 size_t row = gl::bitrev(e, lM);
                 __stcs(J.lde + row * J.ld + col, data[sw(e)]);
@@ -533,11 +533,11 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
             u64* dst = J.lde + row * J.ld + c0;
 #pragma unroll
             for (u32 p = 0; p < kStageCCols; p += 2) {
-                if (J.vec_ok && c0 + p + 2 <= J.ld) {
+                if (J.vec_ok && c0 + p + 2 <= J.wcols) {
                     __stcs(reinterpret_cast<ulonglong2*>(dst + p), make_ulonglong2(a[p], a[p + 1]));
                 } else {
-                    if (c0 + p < J.ld) __stcs(dst + p, a[p]);
-                    if (c0 + p + 1 < J.ld) __stcs(dst + p + 1, a[p + 1]);
+                    if (c0 + p < J.wcols) __stcs(dst + p, a[p]);
+                    if (c0 + p + 1 < J.wcols) __stcs(dst + p + 1, a[p + 1]);
                 }
             }
         }

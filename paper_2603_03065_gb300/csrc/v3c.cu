@@ -211,6 +211,8 @@ static void build_blob(Batch& b, std::vector<char>& blob, std::vector<size_t>& o
     parts.push_back({b.fc.data(), b.fc.size() * 4});
     parts.push_back({b.fl.data(), b.fl.size() * 4});
     for (auto& f : b.fm) parts.push_back({f.data(), f.size() * 4});
+    for (auto& f : b.fac) parts.push_back({f.data(), f.size() * 4});
+    for (auto& f : b.fbc) parts.push_back({f.data(), f.size() * 4});
     off.clear();
     size_t total = 0;
     for (auto& p : parts) {
@@ -248,7 +250,28 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
         return V3C_OK;
     };
     v3c_status st;
-    if (nl) {
+    if (nl && !b.chunks.empty()) {
+        // Per column chunk: wait for its input copy, then stages A and B.
+        const size_t base = 6 + b.fm.size();
+        for (size_t g = 0; g < b.chunks.size(); g++) {
+            CK(cudaStreamWaitEvent(s, b.chunk_ready[g], 0));
+            const LdeJob* dj = dl + b.chunks[g].first;
+            const u32 nj = b.chunks[g].second;
+            StageList la = list(base + g, b.fac[g], nj), lb = list(base + b.chunks.size() + g, b.fbc[g], nj);
+            if (la.total) {
+                StageTimer tm(ctx, timed ? 0 : -1, s);
+                CK(launch_stage_a(dj, la, b.smem_a, t, 0, s));
+                tm.done();
+                ctx->launches++;
+            }
+            if (lb.total) {
+                StageTimer tm(ctx, timed ? 1 : -1, s);
+                CK(launch_stage_b(dj, lb, b.smem_b, t, 0, s));
+                tm.done();
+                ctx->launches++;
+            }
+        }
+    } else if (nl) {
         st = stage(0, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
                          cudaStream_t s) { return launch_stage_a(dl, l, b.smem_a, t, 0, s); },
                    list(2, b.fa, nl), 0);
@@ -257,6 +280,8 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
                          cudaStream_t s) { return launch_stage_b(dl, l, b.smem_b, t, 0, s); },
                    list(3, b.fb, nl), 0);
         if (st) return st;
+    }
+    if (nl) {
         st = stage(2, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
                          cudaStream_t s) { return launch_stage_c(dl, l, b.smem_c, t, 0, s); },
                    list(4, b.fc, nl), 0);
@@ -400,6 +425,7 @@ static v3c_status make_lde_job(v3c_ctx* ctx, const u64* x, u32 c, u32 log_n, u32
     j.x = x;
     j.c = c;
     j.ld = ld;
+    j.wcols = ld;
     j.lde = lde;
     j.vec_ok = ((uintptr_t)lde % 16 == 0) && (ld % 2 == 0);
     if (j.plan.log_n1) {
@@ -666,6 +692,9 @@ v3c_status v3c_destroy(v3c_ctx* ctx)
     if (ctx->arena.ev) cudaEventDestroy(ctx->arena.ev);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
     if (ctx->release_stream) cudaStreamDestroy(ctx->release_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->copy_fork) cudaEventDestroy(ctx->copy_fork);
+    for (auto e : ctx->copy_events) cudaEventDestroy(e);
     for (auto& kv : ctx->graphs)
         for (auto& gi : kv.second.inst) {
             if (gi.exec) cudaGraphExecDestroy(gi.exec);
@@ -820,11 +849,68 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
     }
     Batch b;
     size_t aoff = 0;
+    // Large host inputs on the direct commit path are copied in column chunks
+    // on the context's copy stream; stages A and B of a chunk start when its
+    // copy lands, so the transfer overlaps the first chunks' DFTs.
+    const bool may_chunk = !arena_override && allow_graph && !(ctx->cfg.flags & V3C_FLAG_VALIDATE);
+    bool forked = false;
     for (u32 i = 0; i < nb; i++) {
         const v3c_commit_desc& d = descs[i];
         Object& o = objs[i];
         const u64* x = d.cols;
         size_t n = (size_t)1 << d.log_n;
+        if (may_chunk && d.on_device != V3C_INPUT_DEVICE && d.c >= 16 && ((size_t)d.c << d.log_n) >= ((size_t)1 << 22)) {
+            if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+            if (!forked) {
+                // The copies overwrite arena words that earlier work on s may still read.
+                if (!ctx->copy_fork) CK(cudaEventCreateWithFlags(&ctx->copy_fork, cudaEventDisableTiming));
+                CK(cudaEventRecord(ctx->copy_fork, s));
+                CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_fork, 0));
+                forked = true;
+            }
+            const u32 per = ((d.c + kCopyChunks - 1) / kCopyChunks + 3) & ~3u;  // columns per chunk, multiple of 4
+            for (u32 c0 = 0; c0 < d.c; c0 += per) {
+                const u32 ck = std::min(per, d.c - c0);
+                u64* dst = arena + aoff;
+                aoff += (size_t)ck * n;
+                size_t sw = lde_scratch_words(ck, d.log_n, d.rate_bits);
+                u64* scr = sw ? arena + aoff : nullptr;
+                aoff += sw;
+                cudaError_t e = cudaMemcpyAsync(dst, d.cols + (size_t)c0 * n, (size_t)ck * n * 8,
+                                                cudaMemcpyHostToDevice, ctx->copy_stream);
+                const size_t g = b.chunks.size();
+                while (ctx->copy_events.size() <= g) {
+                    cudaEvent_t ev = nullptr;
+                    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+                    if (e != cudaSuccess) break;
+                    ctx->copy_events.push_back(ev);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_events[g], ctx->copy_stream);
+                if (e != cudaSuccess) {
+                    rollback(nb);
+                    return fail(ctx, V3C_ECUDA, "input copy: %s", cudaGetErrorString(e));
+                }
+                LdeJob j;
+                st = make_lde_job(ctx, dst, ck, d.log_n, d.rate_bits, o.lde + c0, o.ld, scr, s, &j);
+                if (st) {
+                    rollback(nb);
+                    return st;
+                }
+                j.wcols = o.ld - c0;
+                j.vec_ok = j.vec_ok && (c0 % 2 == 0);
+                b.chunks.push_back({(u32)b.lde.size(), 1});
+                b.chunk_ready.push_back(ctx->copy_events[g]);
+                b.lde.push_back(j);
+            }
+            b.tree.push_back(make_tree_job(o.lde, o.ld, d.c, d.log_n + d.rate_bits, d.cap_height, o.tree, o.cap));
+            continue;
+        }
+        if (!b.chunks.empty()) {
+            // Jobs outside the chunked inputs form one more group, ready at once.
+            b.chunks.push_back({(u32)b.lde.size(), 1});
+            if (!ctx->copy_fork) CK(cudaEventCreateWithFlags(&ctx->copy_fork, cudaEventDisableTiming));
+            b.chunk_ready.push_back(ctx->copy_fork);
+        }
         if (d.on_device != V3C_INPUT_DEVICE) {
             u64* dst = arena + aoff;
             aoff += d.c * n;
@@ -867,9 +953,18 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         }
     }
     b.h_threads = h_threads;
-    // Replay a captured graph of this batch signature unless graphs are off
-    // or per-stage timing (events around each launch) is requested.
-    if (!allow_graph || (ctx->cfg.flags & (V3C_FLAG_NO_GRAPH | V3C_FLAG_TIMING))) st = launch_batch(ctx, b, s);
+    if (!b.chunks.empty()) {
+        // Jobs before the first chunked input form a group of their own, ready at once.
+        if (b.chunks.front().first > 0) {
+            b.chunks.insert(b.chunks.begin(), {0u, b.chunks.front().first});
+            b.chunk_ready.insert(b.chunk_ready.begin(), ctx->copy_fork);
+        }
+    }
+    // Replay a captured graph of this batch signature unless graphs are off,
+    // per-stage timing (events around each launch) is requested, or inputs
+    // arrive in chunks on the copy stream.
+    if (!allow_graph || !b.chunks.empty() || (ctx->cfg.flags & (V3C_FLAG_NO_GRAPH | V3C_FLAG_TIMING)))
+        st = launch_batch(ctx, b, s);
     else st = launch_batch_graph(ctx, b, s);
     if (st) {
         rollback(nb);

@@ -300,3 +300,30 @@ def test_autotuned_commit_matches_oracle(v3c):
             cid = ctx.commit([(x, r, h)])[0]
             check_object(ctx, cid, x, r, h)
             ctx.release(cid)
+
+
+# Large host inputs are copied in column chunks on a copy stream, and the
+# LDE's first stages run per chunk as the copies land.
+@pytest.mark.parametrize("c,log_n,r,h", [(135, 16, 3, 4), (65, 16, 2, 2), (4099, 10, 2, 3)])
+def test_chunked_host_input_commit(v3c, ctx, c, log_n, r, h):
+    x = synth.columns(seed=c + log_n, c=c, log_n=log_n, mix="trace")
+    cid = ctx.commit([(x, r, h)])[0]
+    got = ctx.commit_views(cid, c)
+    lde, tree, cap = oracle.commit(x, r, h)
+    assert np.array_equal(got["lde"].reshape(lde.shape), lde)
+    assert np.array_equal(got["cap"].reshape(cap.shape), cap)
+    assert np.array_equal(got["tree"], tree)
+    ctx.release(cid)
+
+
+def test_chunked_and_plain_inputs_in_one_batch(v3c, ctx):
+    a = synth.columns(seed=1, c=9, log_n=12, mix="trace")     # device input
+    b = synth.columns(seed=2, c=40, log_n=17, mix="trace")    # host, chunked
+    c_ = synth.columns(seed=3, c=7, log_n=11, mix="trace")    # host, small
+    ids = ctx.commit([(v3c.to_device_u64(a), 3, 2), (b, 2, 4), (c_, 1, 0)])
+    for cid, (x, r, h) in zip(ids, [(a, 3, 2), (b, 2, 4), (c_, 1, 0)]):
+        got = ctx.commit_views(cid, x.shape[0])
+        lde, tree, cap = oracle.commit(x, r, h)
+        assert np.array_equal(got["lde"].reshape(lde.shape), lde)
+        assert np.array_equal(got["cap"].reshape(cap.shape), cap)
+        ctx.release(cid)
