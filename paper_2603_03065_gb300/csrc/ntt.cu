@@ -44,7 +44,7 @@ size_t plan_table_words(u32 log_n, u32 r)
 {
     u32 l1, l2;
     plan_split(log_n, r, l1, l2);
-    size_t n = (size_t)1 << log_n, N = n << r;
+    size_t n = (size_t)1 << log_n;
     size_t w = n;                          // scale
     if (l1) w += n + kPowWords;            // twa, pw_N
     w += half_or_one(l1) * 2 + half_or_one(l2) + half_or_one(l2 + r);
@@ -120,7 +120,7 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
     p.log_n2 = l2;
     p.log_M = l2 + p.r;
     p.log_N = p.log_n + p.r;
-    size_t n = (size_t)1 << p.log_n, N = n << p.r;
+    size_t n = (size_t)1 << p.log_n;
     TableArgs a;
     u64* cur = base;
     a.twa = l1 ? cur : nullptr;

@@ -41,6 +41,8 @@ __constant__ u64 c_rc_full[8 * 12] = V3C_FAST_RC_FULL_INIT;
 __constant__ u32 c_rc_limbs[31 * 12 * 3] = V3C_RC_LIMBS_INIT;
 // Round constants for the split MDS [round 0..30][36] (see gen_params.cpp).
 __constant__ u32 c_rc_split[31 * 36] = V3C_RC_SPLIT_INIT;
+// Zero accumulator starts, for an MDS that adds no constant.
+__constant__ u32 c_zero36[36] = {0};
 
 __host__ __device__ constexpr u32 mds_coef(int k)
 {
@@ -398,11 +400,11 @@ __device__ __forceinline__ void mds_split(u64 (&s)[12], const u32* init)
 template <class C>
 __device__ __forceinline__ void mds(u64 (&s)[12], const u32* init = nullptr)
 {
-    u64 out[12];
-    if (C::MDS == MDS_SPLIT) {
-        mds_split<C>(s, init);
+    if constexpr (C::MDS == MDS_SPLIT) {
+        mds_split<C>(s, init ? init : c_zero36);
         return;
     }
+    u64 out[12];
     if (C::MDS == MDS_LIMB) {
         u32 a[12], b[12], c[12];
 #pragma unroll
@@ -458,7 +460,7 @@ __device__ __forceinline__ void mds(u64 (&s)[12], const u32* init = nullptr)
 template <class C>
 __device__ __forceinline__ void permute_plain(u64 (&s)[12])
 {
-    if (C::ARCM) {
+    if constexpr (C::ARCM) {
         // Round 0's constants are added here; every MDS adds the next round's.
 #pragma unroll
         for (int i = 0; i < 12; i++) s[i] = gl::add_nc_small(s[i], c_rc[0][i]);
@@ -472,19 +474,19 @@ __device__ __forceinline__ void permute_plain(u64 (&s)[12])
             }
             mds<C>(s, (C::MDS == MDS_SPLIT ? c_rc_split : c_rc_limbs) + (r + 1) * 36);
         }
-        return;
-    }
+    } else {
 #pragma unroll 1
-    for (int r = 0; r < 30; r++) {
-        if (r < 4 || r >= 26) {
+        for (int r = 0; r < 30; r++) {
+            if (r < 4 || r >= 26) {
 #pragma unroll
-            for (int i = 0; i < 12; i++) s[i] = sbox<C>(gl::add_nc_small(s[i], c_rc[r][i]));
-        } else {
+                for (int i = 0; i < 12; i++) s[i] = sbox<C>(gl::add_nc_small(s[i], c_rc[r][i]));
+            } else {
 #pragma unroll
-            for (int i = 0; i < 12; i++) s[i] = gl::add_nc_small(s[i], c_rc[r][i]);
-            s[0] = sbox<C>(s[0]);
+                for (int i = 0; i < 12; i++) s[i] = gl::add_nc_small(s[i], c_rc[r][i]);
+                s[0] = sbox<C>(s[0]);
+            }
+            mds<C>(s);
         }
-        mds<C>(s);
     }
 }
 
@@ -500,6 +502,15 @@ template <class C>
 __device__ __forceinline__ void acc_add(Acc& a, u64 x, u64 k)
 {
     U128 p = mul128<C>(x, k);
+    if (C::RED) {
+        // (lo, hi, top) += p as one carry chain.
+        asm("add.cc.u64 %0, %0, %3;\n\t"
+            "addc.cc.u64 %1, %1, %4;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "+l"(a.lo), "+l"(a.hi), "+r"(a.top)
+            : "l"(p.lo), "l"(p.hi));
+        return;
+    }
     u64 lo = a.lo + p.lo;
     u64 c1 = lo < p.lo;
     u64 hi = a.hi + p.hi;
@@ -514,7 +525,7 @@ __device__ __forceinline__ void acc_add(Acc& a, u64 x, u64 k)
 // lo + 2^64 hi + 2^128 top (top < 2^32) to [0, 2^64); 2^128 = -2^32 (mod p).
 __device__ __forceinline__ u64 acc_reduce(const Acc& a)
 {
-    u64 r = gl::reduce128(a.lo, a.hi);
+    u64 r = gl::reduce128_ptx(a.lo, a.hi);
     u64 t = (u64)a.top << 32;
     u64 d = r - t;
     // On borrow d = r - t + 2^64 = r - t + EPS (mod p), and d >= 2^64 - 2^36 > EPS.
