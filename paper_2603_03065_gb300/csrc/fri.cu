@@ -100,10 +100,14 @@ __device__ __forceinline__ u64 fold192(u64 lo, u64 mid, u32 hi)
     return gl::sub(gl::canon(gl::reduce128_ptx(lo, mid)), (u64)hi << 32);
 }
 
+// Column pairs loaded per iteration of the combine: 4 pairs are one 64-byte
+// run (two whole sectors) per thread; 8 measured no faster.
+constexpr int kCombPairs = 4;
+
 // f[t] (+)= sum_{i<c} pw[i] row_t[i].  One thread per row: 16-byte loads of
-// column pairs, four pairs (one 64-byte run, two whole sectors) per
-// iteration, products summed unreduced and reduced once per row.  The
-// powers pw[i] are the same for every thread of a warp (broadcast loads).
+// column pairs, kCombPairs pairs per iteration, products summed unreduced
+// and reduced once per row.  The powers pw[i] are the same for every thread
+// of a warp (broadcast loads).
 // Rows are 16-byte aligned (ld even); c < 2^31.
 __global__ void __launch_bounds__(256) k_fri_combine(const u64* __restrict__ rows, u32 ld, u32 c,
                                                      const u64* __restrict__ pw, u64 nrows, int acc,
@@ -115,12 +119,12 @@ __global__ void __launch_bounds__(256) k_fri_combine(const u64* __restrict__ row
         u64 lo = 0, mid = 0;
         u32 hi = 0;
         u32 k = 0;
-        for (; k + 4 <= pairs; k += 4) {
-            ulonglong2 v[4];
+        for (; k + kCombPairs <= pairs; k += kCombPairs) {
+            ulonglong2 v[kCombPairs];
 #pragma unroll
-            for (int j = 0; j < 4; j++) v[j] = __ldg(row + k + j);
+            for (int j = 0; j < kCombPairs; j++) v[j] = __ldg(row + k + j);
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
+            for (int j = 0; j < kCombPairs; j++) {
                 mac192(lo, mid, hi, v[j].x, __ldg(pw + 2 * (k + j)));
                 mac192(lo, mid, hi, v[j].y, __ldg(pw + 2 * (k + j) + 1));
             }

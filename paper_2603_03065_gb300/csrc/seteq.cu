@@ -8,13 +8,14 @@
 // (2) One CTA per instance scans the tile products: the prefix of
 // numerators before each tile, the suffix of denominators after it, and the
 // inverse of the full denominator product (the instance's only inversion).
-// (3) Every tile recomputes its elements, scans them with warp shuffles and
-// one shared-memory step per CTA, and writes
+// (3) Every tile reads its numerators and denominators back, scans them with
+// warp shuffles and one shared-memory step per CTA, and writes
 // Z_i = N_{<i} * D_{>=i} * D_all^-1.  Loads and stores are coalesced: the
 // order-free product of phase 1 takes strided elements, and phase 3
 // transposes through shared memory.
-// Each launch streams X and Y once (phase 1 and 3) or touches only tile
-// products (phase 2).
+// X and Y are read once (phase 1); the compressed terms cost 16 bytes per
+// tuple to write and read back instead of a second pass over X, Y and the
+// Horner evaluations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +42,7 @@ struct SeqJob {
     u64* z;
     u64 L;
     u64 alpha, beta;
+    ulonglong2* nd;  // [L]: (alpha - x_i, alpha - y_i), written by phase 1, read by phase 3
     u64* agg;     // [ntiles][2]: tile products of numerators, denominators
     u64* carry;   // [ntiles][2]: numerator product before, denominator product after the tile
     u64* inv;     // [2]: inverse of the denominator product (0 if it is 0), status
@@ -63,10 +65,11 @@ __device__ __forceinline__ u32 seq_find(const SeqJob* __restrict__ jobs, u32 njo
 
 __device__ __forceinline__ u64 compress(const u64* __restrict__ t, u32 T, u64 beta)
 {
-    // Horner from the last component: sum_k t_k beta^k.
+    // Horner from the last component: sum_k t_k beta^k, on values in
+    // [0, 2^64) congruent mod p, canonical at the end.
     u64 s = __ldg(t + T - 1);
-    for (int k = (int)T - 2; k >= 0; k--) s = gl::add(gl::mul(s, beta), __ldg(t + k));
-    return s;
+    for (int k = (int)T - 2; k >= 0; k--) s = gl::add_nc(gl::mul_nc(s, beta), __ldg(t + k));
+    return gl::canon(s);
 }
 
 // numerator and denominator of element e (1 and 1 past the end).
@@ -126,8 +129,10 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_reduce(const SeqJob* __re
         u64 pn = 1, pd = 1;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
+            const u64 e = base + (u64)k * kSeqThreads;
             u64 n, d;
-            seq_terms(J, base + (u64)k * kSeqThreads, n, d);
+            seq_terms(J, e, n, d);
+            if (e < J.L) J.nd[e] = make_ulonglong2(n, d);
             pn = gl::mul(pn, n);
             pd = gl::mul(pd, d);
         }
@@ -205,10 +210,9 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __res
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
             const u32 i = t + k * kSeqThreads;
-            u64 n, d;
-            seq_terms(J, tbase + i, n, d);
-            s_num[seq_pad(i)] = n;
-            s_den[seq_pad(i)] = d;
+            ulonglong2 v = tbase + i < J.L ? __ldcs(J.nd + tbase + i) : make_ulonglong2(1, 1);
+            s_num[seq_pad(i)] = v.x;
+            s_den[seq_pad(i)] = v.y;
         }
         __syncthreads();
         u64 num[kSeqPer], den[kSeqPer];
@@ -270,14 +274,18 @@ extern "C" v3c_status v3c_seteq(v3c_ctx* ctx, const v3c_seteq_desc* descs, uint3
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> g(ctx->mu);
     // Scratch: jobs, per-tile products and carries, per-instance inverse/status.
-    const size_t job_words = (sizeof(SeqJob) * n + 7) / 8;
-    const size_t words = job_words + 4 * tiles + 2 * (size_t)n;
+    u64 elems = 0;
+    for (u32 i = 0; i < n; i++) elems += descs[i].L;
+    const size_t job_words = (sizeof(SeqJob) * n + 15) / 16 * 2;  // an even word count
+    const size_t words = job_words + 4 * tiles + 2 * (size_t)n + 2 * elems;
     u64* mem = nullptr;
     CK(cudaMallocAsync((void**)&mem, words * 8, s));
     std::vector<SeqJob> jobs(n);
     u64* agg = mem + job_words;
     u64* carry = agg + 2 * tiles;
     u64* inv = carry + 2 * tiles;
+    u64* nd = inv + 2 * (size_t)n;  // 16-byte aligned: every earlier part has an even word count
+    u64 e0 = 0;
     u32 t0 = 0;
     for (u32 i = 0; i < n; i++) {
         const v3c_seteq_desc& d = descs[i];
@@ -295,6 +303,8 @@ extern "C" v3c_status v3c_seteq(v3c_ctx* ctx, const v3c_seteq_desc* descs, uint3
         J.agg = agg + 2 * (size_t)t0;
         J.carry = carry + 2 * (size_t)t0;
         J.inv = inv + 2 * (size_t)i;
+        J.nd = reinterpret_cast<ulonglong2*>(nd + 2 * e0);
+        e0 += d.L;
         t0 += J.ntiles;
     }
     cudaError_t e = cudaMemcpyAsync(mem, jobs.data(), sizeof(SeqJob) * n, cudaMemcpyHostToDevice, s);
