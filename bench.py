@@ -246,7 +246,7 @@ def run_v3c(args):
     torch.cuda.set_device(local_rank)
     s = shard_workload(WORKLOADS[args.workload], rank)
     x = s.inputs()
-    ctx = v3c.Context(local_rank, flags=v3c.FLAG_TIMING)
+    ctx = v3c.Context(local_rank, flags=v3c.FLAG_TIMING, autotune=args.autotune)
     stream = torch.cuda.current_stream()
     d_x = v3c.to_device_u64(x)
 
@@ -324,7 +324,7 @@ def run_v3c(args):
             "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(args.workload, s),
+            "config": dict(workload_config(args.workload, s), autotune=bool(args.autotune)),
             "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(32 << s.cap_height), "ms_per_step": e2e_s * 1e3,
                     "clocks": e2e_clk},
@@ -913,6 +913,8 @@ def main():
                     default="large_135x2_20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--int-peak", action="store_true", help="also run the integer-pipe microbenchmark")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the library time its tile choices for the shape during the warm-up")
     ap.add_argument("--rate", type=float, default=200.0, help="serve_poisson: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve_poisson: trace length in seconds")
     ap.add_argument("--max-batch", type=int, default=32, help="serve_poisson: requests per batched pass")
