@@ -327,3 +327,31 @@ def test_chunked_and_plain_inputs_in_one_batch(v3c, ctx):
         assert np.array_equal(got["lde"].reshape(lde.shape), lde)
         assert np.array_equal(got["cap"].reshape(cap.shape), cap)
         ctx.release(cid)
+
+
+def test_maximum_size_commit_sampled(v3c):
+    # The largest shape the library accepts: 2^22 input rows at rate 3, i.e.
+    # 2^25 LDE rows (the V3C_MAX_LOG_LDE limit).  Three columns (rows of
+    # width <= 4 are their own zero-padded leaf digests).  Sampled rows are
+    # checked against the oracle's Horner evaluation, and their Merkle paths,
+    # read back with the batched opening, must verify against the GPU's cap.
+    import torch
+
+    c, log_n, r, h = 3, 22, 3, 4
+    x = synth.columns(seed=2222, c=c, log_n=log_n, mix="trace")
+    with v3c.Context(0) as big:
+        cid = big.commit([(v3c.to_device_u64(x), r, h)])[0]
+        torch.cuda.synchronize()
+        N = 1 << (log_n + r)
+        rng = np.random.default_rng(22)
+        rows = np.unique(np.concatenate([[0, 1, N - 1, N // 2], rng.integers(0, N, size=8)])).astype(np.uint64)
+        got_rows, paths = big.open_batch(cid, rows, c)
+        want_rows = oracle.lde_rows(oracle.coeffs(x), r, rows)
+        assert np.array_equal(got_rows, want_rows)
+        cap = big.cap(cid)
+        for q, t in enumerate(rows):
+            assert oracle.merkle_verify(want_rows[q], c, log_n + r, h, int(t), paths[q], cap)
+        big.release(cid)
+    with v3c.Context(0) as small:
+        with pytest.raises(v3c.V3CError):
+            small.commit([(v3c.to_device_u64(synth.columns(seed=1, c=1, log_n=log_n, mix="uniform")), 4, 0)])
