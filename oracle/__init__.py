@@ -74,6 +74,11 @@ def lib():
                 "orc_fri_fold_coset": (u64, [_u64p, u32, u64, u32, u64, u64]),
                 "orc_fri_fold": (i32, [_u64p, u32, u64, u32, u64, _u64p, i32]),
                 "orc_fri_interpolate": (i32, [_u64p, u32, u64, _u64p]),
+                "orc_ext_mul": (None, [_u64p, _u64p, _u64p]),
+                "orc_ext_inv": (None, [_u64p, _u64p]),
+                "orc_fri_combine_ext": (i32, [_u64p, u32, u32, u64, _u64p, u64, i32, _u64p, i32]),
+                "orc_fri_fold_coset_ext": (None, [_u64p, u32, u64, u32, _u64p, u64, _u64p]),
+                "orc_fri_fold_ext": (i32, [_u64p, u32, u64, u32, _u64p, _u64p, i32]),
                 "orc_snapshot_slot_leaves": (i32, [_u64p, u32, u32, u32, _u64p, i32]),
                 "orc_snapshot_list_root": (i32, [_u64p, u64, u32, u32, _u64p]),
                 "orc_compress_tuple": (u64, [_u64p, u32, u64]),
@@ -283,37 +288,79 @@ def domain_log2(G: int) -> int:
 GENERATOR = 7
 
 
-def fri_combine(ldes, widths, alpha: int, threads: int | None = None) -> np.ndarray:
+def ext_mul(a, b) -> tuple[int, int]:
+    """(a0 + a1 u)(b0 + b1 u) in F_p[u] / (u^2 - 7)."""
+    x, y, out = _u64(a), _u64(b), np.zeros(2, np.uint64)
+    lib().orc_ext_mul(_p(x), _p(y), _p(out))
+    return int(out[0]), int(out[1])
+
+
+def ext_inv(a) -> tuple[int, int]:
+    x, out = _u64(a), np.zeros(2, np.uint64)
+    lib().orc_ext_inv(_p(x), _p(out))
+    return int(out[0]), int(out[1])
+
+
+def _ext_pair(v, ext: int):
+    return [int(v)] if ext == 1 else [int(v[0]), int(v[1])]
+
+
+def fri_combine(ldes, widths, alpha, threads: int | None = None, ext: int = 1) -> np.ndarray:
     """f_0[t] = sum over the committed matrices, in order, of alpha^e row_t[i],
-    with e running on from one matrix to the next."""
+    with e running on from one matrix to the next.  ext = 2: alpha = (re, im)
+    in F_p[u]/(u^2 - 7) and the result has shape [N][2]."""
     f = None
     e0 = 0
     for m, c in zip(ldes, widths):
         a = _u64(m)
         nrows, ld = a.shape
-        if f is None:
-            f = np.zeros(nrows, np.uint64)
-        assert lib().orc_fri_combine(_p(a), ld, c, nrows, alpha, e0, 1, _p(f),
-                                     threads or default_threads()) == 0
+        if ext == 1:
+            if f is None:
+                f = np.zeros(nrows, np.uint64)
+            assert lib().orc_fri_combine(_p(a), ld, c, nrows, int(alpha), e0, 1, _p(f),
+                                         threads or default_threads()) == 0
+        else:
+            if f is None:
+                f = np.zeros((nrows, 2), np.uint64)
+            al = _u64(_ext_pair(alpha, 2))
+            assert lib().orc_fri_combine_ext(_p(a), ld, c, nrows, _p(al), e0, 1, _p(f),
+                                             threads or default_threads()) == 0
         e0 += c
     return f
 
 
-def fri_fold(f, shift: int, arity_bits: int, beta: int, threads: int | None = None) -> np.ndarray:
+def fri_fold(f, shift: int, arity_bits: int, beta, threads: int | None = None, ext: int = 1) -> np.ndarray:
     a = _u64(f)
-    logm = a.size.bit_length() - 1
-    out = np.empty(a.size >> arity_bits, np.uint64)
-    assert lib().orc_fri_fold(_p(a), logm, shift, arity_bits, beta, _p(out),
-                              threads or default_threads()) == 0
+    m = a.shape[0]
+    logm = m.bit_length() - 1
+    if ext == 1:
+        out = np.empty(m >> arity_bits, np.uint64)
+        assert lib().orc_fri_fold(_p(a), logm, shift, arity_bits, int(beta), _p(out),
+                                  threads or default_threads()) == 0
+    else:
+        out = np.empty((m >> arity_bits, 2), np.uint64)
+        b = _u64(_ext_pair(beta, 2))
+        assert lib().orc_fri_fold_ext(_p(a), logm, shift, arity_bits, _p(b), _p(out),
+                                      threads or default_threads()) == 0
     return out
 
 
-def fri_fold_coset(vals, logm: int, shift: int, arity_bits: int, beta: int, w: int) -> int:
-    return int(lib().orc_fri_fold_coset(_p(_u64(vals)), logm, shift, arity_bits, beta, w))
+def fri_fold_coset(vals, logm: int, shift: int, arity_bits: int, beta, w: int, ext: int = 1):
+    if ext == 1:
+        return int(lib().orc_fri_fold_coset(_p(_u64(vals)), logm, shift, arity_bits, int(beta), w))
+    out = np.zeros(2, np.uint64)
+    lib().orc_fri_fold_coset_ext(_p(_u64(vals).reshape(-1)), logm, shift, arity_bits,
+                                 _p(_u64(_ext_pair(beta, 2))), w, _p(out))
+    return int(out[0]), int(out[1])
 
 
 def fri_interpolate(f, shift: int) -> np.ndarray:
+    """Coefficients of the polynomial with values f on the coset (bit-reversed
+    order).  Extension values ([m][2]) interpolate componentwise: the DFT is
+    linear over F_p."""
     a = _u64(f)
+    if a.ndim == 2:
+        return np.stack([fri_interpolate(np.ascontiguousarray(a[:, k]), shift) for k in range(a.shape[1])], axis=1)
     out = np.empty_like(a)
     assert lib().orc_fri_interpolate(_p(a), a.size.bit_length() - 1, shift, _p(out)) == 0
     return out
@@ -330,68 +377,73 @@ def fri_arities(log_N: int, arity_bits: int, final_log: int) -> list[int]:
     return out
 
 
-def fri_commit(ldes, widths, alpha: int, betas, arity_bits: int, final_log: int, cap_height: int,
-               threads: int | None = None) -> dict:
+def fri_commit(ldes, widths, alpha, betas, arity_bits: int, final_log: int, cap_height: int,
+               threads: int | None = None, ext: int = 1) -> dict:
     """Commit phase: layer k (k < R) is committed as a Merkle tree whose leaf w
-    is the coset [w 2^a_k, (w+1) 2^a_k) of the layer; the last layer is sent as
-    polynomial coefficients."""
-    f = fri_combine(ldes, widths, alpha, threads)
-    log_N = f.size.bit_length() - 1
+    is the coset [w 2^a_k, (w+1) 2^a_k) of the layer (2^a_k ext-word values,
+    flattened); the last layer is sent as polynomial coefficients."""
+    f = fri_combine(ldes, widths, alpha, threads, ext)
+    log_N = f.shape[0].bit_length() - 1
     ar = fri_arities(log_N, arity_bits, final_log)
     assert len(betas) >= len(ar)
     layers, trees, caps, shifts, heights = [f], [], [], [GENERATOR], []
     for k, a in enumerate(ar):
         cur = layers[-1]
-        logL = (cur.size.bit_length() - 1) - a
+        logL = (cur.shape[0].bit_length() - 1) - a
         h = min(cap_height, logL)
-        tree, cap = merkle(cur.reshape(-1, 1 << a), 1 << a, h, threads)
+        width = (1 << a) * ext
+        tree, cap = merkle(np.ascontiguousarray(cur).reshape(-1, width), width, h, threads)
         trees.append(tree)
         caps.append(cap)
         heights.append(h)
-        layers.append(fri_fold(cur, shifts[-1], a, betas[k], threads))
+        layers.append(fri_fold(cur, shifts[-1], a, betas[k], threads, ext))
         shifts.append(pow_(shifts[-1], 1 << a))
     final = fri_interpolate(layers[-1], shifts[-1])
-    return {"layers": layers, "trees": trees, "caps": caps, "shifts": shifts, "arities": ar,
-            "heights": heights, "final": final, "betas": [int(b) for b in betas[: len(ar)]]}
+    return {"layers": layers, "trees": trees, "caps": caps, "shifts": shifts, "arities": ar, "ext": ext,
+            "heights": heights, "final": final, "betas": list(betas[: len(ar)])}
 
 
 def fri_query(st: dict, t0: int) -> list[tuple[np.ndarray, np.ndarray]]:
     """Openings of query position t0 (in layer 0): per round, the coset values
-    holding the query's position and their Merkle path."""
+    holding the query's position (flattened) and their Merkle path."""
     out, t = [], t0
     for k, a in enumerate(st["arities"]):
         cur = st["layers"][k]
-        logL = (cur.size.bit_length() - 1) - a
+        logL = (cur.shape[0].bit_length() - 1) - a
         leaf = t >> a
-        vals = cur[leaf << a: (leaf + 1) << a].copy()
+        vals = np.ascontiguousarray(cur[leaf << a: (leaf + 1) << a]).reshape(-1).copy()
         path = merkle_path(st["trees"][k], logL, st["heights"][k], leaf)
         out.append((vals, path))
         t = leaf
     return out
 
 
-def fri_verify_query(caps, heights, arities, betas, final, log_N: int, t0: int, f0_value: int,
-                     openings) -> bool:
+def fri_verify_query(caps, heights, arities, betas, final, log_N: int, t0: int, f0_value, openings,
+                     ext: int = 1) -> bool:
     """Verifier side of one query: the opened cosets authenticate against the
     layer caps, hold the running value at the query position, and fold into
     the next layer's value; the last value equals the final polynomial at the
-    query's point."""
-    t, shift, logm, value = t0, GENERATOR, log_N, int(f0_value)
+    query's point.  ext = 2: values are (re, im) pairs."""
+    t, shift, logm = t0, GENERATOR, log_N
+    value = tuple(int(v) for v in (f0_value if ext == 2 else [f0_value]))
     for k, a in enumerate(arities):
         vals, path = openings[k]
         logL = logm - a
         leaf = t >> a
-        if int(vals[t & ((1 << a) - 1)]) != value:
+        pos = (t & ((1 << a) - 1)) * ext
+        if tuple(int(v) for v in vals[pos: pos + ext]) != value:
             return False
-        if not merkle_verify(vals, 1 << a, logL, heights[k], leaf, path, caps[k]):
+        if not merkle_verify(vals, (1 << a) * ext, logL, heights[k], leaf, path, caps[k]):
             return False
-        value = fri_fold_coset(vals, logm, shift, a, int(betas[k]), leaf)
+        got = fri_fold_coset(vals, logm, shift, a, betas[k], leaf, ext)
+        value = got if ext == 2 else (got,)
         t, logm, shift = leaf, logL, pow_(shift, 1 << a)
     x = mul(shift, pow_(root_of_unity(logm), bitrev(t, logm)))
-    acc = 0
-    for c in reversed([int(v) for v in final]):
-        acc = add(mul(acc, x), c)
-    return acc == value
+    fin = _u64(final).reshape(-1, ext)
+    acc = [0] * ext
+    for row in reversed(fin):
+        acc = [add(mul(acc[k], x), int(row[k])) for k in range(ext)]
+    return tuple(acc) == value
 
 
 # --- snapshot commitment (Sec. 4.3) ----------------------------------------

@@ -921,3 +921,141 @@ int orc_seteq_partial_products(const u64* X, const u64* Y, uint64_t L, uint32_t 
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* FRI over the quadratic extension F_p[u] / (u^2 - 7).  Plonky2's       */
+/* default FRI draws its challenges from a degree-2 extension (§5 names  */
+/* the default configuration); 7 generates F_p^*, so it is a quadratic   */
+/* non-residue and u^2 - 7 is irreducible.  An element is (re, im) =     */
+/* re + im u.  The LDE columns stay in F_p; the combination, the layers  */
+/* and the final coefficients are extension elements.                    */
+/* ------------------------------------------------------------------ */
+
+#define ORC_EXT_W 7ULL
+
+static void ext_mul(const u64* a, const u64* b, u64* out)
+{
+    u64 re = orc_add(orc_mul(a[0], b[0]), orc_mul(ORC_EXT_W, orc_mul(a[1], b[1])));
+    u64 im = orc_add(orc_mul(a[0], b[1]), orc_mul(a[1], b[0]));
+    out[0] = re;
+    out[1] = im;
+}
+
+/* 1 / (re + im u) = (re - im u) / (re^2 - 7 im^2). */
+static void ext_inv(const u64* a, u64* out)
+{
+    u64 n = orc_sub(orc_mul(a[0], a[0]), orc_mul(ORC_EXT_W, orc_mul(a[1], a[1])));
+    u64 ni = orc_inv(n);
+    out[0] = orc_mul(a[0], ni);
+    out[1] = orc_mul(orc_sub(0, a[1]), ni);
+}
+
+void orc_ext_mul(const u64* a, const u64* b, u64* out) { ext_mul(a, b, out); }
+void orc_ext_inv(const u64* a, u64* out) { ext_inv(a, out); }
+
+typedef struct {
+    const u64* rows;
+    uint32_t ld, c;
+    u64 alpha[2], a0[2];
+    int acc;
+    u64* out;
+} combine_ext_ctx;
+static void combine_ext_body(void* vctx, size_t t)
+{
+    combine_ext_ctx* C = (combine_ext_ctx*)vctx;
+    const u64* row = C->rows + t * C->ld;
+    u64 s[2] = {0, 0}, w[2] = {C->a0[0], C->a0[1]};
+    for (uint32_t i = 0; i < C->c; i++) {
+        s[0] = orc_add(s[0], orc_mul(w[0], row[i]));
+        s[1] = orc_add(s[1], orc_mul(w[1], row[i]));
+        u64 nw[2];
+        ext_mul(w, C->alpha, nw);
+        w[0] = nw[0];
+        w[1] = nw[1];
+    }
+    if (C->acc) {
+        C->out[2 * t] = orc_add(C->out[2 * t], s[0]);
+        C->out[2 * t + 1] = orc_add(C->out[2 * t + 1], s[1]);
+    } else {
+        C->out[2 * t] = s[0];
+        C->out[2 * t + 1] = s[1];
+    }
+}
+
+/* out[t] (+)= sum_{i<c} alpha^(e0+i) rows[t][i], alpha and out in F_p^2. */
+int orc_fri_combine_ext(const u64* rows, uint32_t ld, uint32_t c, uint64_t nrows, const u64* alpha, uint64_t e0,
+                        int acc, u64* out, int threads)
+{
+    combine_ext_ctx C;
+    C.rows = rows;
+    C.ld = ld;
+    C.c = c;
+    C.alpha[0] = alpha[0];
+    C.alpha[1] = alpha[1];
+    C.a0[0] = 1;
+    C.a0[1] = 0;
+    for (uint64_t k = 0; k < e0; k++) {
+        u64 nw[2];
+        ext_mul(C.a0, alpha, nw);
+        C.a0[0] = nw[0];
+        C.a0[1] = nw[1];
+    }
+    C.acc = acc;
+    C.out = out;
+    parallel_for(nrows, threads, combine_ext_body, &C);
+    return 0;
+}
+
+/* The coset fold of orc_fri_fold_coset with extension values and challenge:
+ * f_i(y_w) = 2^-a sum_v f(x_v) x_v^-i (x_v in F_p), result = sum_i beta^i f_i. */
+void orc_fri_fold_coset_ext(const u64* vals /* [2^a][2] */, uint32_t logm, u64 shift, uint32_t a, const u64* beta,
+                            uint64_t w, u64* out)
+{
+    uint32_t A = 1u << a;
+    u64 w_m = orc_root_of_unity(logm), inv_arity = orc_inv((u64)A);
+    u64 xinv[256], xpow[256];
+    for (uint32_t v = 0; v < A; v++) {
+        xinv[v] = orc_inv(orc_mul(shift, orc_pow(w_m, bitrev((u64)w * A + v, logm))));
+        xpow[v] = 1;
+    }
+    u64 res[2] = {0, 0}, bpow[2] = {1, 0};
+    for (uint32_t i = 0; i < A; i++) {
+        u64 fi[2] = {0, 0};
+        for (uint32_t v = 0; v < A; v++) {
+            fi[0] = orc_add(fi[0], orc_mul(vals[2 * v], xpow[v]));
+            fi[1] = orc_add(fi[1], orc_mul(vals[2 * v + 1], xpow[v]));
+            xpow[v] = orc_mul(xpow[v], xinv[v]);
+        }
+        fi[0] = orc_mul(fi[0], inv_arity);
+        fi[1] = orc_mul(fi[1], inv_arity);
+        u64 t[2];
+        ext_mul(bpow, fi, t);
+        res[0] = orc_add(res[0], t[0]);
+        res[1] = orc_add(res[1], t[1]);
+        ext_mul(bpow, beta, t);
+        bpow[0] = t[0];
+        bpow[1] = t[1];
+    }
+    out[0] = res[0];
+    out[1] = res[1];
+}
+
+typedef struct {
+    const u64* f;
+    uint32_t logm, a;
+    u64 shift, beta[2];
+    u64* out;
+} fold_ext_ctx;
+static void fold_ext_body(void* vctx, size_t w)
+{
+    fold_ext_ctx* F = (fold_ext_ctx*)vctx;
+    orc_fri_fold_coset_ext(F->f + 2 * (w << F->a), F->logm, F->shift, F->a, F->beta, w, F->out + 2 * w);
+}
+
+int orc_fri_fold_ext(const u64* f, uint32_t logm, u64 shift, uint32_t a, const u64* beta, u64* out, int threads)
+{
+    if (a == 0 || a > 8 || a > logm) return -1;
+    fold_ext_ctx F = {f, logm, a, shift, {beta[0], beta[1]}, out};
+    parallel_for((size_t)1 << (logm - a), threads, fold_ext_body, &F);
+    return 0;
+}

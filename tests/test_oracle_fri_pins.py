@@ -129,3 +129,81 @@ def test_verifier_accepts_honest_and_rejects_tampered_openings():
         bad[1][0][0] = (int(bad[1][0][0]) + 1) % P  # a planted error in the second layer's coset
         assert not oracle.fri_verify_query(st["caps"], st["heights"], st["arities"], st["betas"],
                                            st["final"], 7, t0, int(f0[t0]), bad)
+
+
+# --- quadratic extension F_p[u] / (u^2 - 7) ----------------------------------
+
+def emul(a, b):
+    return ((a[0] * b[0] + 7 * a[1] * b[1]) % P, (a[0] * b[1] + a[1] * b[0]) % P)
+
+
+def test_extension_is_a_field_and_arithmetic_matches():
+    # 7 generates F_p^*, so it is a non-residue (Euler's criterion) and
+    # u^2 - 7 is irreducible.
+    assert pow(7, (P - 1) // 2, P) == P - 1
+    rng = np.random.default_rng(20)
+    for _ in range(20):
+        a = tuple(int(v) for v in rng.integers(0, P, size=2, dtype=np.uint64))
+        b = tuple(int(v) for v in rng.integers(0, P, size=2, dtype=np.uint64))
+        assert oracle.ext_mul(a, b) == emul(a, b)
+        ai = oracle.ext_inv(a)
+        assert emul(a, ai) == (1, 0)
+
+
+@pytest.mark.parametrize("a", [1, 2, 4])
+def test_extension_fold_matches_coefficient_split(a):
+    rng = np.random.default_rng(30 + a)
+    log_m, deg, shift = 6, 24, 7
+    coefs = [tuple(int(v) for v in rng.integers(0, P, size=2, dtype=np.uint64)) for _ in range(deg)]
+    w = root(log_m)
+    xs = [shift * pow(w, brev(t, log_m), P) % P for t in range(1 << log_m)]
+    f = np.array([[horner([c[0] for c in coefs], x), horner([c[1] for c in coefs], x)] for x in xs], np.uint64)
+    beta = tuple(int(v) for v in rng.integers(1, P, size=2, dtype=np.uint64))
+    got = oracle.fri_fold(f, shift, a, beta, ext=2)
+    A = 1 << a
+    padded = coefs + [(0, 0)] * (-len(coefs) % A)
+    parts = [padded[i::A] for i in range(A)]
+    bp = [(1, 0)]
+    for _ in range(A - 1):
+        bp.append(emul(bp[-1], beta))
+    folded = []
+    for j in range(len(parts[0])):
+        acc = (0, 0)
+        for i in range(A):
+            t = emul(bp[i], parts[i][j])
+            acc = ((acc[0] + t[0]) % P, (acc[1] + t[1]) % P)
+        folded.append(acc)
+    ys = [pow(shift, A, P) * pow(root(log_m - a), brev(t, log_m - a), P) % P for t in range(1 << (log_m - a))]
+    want = [[horner([c[0] for c in folded], y), horner([c[1] for c in folded], y)] for y in ys]
+    assert [[int(v) for v in row] for row in got] == want
+
+
+def test_extension_path_reduces_to_the_base_path():
+    rng = np.random.default_rng(40)
+    cols = rng.integers(0, P, size=(3, 32), dtype=np.uint64)
+    e = oracle.lde(cols, 2)
+    base = oracle.fri_commit([e], [3], 12345, [11, 22, 33], 2, 1, 1)
+    ext = oracle.fri_commit([e], [3], (12345, 0), [(11, 0), (22, 0), (33, 0)], 2, 1, 1, ext=2)
+    assert np.array_equal(ext["final"][:, 0], base["final"]) and not ext["final"][:, 1].any()
+    for k in range(len(base["layers"])):
+        assert np.array_equal(ext["layers"][k][:, 0], base["layers"][k])
+
+
+def test_extension_commit_phase_ends_low_degree_and_verifies():
+    rng = np.random.default_rng(50)
+    cols = rng.integers(0, P, size=(5, 64), dtype=np.uint64)
+    e = oracle.lde(cols, 3)
+    alpha = (987654321, 123456789)
+    betas = [tuple(int(v) for v in rng.integers(1, P, size=2, dtype=np.uint64)) for _ in range(4)]
+    st = oracle.fri_commit([e], [5], alpha, betas, 2, 3, 2, ext=2)
+    bound = 64 >> 6
+    assert not st["final"][bound:].any() and st["final"][:bound].any()
+    f0 = st["layers"][0]
+    for t0 in [0, 5, 511]:
+        op = oracle.fri_query(st, t0)
+        assert oracle.fri_verify_query(st["caps"], st["heights"], st["arities"], st["betas"], st["final"], 9, t0,
+                                       f0[t0], op, ext=2)
+        bad = [(v.copy(), p.copy()) for v, p in op]
+        bad[0][0][1] = (int(bad[0][0][1]) + 1) % P  # the imaginary part of one opened value
+        assert not oracle.fri_verify_query(st["caps"], st["heights"], st["arities"], st["betas"], st["final"], 9,
+                                           t0, f0[t0], bad, ext=2)
