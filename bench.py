@@ -200,7 +200,7 @@ def run_reference_fri(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "fri_135x2_20", "columns": 135, "log_rows": 20, "rate_bits": 3,
                    "arity_bits": FRI_CFG[0], "final_log": FRI_CFG[1], "layer_cap_height": FRI_CFG[2],
-                   "queries": FRI_QUERIES},
+                   "queries": FRI_QUERIES, "ext_degree": FRI_EXT},
         "cpu_baseline": {k: base[k] for k in ("kind", "cores", "value", "unit", "sample")},
         "e2e": {"value": base["value"], "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -524,9 +524,10 @@ def run_serving(args):
 FRI_METRIC = "FRI commit phase on the resident LDE: combined LDE elements Gelem/s"
 FRI_QUERIES = 28      # Plonky2's default number of query rounds
 FRI_CFG = (4, 5, 4)   # arity 2^4, final polynomial 2^5 values, cap height 4 per layer
+FRI_EXT = 2           # challenges and layers in the quadratic extension (Plonky2's default)
 # DRAM traffic of one k_fri_combine launch on the 135 x 2^20 workload, from an
 # ncu capture of the same kernel.  Drop the entry when the kernel changes.
-FRI_COMBINE_TRAFFIC = {"fri_135x2_20": 9.724e9}
+FRI_COMBINE_TRAFFIC = {"fri_135x2_20": 9.690e9}
 
 
 def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
@@ -537,12 +538,13 @@ def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
     x = s.inputs()
     threads = oracle.default_threads()
     e = oracle.lde(x, s.rate_bits, threads=threads)
-    ch = synth.challenges(7, 32)
+    ch = synth.challenges(7, 64)
     nr = len(oracle.fri_arities(s.log_N, FRI_CFG[0], FRI_CFG[1]))
     idx = np.array(ch[-FRI_QUERIES:], dtype=np.uint64) % np.uint64(1 << s.log_N)
+    alpha, betas = fri_challenges(ch, nr)
 
     def one():
-        st = oracle.fri_commit([e], [s.c], ch[0], ch[1:1 + nr], *FRI_CFG, threads=threads)
+        st = oracle.fri_commit([e], [s.c], alpha, betas, *FRI_CFG, threads=threads, ext=FRI_EXT)
         for t in idx:
             oracle.fri_query(st, int(t))
 
@@ -552,9 +554,18 @@ def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
         one()
     dt = (time.perf_counter() - t0) / steps
     return {"value": s.lde_elems() / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
-            "sample": f"oracle FRI commit phase (arity 16, final 2^5, cap 4) + {FRI_QUERIES} query openings on "
+            "sample": f"oracle FRI commit phase (arity 16, final 2^5, cap 4, degree-{FRI_EXT} extension) + "
+                      f"{FRI_QUERIES} query openings on "
                       f"the LDE of {s.c} columns x 2^{s.log_n} rows, rate_bits {s.rate_bits}; {dt:.2f} s per step",
             "ms_per_step": dt * 1e3}
+
+
+def fri_challenges(ch, nr):
+    """alpha and the round challenges from a list of seeded field elements:
+    (re, im) pairs for the extension."""
+    if FRI_EXT == 1:
+        return ch[0], ch[1:1 + nr]
+    return (ch[0], ch[1]), [(ch[2 + 2 * k], ch[3 + 2 * k]) for k in range(nr)]
 
 
 def run_fri(args):
@@ -579,17 +590,16 @@ def run_fri(args):
     stream = torch.cuda.current_stream()
     cid = ctx.commit([(v3c.to_device_u64(s.inputs()), s.rate_bits, s.cap_height)], stream=stream)[0]
     ch = synth.challenges(7 + rank, 64)
-    alpha = ch[0]
     a, fl, h = FRI_CFG
-    fid = ctx.fri_begin([cid], alpha, a, fl, h)
+    fid = ctx.fri_begin([cid], (ch[0], ch[1]) if FRI_EXT == 2 else ch[0], a, fl, h, ext=FRI_EXT)
     info = ctx.fri_info(fid)
     ctx.fri_release(fid)
     nr = info["rounds"]
-    betas = ch[1:1 + nr]
+    alpha, betas = fri_challenges(ch, nr)
     idx = np.array(ch[-FRI_QUERIES:], dtype=np.uint64) % np.uint64(1 << s.log_N)
 
     def commit_phase():
-        return ctx.fri_begin([cid], alpha, a, fl, h, betas=betas, stream=stream)
+        return ctx.fri_begin([cid], alpha, a, fl, h, betas=betas, ext=FRI_EXT, stream=stream)
 
     for _ in range(max(args.warmup, 1)):
         ctx.fri_release(commit_phase())
@@ -645,7 +655,7 @@ def run_fri(args):
     comb_ms, comb_n = stats["fri_combine"]
     comb_per = comb_ms / max(comb_n, 1)
     N = 1 << s.log_N
-    comb_bytes = N * s.ld * 8 + N * 8   # every LDE row once (pad column included), f_0 written
+    comb_bytes = N * s.ld * 8 + N * 8 * FRI_EXT   # every LDE row once (pad column included), f_0 written
     achieved = comb_bytes / (comb_per * 1e-3) / 1e9
     peak = measured_peaks().get("hbm_gbs", 6800.0)
     stage_ms = {k: (v[0] / v[1], int(v[1])) for k, v in stats.items() if v[1]}
@@ -656,14 +666,16 @@ def run_fri(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "fri_135x2_20", "columns": s.c, "log_rows": s.log_n,
                        "rate_bits": s.rate_bits, "lde_rows": N, "arity_bits": a, "final_log": fl,
-                       "layer_cap_height": h, "rounds": nr, "queries": FRI_QUERIES,
+                       "layer_cap_height": h, "rounds": nr, "queries": FRI_QUERIES, "ext_degree": FRI_EXT,
                        "l2": "inputs larger than L2 (no flush needed)"},
             "e2e": {"value": world * s.lde_elems() / e2e_s / 1e9, "unit": "Gelem/s",
-                    "h2d_bytes_per_step": int(2 * idx.nbytes + 8 * len(betas)), "d2h_bytes_per_step": int(d2h),
+                    "h2d_bytes_per_step": int(2 * idx.nbytes + 8 * FRI_EXT * (len(betas) + 1)),
+                    "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(launches),
             "clocks": clk,
-            "roofline": {"bound": "hbm", "kernel": "k_fri_combine", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "k_fri_combine_ext" if FRI_EXT == 2 else "k_fri_combine",
+                         "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": FRI_COMBINE_TRAFFIC.get("fri_135x2_20"),
                          "bytes_per_launch": comb_bytes, "ms_per_launch": comb_per, "peak_source": "measured"},
             "stages_ms_per_launch": stage_ms,

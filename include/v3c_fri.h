@@ -26,13 +26,23 @@
  *
  * Layer trees.  For k < R (R = the number of rounds), layer k is committed
  * as a Merkle tree of L_k = N_k / 2^a_k leaves.  Leaf w is the coset
- * f_k[w 2^a_k .. (w+1) 2^a_k), hashed like an LDE row of width 2^a_k: the
- * Poseidon sponge, or zero padding when 2^a_k <= 4.  The cap height is
+ * f_k[w 2^a_k .. (w+1) 2^a_k), hashed like an LDE row of its 2^a_k values
+ * (ext_degree words each): the Poseidon sponge, or zero padding when the
+ * leaf has at most 4 words.  The cap height is
  * min(cap_height, log2 L_k).  The last layer f_R is not hashed; it is
  * returned as the coefficients of its polynomial (v3c_fri_final).
  *
- * Challenges.  alpha and the beta_k are inputs.  A caller that derives
- * beta_k from layer k's cap (Fiat-Shamir) passes no betas to v3c_fri_begin,
+ * Extension.  Plonky2's default FRI draws its challenges from a degree-2
+ * extension.  With ext_degree = 2, alpha and the beta_k are elements
+ * (re, im) = re + im u of F_p[u] / (u^2 - 7).  7 generates F_p^*, so u^2 - 7
+ * is irreducible.  The combination, every layer and the final coefficients
+ * are then pairs of words, (re, im) per value, and a leaf holds 2 * 2^a_k
+ * words.  The LDE columns and the domain stay in F_p.  With ext_degree = 1,
+ * everything is in F_p and a value is one word.
+ *
+ * Challenges.  alpha and the beta_k are inputs, ext_degree words each.  A
+ * caller that derives beta_k from layer k's cap (Fiat-Shamir) passes no
+ * betas to v3c_fri_begin,
  * reads cap 0, then calls v3c_fri_fold with one beta at a time.  A caller
  * that knows all betas passes them at once; the layer trees are then hashed
  * in one batched launch.
@@ -55,6 +65,7 @@ typedef struct {
     uint32_t arity_bits; /* 1..4 */
     uint32_t final_log;  /* 0..10, below log_N */
     uint32_t cap_height; /* per-layer cap height, clamped to the layer's leaf count */
+    uint32_t ext_degree; /* 1 (or 0): values in F_p; 2: in F_p[u]/(u^2 - 7) */
 } v3c_fri_cfg;
 
 #define V3C_FRI_MAX_ROUNDS 25
@@ -68,18 +79,22 @@ typedef struct {
     uint32_t cap_height[V3C_FRI_MAX_ROUNDS];   /* of layer k's tree, k < R */
     uint64_t query_words; /* words per query written by v3c_fri_query */
     uint64_t bytes;       /* device bytes held by the state */
+    uint32_t ext_degree;  /* 1 or 2: words per layer value */
+    uint32_t pad;
 } v3c_fri_info_t;
 
 /* Starts the commit phase over n_ids resident commitments: allocates every
  * layer, builds f_0 and commits layer 0.  Then it applies the first n_betas
- * folds (n_betas <= R), as v3c_fri_fold does.  The state counts against the
+ * folds (n_betas <= R), as v3c_fri_fold does.  alpha points to ext_degree
+ * words; h_betas to n_betas * ext_degree words.  The state counts against the
  * context's HBM budget until v3c_fri_release. */
-v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids, uint64_t alpha,
+v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids, const uint64_t* alpha,
                          const v3c_fri_cfg* cfg, const uint64_t* h_betas, uint32_t n_betas, v3c_fri_id* out,
                          void* stream);
 
-/* Applies the next n_betas rounds: f_{k+1} = fold(f_k, beta_k).  Each new
- * layer below R is then committed.  When the last round is applied, the
+/* Applies the next n_betas rounds: f_{k+1} = fold(f_k, beta_k), with
+ * h_betas holding n_betas * ext_degree words.  Each new layer below R is
+ * then committed.  When the last round is applied, the
  * final polynomial's coefficients are computed.  n_betas must not exceed the
  * rounds left. */
 v3c_status v3c_fri_fold(v3c_ctx* ctx, v3c_fri_id fri, const uint64_t* h_betas, uint32_t n_betas, void* stream);
@@ -91,16 +106,17 @@ v3c_status v3c_fri_info(v3c_ctx* ctx, v3c_fri_id fri, v3c_fri_info_t* out);
  * exist (k <= rounds_done, k < R). */
 v3c_status v3c_fri_cap(v3c_ctx* ctx, v3c_fri_id fri, uint32_t layer, uint64_t* h_cap);
 
-/* Coefficients of the last layer's polynomial: 2^log_size[R] words, lowest
- * degree first.  They are the c_i with f_R(x_t) = sum_i c_i x_t^i on the
- * layer's coset.  All rounds must be done.  For an honest prover, the
+/* Coefficients of the last layer's polynomial: 2^log_size[R] values of
+ * ext_degree words (re, im for degree 2), lowest degree first.  They are the
+ * c_i with f_R(x_t) = sum_i c_i x_t^i on the layer's coset.  All rounds must be done.  For an honest prover, the
  * coefficients at and above deg / 2^(log_N - log_size[R]) are zero. */
 v3c_status v3c_fri_final(v3c_ctx* ctx, v3c_fri_id fri, uint64_t* h_coeffs);
 
 /* Batched query openings (all rounds done).  For each query position
  * t_0 = h_idx[q] < N the call writes query_words words at
  * h_out + q * query_words.  For each layer k < R, in order, they are:
- *   the 2^a_k values of leaf w_k = t_k >> a_k, where t_k = t_0 >> (a_0 + ... + a_{k-1});
+ *   the 2^a_k values of leaf w_k = t_k >> a_k, ext_degree words each, where
+ *   t_k = t_0 >> (a_0 + ... + a_{k-1});
  *   its Merkle path, the siblings level_j[(w_k >> j) ^ 1] for
  *   j = 0 .. log2 L_k - cap_height[k] - 1, 4 words each.
  * The initial rows at t_0 come from v3c_open_batch on the commitments. */

@@ -67,13 +67,14 @@ FRI_MAX_ROUNDS = 25
 
 
 class FriCfg(ctypes.Structure):
-    _fields_ = [("arity_bits", _u32), ("final_log", _u32), ("cap_height", _u32)]
+    _fields_ = [("arity_bits", _u32), ("final_log", _u32), ("cap_height", _u32), ("ext_degree", _u32)]
 
 
 class FriInfo(ctypes.Structure):
     _fields_ = [("rounds", _u32), ("rounds_done", _u32), ("log_N", _u32), ("n_columns", _u32),
                 ("arity_bits", _u32 * FRI_MAX_ROUNDS), ("log_size", _u32 * (FRI_MAX_ROUNDS + 1)),
-                ("cap_height", _u32 * FRI_MAX_ROUNDS), ("query_words", _u64), ("bytes", _u64)]
+                ("cap_height", _u32 * FRI_MAX_ROUNDS), ("query_words", _u64), ("bytes", _u64),
+                ("ext_degree", _u32), ("pad", _u32)]
 
 
 class SnapshotDesc(ctypes.Structure):
@@ -116,7 +117,7 @@ SIGNATURES = {
     "v3c_lde_noalloc": (ctypes.c_int, [_vp, _u32, _u32, _u32, _vp, _u32, _vp]),
     "v3c_int_peak": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     # include/v3c_fri.h
-    "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
+    "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64p, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
     "v3c_fri_fold": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _vp]),
     "v3c_fri_info": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(FriInfo)]),
     "v3c_fri_cap": (ctypes.c_int, [_vp, _u64, _u32, _u64p]),
@@ -394,20 +395,24 @@ class Context:
         return r, pth
 
     # --------------------------------------------------------------- FRI
-    def fri_begin(self, cids, alpha: int, arity_bits: int = 4, final_log: int = 5, cap_height: int = 4,
-                  betas=(), stream=None) -> int:
+    def fri_begin(self, cids, alpha, arity_bits: int = 4, final_log: int = 5, cap_height: int = 4,
+                  betas=(), ext: int = 1, stream=None) -> int:
+        """alpha: an int (ext 1) or an (re, im) pair (ext 2); betas: a list of
+        those."""
         ids = np.ascontiguousarray(cids, dtype=np.uint64)
-        bs = np.ascontiguousarray(betas, dtype=np.uint64)
-        cfg = FriCfg(arity_bits, final_log, cap_height)
+        al = np.ascontiguousarray(np.array(alpha, dtype=object).reshape(-1).astype(np.uint64))
+        bs = np.ascontiguousarray(np.array(list(betas), dtype=object).reshape(-1).astype(np.uint64))
+        cfg = FriCfg(arity_bits, final_log, cap_height, ext)
         out = _u64()
-        self._check(self.lib.v3c_fri_begin(self.h, ids.ctypes.data_as(_u64p), ids.size, alpha, ctypes.byref(cfg),
-                                           bs.ctypes.data_as(_u64p) if bs.size else None, bs.size,
-                                           ctypes.byref(out), _stream(stream)))
+        self._check(self.lib.v3c_fri_begin(self.h, ids.ctypes.data_as(_u64p), ids.size, al.ctypes.data_as(_u64p),
+                                           ctypes.byref(cfg), bs.ctypes.data_as(_u64p) if bs.size else None,
+                                           bs.size // ext, ctypes.byref(out), _stream(stream)))
         return out.value
 
     def fri_fold(self, fid: int, betas, stream=None):
-        bs = np.ascontiguousarray(betas, dtype=np.uint64)
-        self._check(self.lib.v3c_fri_fold(self.h, fid, bs.ctypes.data_as(_u64p), bs.size, _stream(stream)))
+        ext = self.fri_info(fid)["ext"]
+        bs = np.ascontiguousarray(np.array(list(betas), dtype=object).reshape(-1).astype(np.uint64))
+        self._check(self.lib.v3c_fri_fold(self.h, fid, bs.ctypes.data_as(_u64p), bs.size // ext, _stream(stream)))
 
     def fri_info(self, fid: int) -> dict:
         i = FriInfo()
@@ -415,7 +420,8 @@ class Context:
         R = i.rounds
         return {"rounds": R, "rounds_done": i.rounds_done, "log_N": i.log_N, "n_columns": i.n_columns,
                 "arities": list(i.arity_bits[:R]), "log_sizes": list(i.log_size[: R + 1]),
-                "heights": list(i.cap_height[:R]), "query_words": i.query_words, "bytes": i.bytes}
+                "heights": list(i.cap_height[:R]), "query_words": i.query_words, "bytes": i.bytes,
+                "ext": i.ext_degree}
 
     def fri_cap(self, fid: int, layer: int) -> np.ndarray:
         info = self.fri_info(fid)
@@ -424,10 +430,12 @@ class Context:
         return out.reshape(-1, 4)
 
     def fri_final(self, fid: int) -> np.ndarray:
+        """Final coefficients: shape [m] (ext 1) or [m][2] (ext 2)."""
         info = self.fri_info(fid)
-        out = np.zeros(1 << info["log_sizes"][-1], np.uint64)
+        m, ext = 1 << info["log_sizes"][-1], info["ext"]
+        out = np.zeros(m * ext, np.uint64)
         self._check(self.lib.v3c_fri_final(self.h, fid, out.ctypes.data_as(_u64p)))
-        return out
+        return out if ext == 1 else out.reshape(m, ext)
 
     def fri_query(self, fid: int, indices) -> np.ndarray:
         """Raw opening records [nq][query_words]: per layer, the coset values

@@ -34,6 +34,7 @@ using gl::u64;
 struct FriState {
     u64 id = 0;
     u32 rounds = 0, done = 0, log_N = 0, ncols = 0;
+    u32 ext = 1;  // extension degree of the layers: 1 (F_p) or 2 (F_p[u]/(u^2 - 7))
     u32 arity[V3C_FRI_MAX_ROUNDS] = {0};
     u32 log_size[V3C_FRI_MAX_ROUNDS + 1] = {0};
     u32 h[V3C_FRI_MAX_ROUNDS] = {0};
@@ -58,6 +59,28 @@ __global__ void k_fri_powers(u64 alpha, u32 count, u64* out)
 {
     for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
         out[i] = gl::pow(alpha, i);
+}
+
+// (a0 + a1 u)(b0 + b1 u) in F_p[u] / (u^2 - 7); canonical in and out.
+__device__ __forceinline__ void ext_mul_d(u64 a0, u64 a1, u64 b0, u64 b1, u64& r0, u64& r1)
+{
+    const u64 x = gl::add(gl::mul(a0, b0), gl::mul(7, gl::mul(a1, b1)));
+    r1 = gl::add(gl::mul(a0, b1), gl::mul(a1, b0));
+    r0 = x;
+}
+
+// out[2i], out[2i+1] = alpha^i in the quadratic extension.
+__global__ void k_fri_powers_ext(u64 a0, u64 a1, u32 count, u64* out)
+{
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        u64 r0 = 1, r1 = 0, x0 = a0, x1 = a1;
+        for (u32 e = i; e; e >>= 1) {
+            if (e & 1) ext_mul_d(r0, r1, x0, x1, r0, r1);
+            ext_mul_d(x0, x1, x0, x1, x0, x1);
+        }
+        out[2 * i] = r0;
+        out[2 * i + 1] = r1;
+    }
 }
 
 // pw[512 l + j] = winv^((j << 9 l) mod N): w_N^-e for e < 2^27 is then the
@@ -140,6 +163,57 @@ __global__ void __launch_bounds__(256) k_fri_combine(const u64* __restrict__ row
     }
 }
 
+// f[t] (+)= sum_{i<c} alpha^i row_t[i] with alpha^i in the extension (pw
+// holds (re, im) pairs): the same row walk as k_fri_combine with two
+// unreduced sums, one per component.  Two 64x64 products per element make
+// it IMAD-bound rather than HBM-bound (two lanes per row measured slower).
+__global__ void __launch_bounds__(256) k_fri_combine_ext(const u64* __restrict__ rows, u32 ld, u32 c,
+                                                         const u64* __restrict__ pw, u64 nrows, int acc,
+                                                         u64* __restrict__ f)
+{
+    const u32 pairs = c >> 1;
+    const ulonglong2* pw2 = reinterpret_cast<const ulonglong2*>(pw);
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < nrows; t += (u64)gridDim.x * blockDim.x) {
+        const ulonglong2* row = reinterpret_cast<const ulonglong2*>(rows + t * ld);
+        u64 lo0 = 0, mid0 = 0, lo1 = 0, mid1 = 0;
+        u32 hi0 = 0, hi1 = 0;
+        u32 k = 0;
+        for (; k + kCombPairs <= pairs; k += kCombPairs) {
+            ulonglong2 v[kCombPairs];
+#pragma unroll
+            for (int j = 0; j < kCombPairs; j++) v[j] = __ldg(row + k + j);
+#pragma unroll
+            for (int j = 0; j < kCombPairs; j++) {
+                const ulonglong2 p0 = __ldg(pw2 + 2 * (k + j)), p1 = __ldg(pw2 + 2 * (k + j) + 1);
+                mac192(lo0, mid0, hi0, v[j].x, p0.x);
+                mac192(lo1, mid1, hi1, v[j].x, p0.y);
+                mac192(lo0, mid0, hi0, v[j].y, p1.x);
+                mac192(lo1, mid1, hi1, v[j].y, p1.y);
+            }
+        }
+        for (; k < pairs; k++) {
+            const ulonglong2 v = __ldg(row + k);
+            const ulonglong2 p0 = __ldg(pw2 + 2 * k), p1 = __ldg(pw2 + 2 * k + 1);
+            mac192(lo0, mid0, hi0, v.x, p0.x);
+            mac192(lo1, mid1, hi1, v.x, p0.y);
+            mac192(lo0, mid0, hi0, v.y, p1.x);
+            mac192(lo1, mid1, hi1, v.y, p1.y);
+        }
+        if (c & 1) {
+            const u64 x = __ldg(rows + t * ld + c - 1);
+            const ulonglong2 p0 = __ldg(pw2 + c - 1);
+            mac192(lo0, mid0, hi0, x, p0.x);
+            mac192(lo1, mid1, hi1, x, p0.y);
+        }
+        u64 r0 = fold192(lo0, mid0, hi0), r1 = fold192(lo1, mid1, hi1);
+        if (acc) {
+            r0 = gl::add(f[2 * t], r0);
+            r1 = gl::add(f[2 * t + 1], r1);
+        }
+        reinterpret_cast<ulonglong2*>(f)[t] = make_ulonglong2(r0, r1);
+    }
+}
+
 // Per-round fold constants.  Step m of a round pairs positions (2u, 2u+1) of
 // the intermediate layer; with u = w 2^b + v' (b = a-1-m) the point of
 // position 2u is x = s^(2^m) w_{2^(b+1)}^bitrev_b(v') (w_{N_k}^e)^(2^m),
@@ -152,24 +226,24 @@ struct FoldArgs {
     u32 log_out;    // log2 N_{k+1}
     u32 exp_shift;  // log2 (N_0 / N_k)
     u64 inv2;
-    u64 K[15];
+    u64 K[15][2];  // (re, im); im = 0 in the base field
 };
 
 // g(x^2) = (f(x) + f(-x)) / 2 + beta (f(x) - f(-x)) / (2x), applied a times
-// in registers to one coset of 2^a values.
-template <int A_BITS>
+// in registers to one coset of 2^a values (EXT words each; x is in F_p).
+template <int A_BITS, int EXT>
 __global__ void __launch_bounds__(256) k_fri_fold(FoldArgs p)
 {
     constexpr int A = 1 << A_BITS;
     const u64 nout = (u64)1 << p.log_out;
     for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nout; w += (u64)gridDim.x * blockDim.x) {
-        u64 v[A];
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(p.in + (w << A_BITS));
+        u64 v[A][EXT];
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(p.in + ((w << A_BITS) * EXT));
 #pragma unroll
-        for (int k = 0; k < A / 2; k++) {
+        for (int k = 0; k < A * EXT / 2; k++) {
             ulonglong2 q = __ldg(src + k);
-            v[2 * k] = q.x;
-            v[2 * k + 1] = q.y;
+            v[(2 * k) / EXT][(2 * k) % EXT] = q.x;
+            v[(2 * k + 1) / EXT][(2 * k + 1) % EXT] = q.y;
         }
         u64 e = (u64)gl::bitrev((u32)w, p.log_out) << p.exp_shift;
         u64 z = pow3(p.pw_inv, e);  // 1 / (w_{N_k}^e)
@@ -179,25 +253,40 @@ __global__ void __launch_bounds__(256) k_fri_fold(FoldArgs p)
             const int half = A >> (m + 1);
 #pragma unroll
             for (int u = 0; u < half; u++) {
-                u64 a0 = v[2 * u], a1 = v[2 * u + 1];
-                u64 t = gl::mul(p.K[kidx + u], z);
-                v[u] = gl::add(gl::mul(gl::add(a0, a1), p.inv2), gl::mul(gl::sub(a0, a1), t));
+                if (EXT == 1) {
+                    u64 a0 = v[2 * u][0], a1 = v[2 * u + 1][0];
+                    u64 t = gl::mul(p.K[kidx + u][0], z);
+                    v[u][0] = gl::add(gl::mul(gl::add(a0, a1), p.inv2), gl::mul(gl::sub(a0, a1), t));
+                } else {
+                    const u64 t0 = gl::mul(p.K[kidx + u][0], z), t1 = gl::mul(p.K[kidx + u][EXT - 1], z);
+                    const u64 s0 = gl::add(v[2 * u][0], v[2 * u + 1][0]);
+                    const u64 s1 = gl::add(v[2 * u][EXT - 1], v[2 * u + 1][EXT - 1]);
+                    const u64 d0 = gl::sub(v[2 * u][0], v[2 * u + 1][0]);
+                    const u64 d1 = gl::sub(v[2 * u][EXT - 1], v[2 * u + 1][EXT - 1]);
+                    u64 q0, q1;
+                    ext_mul_d(d0, d1, t0, t1, q0, q1);
+                    v[u][0] = gl::add(gl::mul(s0, p.inv2), q0);
+                    v[u][EXT - 1] = gl::add(gl::mul(s1, p.inv2), q1);
+                }
             }
             kidx += half;
             z = gl::mul(z, z);
         }
-        p.out[w] = v[0];
+#pragma unroll
+        for (int x = 0; x < EXT; x++) p.out[w * EXT + x] = v[0][x];
     }
 }
 
 // c_i = m^-1 s^-i sum_j E_j w_m^-ij with E_j = f[bitrev(j)]: the inverse DFT
 // of the natural-order values, unshifted.  One CTA, m <= 1024.
+// Extension values are interpolated componentwise (the DFT is linear over
+// F_p): component `comp` of element j sits at f[ext j + comp].
 __global__ void __launch_bounds__(256) k_fri_final(const u64* __restrict__ f, u32 logm, u64 winv, u64 sinv,
-                                                   u64 minv, u64* __restrict__ out)
+                                                   u64 minv, u64* __restrict__ out, u32 ext, u32 comp)
 {
     __shared__ u64 E[1024];
     const u32 m = 1u << logm;
-    for (u32 j = threadIdx.x; j < m; j += blockDim.x) E[j] = f[gl::bitrev(j, logm)];
+    for (u32 j = threadIdx.x; j < m; j += blockDim.x) E[j] = f[(size_t)ext * gl::bitrev(j, logm) + comp];
     __syncthreads();
     for (u32 i = threadIdx.x; i < m; i += blockDim.x) {
         u64 wi = gl::pow(winv, i), wij = 1, acc = 0;
@@ -205,7 +294,7 @@ __global__ void __launch_bounds__(256) k_fri_final(const u64* __restrict__ f, u3
             acc = gl::add(acc, gl::mul(E[j], wij));
             wij = gl::mul(wij, wi);
         }
-        out[i] = gl::mul(acc, gl::mul(gl::pow(sinv, i), minv));
+        out[(size_t)ext * i + comp] = gl::mul(acc, gl::mul(gl::pow(sinv, i), minv));
     }
 }
 
@@ -218,6 +307,7 @@ struct QueryLayer {
 struct QueryArgs {
     QueryLayer L[V3C_FRI_MAX_ROUNDS];
     u32 R;
+    u32 ext;
     u32 nq;
     u64 words;
     const u64* idx;
@@ -237,10 +327,11 @@ __global__ void k_fri_query(QueryArgs p)
         u64 off = o - L.word0;
         u64 leaf = (p.idx[q] >> L.tshift) >> L.a;
         u64 val;
-        if (off < ((u64)1 << L.a)) {
-            val = L.f[(leaf << L.a) + off];
+        const u64 vw = ((u64)1 << L.a) * p.ext;  // value words of one leaf
+        if (off < vw) {
+            val = L.f[(leaf << L.a) * p.ext + off];
         } else {
-            off -= (u64)1 << L.a;
+            off -= vw;
             u32 lvl = (u32)(off >> 2), comp = (u32)(off & 3);
             u64 eightL = (u64)8 << L.logL;
             val = L.tree[(eightL - (eightL >> lvl)) + 4 * ((leaf >> lvl) ^ 1) + comp];
@@ -277,14 +368,25 @@ using namespace v3c::detail;
 
 namespace {
 
+// Host arithmetic in F_p[u] / (u^2 - 7).  The sums of two values below p
+// are taken in 128 bits (they can exceed 2^64).
+u64 h_add(u64 a, u64 b) { return (u64)(((unsigned __int128)a + b) % gl::P); }
+void h_ext_mul(const u64* a, const u64* b, u64* r)
+{
+    const u64 r0 = h_add(gl::h_mul(a[0], b[0]), gl::h_mul(7, gl::h_mul(a[1], b[1])));
+    const u64 r1 = h_add(gl::h_mul(a[0], b[1]), gl::h_mul(a[1], b[0]));
+    r[0] = r0;
+    r[1] = r1;
+}
+
 int grid_for(u64 work, int threads)
 {
     u64 g = (work + threads - 1) / threads;
     return (int)std::max<u64>(1, std::min<u64>(g, (u64)num_sms() * 16));
 }
 
-// Enqueues round k's fold: f_{k+1} from f_k with challenge beta.
-v3c_status launch_fold(v3c_ctx* ctx, FriState& st, u32 k, u64 beta, cudaStream_t s)
+// Enqueues round k's fold: f_{k+1} from f_k with challenge beta (st.ext words).
+v3c_status launch_fold(v3c_ctx* ctx, FriState& st, u32 k, const u64* beta, cudaStream_t s)
 {
     const u32 a = st.arity[k];
     FoldArgs p;
@@ -296,25 +398,38 @@ v3c_status launch_fold(v3c_ctx* ctx, FriState& st, u32 k, u64 beta, cudaStream_t
     p.exp_shift = st.log_N - st.log_size[k];
     p.inv2 = gl::h_inv(2);
     int kidx = 0;
-    u64 bm = beta, sm = st.shift[k];
+    u64 bm[2] = {beta[0], st.ext == 2 ? beta[1] : 0}, sm = st.shift[k];
     for (u32 m = 0; m < a; m++) {
         const u32 b = a - 1 - m;
-        const u64 base = gl::h_mul(bm, gl::h_inv(gl::h_mul(2, sm)));
+        const u64 scale = gl::h_inv(gl::h_mul(2, sm));
         const u64 rinv = gl::h_inv(gl::h_root(b + 1));
-        for (u32 vp = 0; vp < (1u << b); vp++)
-            p.K[kidx + vp] = gl::h_mul(base, gl::h_pow(rinv, gl::bitrev(vp, b)));
+        for (u32 vp = 0; vp < (1u << b); vp++) {
+            const u64 c = gl::h_mul(scale, gl::h_pow(rinv, gl::bitrev(vp, b)));
+            p.K[kidx + vp][0] = gl::h_mul(bm[0], c);
+            p.K[kidx + vp][1] = gl::h_mul(bm[1], c);
+        }
         kidx += 1 << b;
-        bm = gl::h_mul(bm, bm);
+        if (st.ext == 2) h_ext_mul(bm, bm, bm);
+        else bm[0] = gl::h_mul(bm[0], bm[0]);
         sm = gl::h_mul(sm, sm);
     }
     const int threads = 256;
     const int grid = grid_for((u64)1 << p.log_out, threads);
     StageTimer tm(ctx, 6, s);
-    switch (a) {
-    case 1: k_fri_fold<1><<<grid, threads, 0, s>>>(p); break;
-    case 2: k_fri_fold<2><<<grid, threads, 0, s>>>(p); break;
-    case 3: k_fri_fold<3><<<grid, threads, 0, s>>>(p); break;
-    default: k_fri_fold<4><<<grid, threads, 0, s>>>(p); break;
+    if (st.ext == 2) {
+        switch (a) {
+        case 1: k_fri_fold<1, 2><<<grid, threads, 0, s>>>(p); break;
+        case 2: k_fri_fold<2, 2><<<grid, threads, 0, s>>>(p); break;
+        case 3: k_fri_fold<3, 2><<<grid, threads, 0, s>>>(p); break;
+        default: k_fri_fold<4, 2><<<grid, threads, 0, s>>>(p); break;
+        }
+    } else {
+        switch (a) {
+        case 1: k_fri_fold<1, 1><<<grid, threads, 0, s>>>(p); break;
+        case 2: k_fri_fold<2, 1><<<grid, threads, 0, s>>>(p); break;
+        case 3: k_fri_fold<3, 1><<<grid, threads, 0, s>>>(p); break;
+        default: k_fri_fold<4, 1><<<grid, threads, 0, s>>>(p); break;
+        }
     }
     CK(cudaGetLastError());
     tm.done();
@@ -329,8 +444,10 @@ v3c_status launch_final(v3c_ctx* ctx, FriState& st, cudaStream_t s)
     const u64 sinv = gl::h_inv(st.shift[st.rounds]);
     const u64 minv = gl::h_inv((u64)1 << logm);
     StageTimer tm(ctx, 6, s);
-    k_fri_final<<<1, 256, 0, s>>>(st.f[st.rounds], logm, winv, sinv, minv, st.final_coef);
-    CK(cudaGetLastError());
+    for (u32 comp = 0; comp < st.ext; comp++) {
+        k_fri_final<<<1, 256, 0, s>>>(st.f[st.rounds], logm, winv, sinv, minv, st.final_coef, st.ext, comp);
+        CK(cudaGetLastError());
+    }
     tm.done();
     ctx->launches++;
     return V3C_OK;
@@ -346,7 +463,7 @@ v3c_status commit_layers(v3c_ctx* ctx, FriState& st, cudaStream_t s)
         TreeJob t;
         memset(&t, 0, sizeof t);
         t.rows = st.f[k];
-        t.ld = t.width = 1u << st.arity[k];
+        t.ld = t.width = (1u << st.arity[k]) * st.ext;
         t.log_N = st.log_size[k] - st.arity[k];
         t.h = st.h[k];
         t.tree = st.tree[k];
@@ -365,11 +482,11 @@ v3c_status commit_layers(v3c_ctx* ctx, FriState& st, cudaStream_t s)
 // coefficients once every round is done.  Caller holds ctx->mu.
 v3c_status advance(v3c_ctx* ctx, FriState& st, const uint64_t* betas, u32 n, cudaStream_t s)
 {
-    for (u32 i = 0; i < n; i++) {
-        if (betas[i] >= gl::P) return fail(ctx, V3C_EINVAL, "v3c_fri: beta %u not canonical", i);
+    for (u32 i = 0; i < n * st.ext; i++) {
+        if (betas[i] >= gl::P) return fail(ctx, V3C_EINVAL, "v3c_fri: beta word %u not canonical", i);
     }
     for (u32 i = 0; i < n; i++) {
-        v3c_status r = launch_fold(ctx, st, st.done, betas[i], s);
+        v3c_status r = launch_fold(ctx, st, st.done, betas + (size_t)i * st.ext, s);
         if (r) return r;
         st.done++;
     }
@@ -410,16 +527,18 @@ void fri_free_all(v3c_ctx* ctx)
 
 extern "C" {
 
-v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids, uint64_t alpha,
+v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids, const uint64_t* alpha,
                          const v3c_fri_cfg* cfg, const uint64_t* h_betas, uint32_t n_betas, v3c_fri_id* out,
                          void* stream)
 {
     if (!ctx) return V3C_EINVAL;
-    if (!ids || !n_ids || !cfg || !out || (n_betas && !h_betas))
+    if (!ids || !n_ids || !cfg || !out || !alpha || (n_betas && !h_betas))
         return fail(ctx, V3C_EINVAL, "v3c_fri_begin: NULL argument or no commitments");
-    if (cfg->arity_bits < 1 || cfg->arity_bits > 4 || cfg->final_log > 10 || alpha >= gl::P)
-        return fail(ctx, V3C_EINVAL, "v3c_fri_begin: arity_bits %u, final_log %u or alpha out of range",
-                    cfg->arity_bits, cfg->final_log);
+    const u32 ext = cfg->ext_degree ? cfg->ext_degree : 1;
+    if (cfg->arity_bits < 1 || cfg->arity_bits > 4 || cfg->final_log > 10 || ext > 2 || alpha[0] >= gl::P ||
+        (ext == 2 && alpha[1] >= gl::P))
+        return fail(ctx, V3C_EINVAL, "v3c_fri_begin: arity_bits %u, final_log %u, ext_degree %u or alpha out of range",
+                    cfg->arity_bits, cfg->final_log, cfg->ext_degree);
     v3c_status r = use_device(ctx);
     if (r) return r;
     cudaStream_t s = (cudaStream_t)stream;
@@ -440,6 +559,7 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
     FriState* st = new FriState();
     st->log_N = log_N;
     st->ncols = ncols;
+    st->ext = ext;
     st->log_size[0] = log_N;
     st->shift[0] = 7;
     for (u32 m = log_N; m > cfg->final_log;) {
@@ -457,11 +577,11 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
     }
     // One allocation: root tables, alpha powers, layers, trees, caps, final.
     auto even = [](size_t w) { return (w + 1) & ~(size_t)1; };
-    size_t words = 1536 + even(ncols);
+    size_t words = 1536 + even((size_t)ncols * ext);
     size_t off_f[V3C_FRI_MAX_ROUNDS + 1], off_t[V3C_FRI_MAX_ROUNDS], off_c[V3C_FRI_MAX_ROUNDS];
     for (u32 k = 0; k <= st->rounds; k++) {
         off_f[k] = words;
-        words += even((size_t)1 << st->log_size[k]);
+        words += even(((size_t)1 << st->log_size[k]) * ext);
     }
     st->query_words = 0;
     for (u32 k = 0; k < st->rounds; k++) {
@@ -470,10 +590,10 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
         words += (2 * L - ((size_t)2 << st->h[k])) * 4;
         off_c[k] = words;
         words += (size_t)4 << st->h[k];
-        st->query_words += ((u64)1 << st->arity[k]) + 4 * (st->log_size[k] - st->arity[k] - st->h[k]);
+        st->query_words += ((u64)1 << st->arity[k]) * ext + 4 * (st->log_size[k] - st->arity[k] - st->h[k]);
     }
     size_t off_final = words;
-    words += even((size_t)1 << st->log_size[st->rounds]);
+    words += even(((size_t)1 << st->log_size[st->rounds]) * ext);
     st->bytes = words * 8;
     if (ctx->resident + st->bytes > ctx->cfg.hbm_budget_bytes) {
         size_t need = st->bytes;
@@ -512,7 +632,8 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
     for (auto& o : objs) CKB(cudaStreamWaitEvent(s, o.done, 0));
     k_fri_root_tables<<<6, 256, 0, s>>>(gl::h_inv(gl::h_root(log_N)), log_N, st->pw_inv);
     CKB(cudaGetLastError());
-    k_fri_powers<<<grid_for(ncols, 256), 256, 0, s>>>(alpha, ncols, st->alpha_pw);
+    if (ext == 2) k_fri_powers_ext<<<grid_for(ncols, 256), 256, 0, s>>>(alpha[0], alpha[1], ncols, st->alpha_pw);
+    else k_fri_powers<<<grid_for(ncols, 256), 256, 0, s>>>(alpha[0], ncols, st->alpha_pw);
     CKB(cudaGetLastError());
     ctx->launches += 2;
     u32 e0 = 0;
@@ -523,7 +644,11 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
         CKB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fri_combine, 256, 0));
         int grid = (int)std::min<u64>((u64)std::max(nb, 1) * num_sms(), (N + 255) / 256);
         StageTimer tm(ctx, 5, s);
-        k_fri_combine<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + e0, N, i > 0, st->f[0]);
+        if (ext == 2)
+            k_fri_combine_ext<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + 2 * (size_t)e0, N,
+                                                                i > 0, st->f[0]);
+        else
+            k_fri_combine<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + e0, N, i > 0, st->f[0]);
         CKB(cudaGetLastError());
         tm.done();
         ctx->launches++;
@@ -574,6 +699,7 @@ v3c_status v3c_fri_info(v3c_ctx* ctx, v3c_fri_id fri, v3c_fri_info_t* out)
     for (u32 k = 0; k <= st->rounds; k++) out->log_size[k] = st->log_size[k];
     out->query_words = st->query_words;
     out->bytes = st->bytes;
+    out->ext_degree = st->ext;
     return V3C_OK;
 }
 
@@ -601,7 +727,8 @@ v3c_status v3c_fri_final(v3c_ctx* ctx, v3c_fri_id fri, uint64_t* h_coeffs)
     if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
     if (st->done != st->rounds) return fail(ctx, V3C_EINVAL, "v3c_fri_final: %u of %u rounds done", st->done, st->rounds);
     CK(cudaEventSynchronize(st->ev));
-    CK(cudaMemcpy(h_coeffs, st->final_coef, ((size_t)1 << st->log_size[st->rounds]) * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h_coeffs, st->final_coef, ((size_t)1 << st->log_size[st->rounds]) * st->ext * 8,
+                  cudaMemcpyDeviceToHost));
     return V3C_OK;
 }
 
@@ -633,10 +760,11 @@ v3c_status v3c_fri_query(v3c_ctx* ctx, v3c_fri_id fri, const uint64_t* h_idx, ui
         L.logL = st->log_size[k] - st->arity[k];
         L.h = st->h[k];
         L.tshift = tsh;
-        w0 += ((u64)1 << L.a) + 4 * (L.logL - L.h);
+        w0 += ((u64)1 << L.a) * st->ext + 4 * (L.logL - L.h);
         tsh += L.a;
     }
     p.R = st->rounds;
+    p.ext = st->ext;
     p.nq = nq;
     p.words = st->query_words;
     size_t out_words = (size_t)nq * st->query_words;

@@ -48,26 +48,30 @@ def oracle_records(st, idx):
     return np.stack(out)
 
 
-def run_case(v3c, ctx, shapes, r, h_lde, arity_bits, final_log, cap_height, seed, stepwise=False):
+def run_case(v3c, ctx, shapes, r, h_lde, arity_bits, final_log, cap_height, seed, stepwise=False, ext=1):
     xs = [synth.columns(seed=seed + i, c=c, log_n=log_n, mix="trace" if c >= 4 else "uniform")
           for i, (c, log_n) in enumerate(shapes)]
     ids = ctx.commit([(v3c.to_device_u64(x), r, h_lde) for x in xs])
-    ch = synth.challenges(seed, 40)
-    alpha, betas = ch[0], ch[1:30]
+    ch = synth.challenges(seed, 80)
+    if ext == 1:
+        alpha, betas = ch[0], ch[1:30]
+    else:
+        alpha, betas = (ch[0], ch[1]), [(ch[2 + 2 * k], ch[3 + 2 * k]) for k in range(30)]
     log_N = shapes[0][1] + r
     R = len(oracle.fri_arities(log_N, arity_bits, final_log))
     if stepwise:
-        fid = ctx.fri_begin(ids, alpha, arity_bits, final_log, cap_height)
+        fid = ctx.fri_begin(ids, alpha, arity_bits, final_log, cap_height, ext=ext)
         caps_early = [ctx.fri_cap(fid, 0)]
         for k in range(R):
             ctx.fri_fold(fid, [betas[k]])
             if k + 1 < R:
                 caps_early.append(ctx.fri_cap(fid, k + 1))
     else:
-        fid = ctx.fri_begin(ids, alpha, arity_bits, final_log, cap_height, betas=betas[:R])
+        fid = ctx.fri_begin(ids, alpha, arity_bits, final_log, cap_height, betas=betas[:R], ext=ext)
     info = ctx.fri_info(fid)
+    assert info["ext"] == ext
     ldes = [oracle.lde(x, r) for x in xs]
-    st = oracle.fri_commit(ldes, [x.shape[0] for x in xs], alpha, betas, arity_bits, final_log, cap_height)
+    st = oracle.fri_commit(ldes, [x.shape[0] for x in xs], alpha, betas, arity_bits, final_log, cap_height, ext=ext)
     assert info["rounds"] == R == len(st["arities"])
     assert info["arities"] == st["arities"]
     assert info["heights"] == st["heights"]
@@ -104,6 +108,25 @@ FRI_CASES = [
 @pytest.mark.parametrize("shapes,r,h_lde,a,final_log,h", FRI_CASES)
 def test_fri_matches_oracle(v3c, ctx, shapes, r, h_lde, a, final_log, h):
     run_case(v3c, ctx, shapes, r, h_lde, a, final_log, h, seed=sum(c for c, _ in shapes) + a)
+
+
+EXT_CASES = [
+    ([(8, 10)], 3, 0, 4, 5, 4),
+    ([(8, 10)], 3, 0, 3, 5, 2),     # ragged last round
+    ([(5, 9)], 2, 1, 1, 3, 3),      # arity 2: leaves of 4 words, zero-padded, not hashed
+    ([(13, 11), (6, 11)], 3, 2, 4, 4, 3),
+    ([(1, 4)], 1, 0, 4, 5, 0),      # no fold
+]
+
+
+@pytest.mark.parametrize("shapes,r,h_lde,a,final_log,h", EXT_CASES)
+def test_fri_extension_matches_oracle(v3c, ctx, shapes, r, h_lde, a, final_log, h):
+    run_case(v3c, ctx, shapes, r, h_lde, a, final_log, h, seed=100 + sum(c for c, _ in shapes) + a, ext=2)
+
+
+def test_fri_extension_stepwise_and_trace_135x2_16(v3c, ctx):
+    run_case(v3c, ctx, [(9, 10)], 3, 0, 2, 3, 4, seed=191, stepwise=True, ext=2)
+    run_case(v3c, ctx, [(135, 16)], 3, 4, 4, 5, 4, seed=235, ext=2)
 
 
 def test_fri_stepwise_equals_oracle(v3c, ctx):
