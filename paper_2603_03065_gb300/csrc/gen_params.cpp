@@ -399,9 +399,9 @@ int main(int argc, char** argv)
         }
     fprintf(f, "}\n");
     // Round constants for the split MDS (21-bit limbs a = bits 0-20,
-    // b = 21-41, c = 42-63), rounds 0..29 plus a zero row 30.  Per round:
-    // [a_i + a_(i+6)] (6), [a_i - a_(i+6) mod 2^32] (6), the same for b
-    // (12), then c_i (12).
+    // b = 21-41, c = 42-63), rounds 0..29 plus a zero row 30.  Per round and
+    // limb: [a_i + a_(i+6)] (6), [a_i - a_(i+6) mod 2^32] (6); a, then b,
+    // then c.
     fprintf(f, "#define V3C_RC_SPLIT_INIT {");
     for (int r = 0; r <= kRounds; r++) {
         uint32_t la[kW], lb[kW], lc[kW];
@@ -417,8 +417,9 @@ int main(int argc, char** argv)
             row[6 + i] = la[i] - la[i + 6];
             row[12 + i] = lb[i] + lb[i + 6];
             row[18 + i] = lb[i] - lb[i + 6];
+            row[24 + i] = lc[i] + lc[i + 6];
+            row[30 + i] = lc[i] - lc[i + 6];
         }
-        for (int i = 0; i < kW; i++) row[24 + i] = lc[i];
         for (int k = 0; k < 36; k++)
             fprintf(f, "%s%s%uu", (r || k) ? ", " : "", k % 12 == 0 ? "\\\n  " : "", (unsigned)row[k]);
     }

@@ -51,9 +51,9 @@ __host__ __device__ constexpr u32 mds_coef(int k)
 }
 
 enum MulKind { MUL_INTRINSIC = 0, MUL_PTX = 1, MUL_WIDE = 2 };
-// MDS_SPLIT: 21-bit limbs; the two low limb vectors use the block form of
-// the circulant (two 6x6 products instead of one 12x12), the top limb the
-// direct product (see mds_split).
+// MDS_SPLIT: 21-bit limbs (the top one 22 bits); every limb vector uses the
+// block form of the circulant, two 6x6 products instead of one 12x12 (see
+// mds_split).
 enum MdsKind { MDS_WIDE = 0, MDS_LIMB = 1, MDS_SPLIT = 2 };
 
 // FOLD2: the limb sums are recombined with 32x32->64 multiply-adds and one
@@ -344,10 +344,36 @@ __host__ __device__ constexpr u32 split_d(int i, int j)
     return mds_coef(((j - i) % 12 + 12) % 12) - mds_coef(((j - i + 6) % 12 + 12) % 12);  // mod 2^32
 }
 
-// y = M x + rc for one vector of 21-bit limbs.  Bounds: u < 2^22, so
-// P <= 6 * 126 * (2^22 - 2) + 2^22 < 2^32; |v| < 2^21 and |Q| < 2^30; the true
-// P + Q and P - Q are 2 y in [0, 2^32), so the 32-bit sums are exact and the
-// halving is a logical shift.  init = [P inits (6), Q inits (6)].
+// Sums over the MDS row and over one row of |A - B|, for the bounds below.
+__host__ __device__ constexpr u32 mds_row_sum()
+{
+    u32 t = 0;
+    for (int k = 0; k < 12; k++) t += mds_coef(k);
+    return t;
+}
+__host__ __device__ constexpr u32 split_d_abs_sum()
+{
+    u32 t = 0;
+    for (int j = 0; j < 6; j++) {
+        int d = (int)mds_coef(j) - (int)mds_coef(j + 6);
+        t += (u32)(d < 0 ? -d : d);
+    }
+    return t;
+}
+// Limbs below 2^22 (the top limb of a 64-bit lane; the low limbs are
+// narrower), constants' limbs below 2^22 as well.  P sums S = sum(m) < 2^10
+// products of u = x_j + x_(j+6) < 2^23; Q sums products of |v| < 2^22 with
+// |A - B| entries; y = sum_j m x_j + rc < S 2^22 + 2^22, and P + Q, P - Q are
+// 2 y, so none of them leaves [0, 2^32) (|Q| stays below 2^31).
+static_assert((unsigned long long)mds_row_sum() * ((1u << 23) - 2) + (1u << 23) < (1ull << 32), "P bound");
+static_assert((unsigned long long)(split_d_abs_sum() + 1) * (1u << 22) < (1ull << 31), "Q bound");
+static_assert(2ull * ((unsigned long long)mds_row_sum() * ((1u << 22) - 1) + (1u << 22)) < (1ull << 32),
+              "output bound");
+
+// y = M x + rc for one vector of limbs below 2^22.  The 32-bit sums are exact
+// (bounds above): P and Q as signed values mod 2^32, P + Q and P - Q as the
+// even values 2 y, so the halving is a logical shift.  init = [P inits (6),
+// Q inits (6)]: rc_i + rc_(i+6) and rc_i - rc_(i+6).
 template <class C>
 __device__ __forceinline__ void split6(const u32 (&x)[12], const u32* init, u32 (&y)[12])
 {
@@ -370,7 +396,8 @@ __device__ __forceinline__ void split6(const u32 (&x)[12], const u32* init, u32 
     }
 }
 
-// s <- M s (+ the next round's constants, from init) with 21-bit limbs.
+// s <- M s (+ the next round's constants, from init) with limbs of 21, 21
+// and 22 bits, each through the block form.
 template <class C>
 __device__ __forceinline__ void mds_split(u64 (&s)[12], const u32* init)
 {
@@ -381,17 +408,12 @@ __device__ __forceinline__ void mds_split(u64 (&s)[12], const u32* init)
         b[j] = (u32)(s[j] >> 21) & 0x1FFFFFu;
         c[j] = (u32)(s[j] >> 42);
     }
-    u32 ya[12], yb[12];
+    u32 ya[12], yb[12], yc[12];
     split6<C>(a, init, ya);
     split6<C>(b, init + 12, yb);
+    split6<C>(c, init + 24, yc);
 #pragma unroll
-    for (int i = 0; i < 12; i++) {
-        // The 22-bit top limb: direct product; 12 * 63 * (2^22 - 1) + 2^22 < 2^32.
-        u32 Cc = init[24 + i];
-#pragma unroll
-        for (int j = 0; j < 12; j++) Cc = mac_const(Cc, c[j], (int)mds_coef((j - i + 12) % 12), C::SHIFT);
-        s[i] = limb_fold21(ya[i], yb[i], Cc);
-    }
+    for (int i = 0; i < 12; i++) s[i] = limb_fold21(ya[i], yb[i], yc[i]);
 }
 
 // s <- M s, M[i][j] = m[(j - i) mod 12].  With C::ARCM the accumulators start
