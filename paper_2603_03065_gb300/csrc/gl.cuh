@@ -24,7 +24,7 @@ constexpr u64 EPS = 0xFFFFFFFFull;  // 2^64 mod p
 __host__ __device__ __forceinline__ u64 canon(u64 x) { return x >= P ? x - P : x; }
 
 // 128-bit (hi:lo) -> a value in [0, 2^64) congruent mod p.
-__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi)
+__host__ __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi)
 {
     u32 h0 = (u32)hi;
     u32 h1 = (u32)(hi >> 32);
@@ -80,7 +80,7 @@ __device__ __forceinline__ u64 mul_nc(u64 a, u64 b) { return reduce128_ptx(a * b
 __device__ __forceinline__ u64 mul(u64 a, u64 b) { return canon(mul_nc(a, b)); }
 
 // Canonical add/sub: inputs and outputs in [0, p).
-__device__ __forceinline__ u64 add(u64 a, u64 b)
+__host__ __device__ __forceinline__ u64 add(u64 a, u64 b)
 {
     u64 s = a + b;
     // On carry the true sum is s + 2^64 < 2p, and s - p (mod 2^64) = s + EPS.
@@ -88,11 +88,37 @@ __device__ __forceinline__ u64 add(u64 a, u64 b)
     return s;
 }
 
-__device__ __forceinline__ u64 sub(u64 a, u64 b)
+__host__ __device__ __forceinline__ u64 sub(u64 a, u64 b)
 {
     u64 d = a - b;
     if (a < b) d += P;  // wrapped a - b + 2^64, plus p (mod 2^64) = a - b + p
     return d;
+}
+
+// x 2^e mod p for canonical x and 0 <= e < 96, canonical result; e is a
+// constant wherever this is inlined into unrolled code, so only one branch
+// remains.  With 2^64 = 2^32 - 1 and 2^128 = -2^32 (mod p):
+//   e <= 32:      x 2^e = lo + 2^64 h (h < 2^32) = lo + h (2^32 - 1);
+//   32 < e < 64:  lo + 2^64 hi, the 128-bit reduction;
+//   64 <= e < 96: y = x 2^(e-64) = yl + 2^64 yh (yh < 2^31), and
+//                 x 2^e = y 2^64 = yl 2^64 + yh 2^128 = (yl 2^64 mod p) - yh 2^32.
+// Multiplying by 2^(e+96) is the negation of this (2^96 = -1 mod p).
+__host__ __device__ __forceinline__ u64 mul_pow2(u64 x, u32 e)
+{
+    if (e == 0) return x;
+    if (e <= 32) {
+        u64 lo = x << e;
+        u64 h = x >> (64 - e);
+        u64 t = (h << 32) - h;  // < 2^64 - 2^32
+        u64 r = lo + t;
+        if (r < t) r += EPS;    // carry: r + 2^64 = r + EPS, and r < t here
+        return canon(r);
+    }
+    if (e < 64) return canon(reduce128(x << e, x >> (64 - e)));
+    const u32 f = e - 64;
+    const u64 yl = f ? x << f : x;
+    const u64 yh = f ? x >> (64 - f) : 0;
+    return sub(canon(reduce128(0, yl)), yh << 32);
 }
 
 // a in [0, 2^64), k canonical: a + k mod p as a value in [0, 2^64).

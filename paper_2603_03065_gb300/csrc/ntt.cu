@@ -172,21 +172,124 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
 // ---------------------------------------------------------------- in-CTA DFTs
 
 // B transforms of size L = 2^logL stored back to back in shared memory,
-// radix-2 stages applied K at a time in registers: each thread loads the
-// 2^K elements that K consecutive stages combine, runs those stages, and
-// stores them back, so a transform costs ceil(logL / K) shared-memory
-// round trips instead of logL.
+// radix-2^K passes applied in registers: each thread loads the 2^K elements
+// that K consecutive radix-2 stages combine, transforms them, and stores
+// them back, so a transform costs ceil(logL / K) shared-memory round trips
+// instead of logL.
 //
-// Decimation in frequency (natural order in, bit-reversed out): stage s has
-// half-span h = L >> (s+1) and butterfly (e, e+h) uses w_{2h}^(e mod h) =
-// tw[(e mod h) << s], tw[j] = w_L^(+-j) for j < L/2.  A pass over stages
-// s0 .. s0+K-1 takes the elements base + j*stride, stride = L >> (s0+K).
+// A pass is a 2^K-point DFT plus one twiddle per element (the Cooley-Tukey
+// split of a size-2^(K+j) transform into 2^K-point and 2^j-point ones).
+// Decimation in frequency (natural order in, bit-reversed out), stages s0 ..
+// s0+K-1, stride 2^l with l = logL - s0 - K: the thread holds
+// v_j = a[i0 + j 2^l] with i0 mod 2^l = lo; after the 2^K-point DIF,
+// v_j is scaled by w_{2^(l+K)}^(lo bitrev_K(j)) = w_L^((lo bitrev_K(j)) 2^s0).
+// Decimation in time (bit-reversed in, natural out), stages s0 .. s0+K-1:
+// v_j = a[i0 + j 2^s0] with i0 mod 2^s0 = lo is first scaled by
+// w_{2^(s0+K)}^(lo bitrev_K(j)) = w_L^((lo bitrev_K(j)) 2^(logL-s0-K)),
+// then the 2^K-point DIT runs.  The table tw holds w_L^i (or w_L^-i) for
+// i < L/2; w_L^(i + L/2) = -w_L^i.
+//
+// The 2^K-point DFTs (K <= 5) need only 32nd roots of unity, and these are
+// powers of 2: 2 has order 192 mod p (2^96 = -1) and w_32 = 2^kG32, so their
+// twiddles are shifts with a special-form reduction (gl::mul_pow2) instead
+// of full products.  A twiddle 2^e with e >= 96 is -2^(e-96); the sign is
+// folded into the butterfly's add and subtract.
+//
 // Shared-memory arrays of 8-byte words are stored XOR-swizzled on 16-word
 // lines: word i lives at sw(i).  A half-warp that walks a column of a strided
 // pass then touches 16 different bank pairs instead of one.
 __device__ __forceinline__ u32 sw(u32 i) { return i ^ ((i >> 4) & 15u); }
 
-template <int K>
+constexpr u64 cx_mul(u64 a, u64 b) { return (u64)((unsigned __int128)a * b % gl::P); }
+constexpr u64 cx_pow(u64 a, u64 e)
+{
+    u64 r = 1;
+    while (e) {
+        if (e & 1) r = cx_mul(r, a);
+        a = cx_mul(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+constexpr u32 root32_log2()
+{
+    const u64 w = cx_pow(7, (gl::P - 1) / 32);
+    u64 t = 1;
+    for (u32 g = 0; g < 192; g++) {
+        if (t == w) return g;
+        t = cx_mul(t, 2);
+    }
+    return 192;
+}
+constexpr u32 kG32 = root32_log2();
+static_assert(kG32 < 192 && kG32 % 6 == 0 && (kG32 / 6) % 2 == 1, "w_32 must be an odd power of 2^6");
+
+// Exponent of 2 for w_R^m (INV: w_R^-m), R = 2^K.
+__host__ __device__ constexpr u32 root_exp(int K, bool INV, int m)
+{
+    const u32 e = (u32)((kG32 * (u32)(32 >> K) * (u32)m) % 192u);
+    return INV ? (192u - e) % 192u : e;
+}
+
+__host__ __device__ constexpr int bitrev_c(int j, int K)
+{
+    int r = 0;
+    for (int b = 0; b < K; b++) r |= ((j >> b) & 1) << (K - 1 - b);
+    return r;
+}
+
+// In-register 2^K-point DIF, natural order in, bit-reversed out.
+template <int K, bool INV>
+__device__ __forceinline__ void small_dif(u64 (&v)[1 << K])
+{
+#pragma unroll
+    for (int t = 0; t < K; t++) {
+        const int h = (1 << K) >> (t + 1);
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++) {
+            if (j & h) continue;
+            const u32 e = root_exp(K, INV, (j & (h - 1)) << t);  // w_{2h}^(j mod h)
+            const u64 x = v[j], y = v[j + h];
+            v[j] = gl::add(x, y);
+            v[j + h] = e < 96 ? gl::mul_pow2(gl::sub(x, y), e) : gl::mul_pow2(gl::sub(y, x), e - 96);
+        }
+    }
+}
+
+// In-register 2^K-point DIT, bit-reversed order in, natural out.
+template <int K, bool INV>
+__device__ __forceinline__ void small_dit(u64 (&v)[1 << K])
+{
+#pragma unroll
+    for (int t = 0; t < K; t++) {
+        const int h = 1 << t;
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++) {
+            if (j & h) continue;
+            const u32 e = root_exp(K, INV, (j & (h - 1)) << (K - 1 - t));  // w_{2h}^(j mod h)
+            const u64 x = v[j];
+            const u64 y = gl::mul_pow2(v[j + h], e < 96 ? e : e - 96);
+            if (e < 96) {
+                v[j] = gl::add(x, y);
+                v[j + h] = gl::sub(x, y);
+            } else {
+                v[j] = gl::sub(x, y);
+                v[j + h] = gl::add(x, y);
+            }
+        }
+    }
+}
+
+// v * w_L^e for 0 <= e < L from the half table (w_L^(e + L/2) = -w_L^e).
+__device__ __forceinline__ u64 mul_tw(u64 v, const u64* tw, u32 e, u32 logL)
+{
+    const u32 half = (1u << logL) >> 1;
+    u64 t = tw[sw(half ? e & (half - 1) : 0)];
+    if (half && (e & half)) t = gl::P - t;  // roots of unity are nonzero
+    return gl::mul(v, t);
+}
+
+template <int K, bool INV>
 __device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
 {
     const u32 lst = logL - s0 - K;  // log2 of the stride
@@ -200,24 +303,10 @@ __device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const 
         u64 v[1 << K];
 #pragma unroll
         for (int j = 0; j < (1 << K); j++) v[j] = a[sw(i0 + ((u32)j << lst))];
+        small_dif<K, INV>(v);
+        if (lst) {
 #pragma unroll
-        for (int t = 0; t < K; t++) {
-            const u32 s = s0 + t;
-            const int hb = 1 << (K - 1 - t);
-#pragma unroll
-            for (int j = 0; j < (1 << K); j++) {
-                if (j & hb) continue;
-                const int jj = j | hb;
-                u64 u = v[j], y = v[jj];
-                v[j] = gl::add(u, y);
-                u64 d = gl::sub(u, y);
-                if (s + 1 == logL) {
-                    v[jj] = d;  // last stage: h = 1, twiddle 1
-                } else {
-                    u32 pos = lo + ((u32)(j & (hb - 1)) << lst);
-                    v[jj] = gl::mul(d, tw[sw(pos << s)]);
-                }
-            }
+            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw(v[j], tw, (lo * (u32)bitrev_c(j, K)) << s0, logL);
         }
 #pragma unroll
         for (int j = 0; j < (1 << K); j++) a[sw(i0 + ((u32)j << lst))] = v[j];
@@ -225,11 +314,7 @@ __device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const 
     __syncthreads();
 }
 
-// Decimation in time (bit-reversed order in, natural out): stage s has
-// half-span h = 2^s and butterfly (e, e+h) uses w_{2h}^(e mod h) =
-// tw[(e mod h) << (logL-1-s)].  A pass over stages s0 .. s0+K-1 takes the
-// elements base + (j << s0).
-template <int K>
+template <int K, bool INV>
 __device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
 {
     const u32 G = B << (logL - K);
@@ -242,24 +327,12 @@ __device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const 
         u64 v[1 << K];
 #pragma unroll
         for (int j = 0; j < (1 << K); j++) v[j] = a[sw(i0 + ((u32)j << s0))];
+        if (s0) {
+            const u32 sh = logL - s0 - K;
 #pragma unroll
-        for (int t = 0; t < K; t++) {
-            const u32 s = s0 + t;
-#pragma unroll
-            for (int j = 0; j < (1 << K); j++) {
-                if (j & (1 << t)) continue;
-                const int jj = j | (1 << t);
-                u64 tt;
-                if (s == 0) {
-                    tt = v[jj];  // first stage: h = 1, twiddle 1
-                } else {
-                    u32 pos = lo + ((u32)(j & ((1 << t) - 1)) << s0);
-                    tt = gl::mul(v[jj], tw[sw(pos << (logL - 1 - s))]);
-                }
-                v[jj] = gl::sub(v[j], tt);
-                v[j] = gl::add(v[j], tt);
-            }
+            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw(v[j], tw, (lo * (u32)bitrev_c(j, K)) << sh, logL);
         }
+        small_dit<K, INV>(v);
 #pragma unroll
         for (int j = 0; j < (1 << K); j++) a[sw(i0 + ((u32)j << s0))] = v[j];
     }
@@ -275,32 +348,35 @@ __device__ __forceinline__ u32 pass_k(u32 B, u32 logL, u32 kcap)
     return max(1u, min(k, kcap));
 }
 
+// INV: tw holds w_L^-i and the in-register DFTs use the inverse roots.
+template <bool INV>
 __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, u32 kcap)
 {
     const u32 kmax = pass_k(B, logL, kcap);
     for (u32 s = 0; s < logL;) {
         u32 k = min(kmax, logL - s);
         switch (k) {
-        case 4: dif_pass<4>(a, B, logL, s, tw); break;
-        case 3: dif_pass<3>(a, B, logL, s, tw); break;
-        case 2: dif_pass<2>(a, B, logL, s, tw); break;
-        default: dif_pass<1>(a, B, logL, s, tw); break;
+        case 4: dif_pass<4, INV>(a, B, logL, s, tw); break;
+        case 3: dif_pass<3, INV>(a, B, logL, s, tw); break;
+        case 2: dif_pass<2, INV>(a, B, logL, s, tw); break;
+        default: dif_pass<1, INV>(a, B, logL, s, tw); break;
         }
         s += k;
     }
 }
 
 // Stages s < first are skipped (the caller has already applied them).
+template <bool INV>
 __device__ __forceinline__ void dft_dit(u64* a, u32 B, u32 logL, const u64* tw, u32 first, u32 kcap)
 {
     const u32 kmax = pass_k(B, logL, kcap);
     for (u32 s = first; s < logL;) {
         u32 k = min(kmax, logL - s);
         switch (k) {
-        case 4: dit_pass<4>(a, B, logL, s, tw); break;
-        case 3: dit_pass<3>(a, B, logL, s, tw); break;
-        case 2: dit_pass<2>(a, B, logL, s, tw); break;
-        default: dit_pass<1>(a, B, logL, s, tw); break;
+        case 4: dit_pass<4, INV>(a, B, logL, s, tw); break;
+        case 3: dit_pass<3, INV>(a, B, logL, s, tw); break;
+        case 2: dit_pass<2, INV>(a, B, logL, s, tw); break;
+        default: dit_pass<1, INV>(a, B, logL, s, tw); break;
         }
         s += k;
     }
@@ -371,7 +447,7 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
         }
         cp_async_wait_all();
         __syncthreads();
-        dft_dif(data, T2, l1, tw, J.kcap);
+        dft_dif<true>(data, T2, l1, tw, J.kcap);
         u64* Y = J.Y + ((size_t)col << J.plan.log_n);
         for (u32 e = threadIdx.x; e < (T2 << l1); e += blockDim.x) {
             u32 u = e & (T2 - 1), t = e >> lT2;
@@ -424,7 +500,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
                             : J.x + ((size_t)col << J.plan.log_n);
         for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[sw(e)] = __ldcs(src + e);
         __syncthreads();
-        dft_dif(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
+        dft_dif<true>(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
         const u64* sc = J.plan.scale + ((size_t)k1 << l2);
         // Scale by 7^j / n and spread for the zero-padded size-M transform.
         // In bit-reversed order over log M bits, coefficient k2 sits at
@@ -434,7 +510,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
         __syncthreads();
         for (u32 e = threadIdx.x; e < M; e += blockDim.x) data[sw(e)] = stage[sw(e >> r)];
         __syncthreads();
-        dft_dit(data, 1, lM, twf, r, J.kcap);
+        dft_dit<false>(data, 1, lM, twf, r, J.kcap);
         if (l1) {
             // Z is q-blocked: block q >> lQ holds [k1][q & (Q-1)], so that
             // stage C reads one contiguous run per column.
@@ -522,7 +598,7 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
         }
         cp_async_wait_all();
         __syncthreads();
-        dft_dif(data, kStageCCols * Q, l1, tw, J.kcap);
+        dft_dif<false>(data, kStageCCols * Q, l1, tw, J.kcap);
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
