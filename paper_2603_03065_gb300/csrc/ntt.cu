@@ -339,12 +339,13 @@ __device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const 
     __syncthreads();
 }
 
-// Largest radix exponent that keeps every thread busy, capped at 2^4 (32
-// registers of values per thread).
+// Largest radix exponent that keeps every thread busy, capped at kcap
+// (2^5 values per thread at most).  A higher radix with threads left idle
+// measured slower on the 1024-point inverse transform of stage B.
 __device__ __forceinline__ u32 pass_k(u32 B, u32 logL, u32 kcap)
 {
     u32 per = (B << logL) / blockDim.x;  // elements per thread
-    u32 k = per >= 16 ? 4 : per >= 8 ? 3 : per >= 4 ? 2 : 1;
+    u32 k = per >= 32 ? 5 : per >= 16 ? 4 : per >= 8 ? 3 : per >= 4 ? 2 : 1;
     return max(1u, min(k, kcap));
 }
 
@@ -373,6 +374,7 @@ __device__ __forceinline__ void dft_dit(u64* a, u32 B, u32 logL, const u64* tw, 
     for (u32 s = first; s < logL;) {
         u32 k = min(kmax, logL - s);
         switch (k) {
+        case 5: dit_pass<5, INV>(a, B, logL, s, tw); break;
         case 4: dit_pass<4, INV>(a, B, logL, s, tw); break;
         case 3: dit_pass<3, INV>(a, B, logL, s, tw); break;
         case 2: dit_pass<2, INV>(a, B, logL, s, tw); break;
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
         __syncthreads();
         for (u32 e = threadIdx.x; e < M; e += blockDim.x) data[sw(e)] = stage[sw(e >> r)];
         __syncthreads();
-        dft_dit<false>(data, 1, lM, twf, r, J.kcap);
+        dft_dit<false>(data, 1, lM, twf, r, J.kcap + 1);  // the forward M-point transform may use radix 2^5
         if (l1) {
             // Z is q-blocked: block q >> lQ holds [k1][q & (Q-1)], so that
             // stage C reads one contiguous run per column.
