@@ -399,9 +399,10 @@ int main(int argc, char** argv)
         }
     fprintf(f, "}\n");
     // Round constants for the split MDS (21-bit limbs a = bits 0-20,
-    // b = 21-41, c = 42-63), rounds 0..29 plus a zero row 30.  Per round and
-    // limb: [a_i + a_(i+6)] (6), [a_i - a_(i+6) mod 2^32] (6); a, then b,
-    // then c.
+    // b = 21-41, c = 42-63), rounds 0..29 plus a zero row 30, all mod 2^32.
+    // Limbs a and b (second split): with P_i = a_i + a_(i+6),
+    // [P_i + P_(i+3)] (3), [P_i - P_(i+3)] (3), [2 (a_i - a_(i+6))] (6);
+    // limb c: [c_i + c_(i+6)] (6), [c_i - c_(i+6)] (6).
     fprintf(f, "#define V3C_RC_SPLIT_INIT {");
     for (int r = 0; r <= kRounds; r++) {
         uint32_t la[kW], lb[kW], lc[kW];
@@ -412,11 +413,18 @@ int main(int argc, char** argv)
             lc[i] = (uint32_t)(v >> 42);
         }
         uint32_t row[36];
+        const uint32_t* lab[2] = {la, lb};
+        for (int h = 0; h < 2; h++) {
+            const uint32_t* l = lab[h];
+            uint32_t Pi[6];
+            for (int i = 0; i < 6; i++) Pi[i] = l[i] + l[i + 6];
+            for (int i = 0; i < 3; i++) {
+                row[12 * h + i] = Pi[i] + Pi[i + 3];
+                row[12 * h + 3 + i] = Pi[i] - Pi[i + 3];
+            }
+            for (int i = 0; i < 6; i++) row[12 * h + 6 + i] = 2u * (l[i] - l[i + 6]);
+        }
         for (int i = 0; i < 6; i++) {
-            row[i] = la[i] + la[i + 6];
-            row[6 + i] = la[i] - la[i + 6];
-            row[12 + i] = lb[i] + lb[i + 6];
-            row[18 + i] = lb[i] - lb[i + 6];
             row[24 + i] = lc[i] + lc[i + 6];
             row[30 + i] = lc[i] - lc[i + 6];
         }
