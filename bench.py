@@ -893,7 +893,7 @@ def run_seteq(args):
         "roofline": {"bound": "hbm", "kernel": "k_seteq_reduce+k_seteq_carries+k_seteq_apply",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "bytes_per_launch": alg_bytes, "ms_per_launch": seq_ms, "peak_source": "measured",
-                     "note": "algorithmic bytes: X and Y read once, Z written once; the kernels read X and Y twice"},
+                     "note": "algorithmic bytes: X and Y read once, Z written once; the kernels also write and read back 16 bytes of compressed (num, den) per tuple"},
         "stages_ms_per_launch": stage_ms,
     }
     if not args.no_cpu_baseline:

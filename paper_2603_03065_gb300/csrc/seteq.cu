@@ -66,9 +66,22 @@ __device__ __forceinline__ u32 seq_find(const SeqJob* __restrict__ jobs, u32 njo
 __device__ __forceinline__ u64 compress(const u64* __restrict__ t, u32 T, u64 beta)
 {
     // Horner from the last component: sum_k t_k beta^k, on values in
-    // [0, 2^64) congruent mod p, canonical at the end.
-    u64 s = __ldg(t + T - 1);
-    for (int k = (int)T - 2; k >= 0; k--) s = gl::add_nc(gl::mul_nc(s, beta), __ldg(t + k));
+    // [0, 2^64) congruent mod p, canonical at the end.  A tuple of even
+    // width at a 16-byte aligned address is read in 16-byte pairs.
+    u64 s;
+    if (!(T & 1) && !((uintptr_t)t & 15)) {
+        const ulonglong2* t2 = reinterpret_cast<const ulonglong2*>(t);
+        ulonglong2 q = __ldg(t2 + (T >> 1) - 1);
+        s = gl::add_nc(gl::mul_nc(q.y, beta), q.x);
+        for (int k = (int)(T >> 1) - 2; k >= 0; k--) {
+            q = __ldg(t2 + k);
+            s = gl::add_nc(gl::mul_nc(s, beta), q.y);
+            s = gl::add_nc(gl::mul_nc(s, beta), q.x);
+        }
+    } else {
+        s = __ldg(t + T - 1);
+        for (int k = (int)T - 2; k >= 0; k--) s = gl::add_nc(gl::mul_nc(s, beta), __ldg(t + k));
+    }
     return gl::canon(s);
 }
 
@@ -224,8 +237,9 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __res
             pn = gl::mul(pn, num[k]);
             pd = gl::mul(pd, den[k]);
         }
+        // N carries the factor D^-1 from the start: Z_i = (N_{<i} D^-1) D_{>=i}.
         const u64 inv = __ldg(J.inv);
-        u64 N = gl::mul(__ldg(J.carry + 2 * lt), block_exclusive<false>(pn, sh));
+        u64 N = gl::mul(gl::mul(__ldg(J.carry + 2 * lt), inv), block_exclusive<false>(pn, sh));
         u64 S = gl::mul(__ldg(J.carry + 2 * lt + 1), block_exclusive<true>(pd, sh));
         // S: denominators after this thread's elements; walk them backwards.
         u64 suf[kSeqPer];
@@ -237,9 +251,9 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __res
         const u64 ebase = tbase + (u64)kSeqPer * t;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
-            s_num[seq_pad(kSeqPer * t + k)] = gl::mul(gl::mul(N, suf[k]), inv);  // every read above is done
+            s_num[seq_pad(kSeqPer * t + k)] = gl::mul(N, suf[k]);  // every read above is done
             N = gl::mul(N, num[k]);
-            if (ebase + k + 1 == J.L) J.z[J.L] = gl::mul(N, inv);
+            if (ebase + k + 1 == J.L) J.z[J.L] = N;
         }
         __syncthreads();
 #pragma unroll
