@@ -110,13 +110,16 @@ __global__ void __launch_bounds__(128) k_snap_centroids(const u64* __restrict__ 
 // root_cb = Hash of the flattened codebooks.  The sponge is sequential
 // (count / 8 permutations, each on the previous state), so its time is the
 // latency of one permutation times their number.  One warp shares each
-// permutation: lane l < 12 holds state word s_l.  A round adds the round
-// constant, applies the S-box (every lane in a full round, lane 0 in a
-// partial one), and forms its MDS row
-//   s'_l = sum_j m[(j - l) mod 12] s_j
-// from the other lanes' words, gathered by shuffles.  The products by
-// m < 2^6 are summed unreduced in 128 bits and reduced once per round.
-// Words stay non-canonical (in [0, 2^64), congruent mod p) until the digest.
+// permutation: lane l < 12 holds state word s_l.  A round applies the S-box
+// (every lane in a full round, lane 0 in a partial one) and forms its MDS
+// row plus the next round's constant,
+//   s'_l = sum_j m[(j - l) mod 12] s_j + rc_(r+1)[l],
+// on 21/21/22-bit limbs: every lane splits its word once, each term is three
+// 32-bit shuffles and three 32-bit multiply-adds (no carries: the sums stay
+// below 2^32 since sum m < 2^9 and the constant limbs are below 2^22), and
+// the limb sums are folded once per round.  The constants' limbs sit in
+// shared memory, one 16-byte row per lane and round.  Words stay
+// non-canonical (in [0, 2^64), congruent mod p) until the digest.
 __constant__ u32 c_mds_row[12] = V3C_MDS_ROW_INIT;
 
 // x^7 on non-canonical values (inputs and output in [0, 2^64)).
@@ -133,15 +136,23 @@ __device__ __forceinline__ u64 sbox7_nc(u64 x)
 __global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb, u32 count, u64* __restrict__ out,
                                                      const u64* __restrict__ same, const u64* __restrict__ cached)
 {
+    __shared__ uint4 s_rc[31][12];  // limbs (a, b, c) of rc_r[l]; row 30 is zero
     const u32 l = threadIdx.x;
     if (same && *same == 0) {
         if (l < 4) out[l] = cached[l];
         return;
     }
+    for (u32 e = l; e < 31 * 12; e += 32) {
+        const u32 r = e / 12, i = e % 12;
+        const u64 v = r < 30 ? pos::c_rc[r][i] : 0;
+        s_rc[r][i] = make_uint4((u32)v & 0x1FFFFFu, (u32)(v >> 21) & 0x1FFFFFu, (u32)(v >> 42), 0);
+    }
+    __syncwarp();
     const bool own = l < 12;
+    const u32 li = own ? l : 0;
     u32 m[12];  // m[j] = row[(j - l) mod 12]: this lane's MDS row
 #pragma unroll
-    for (int j = 0; j < 12; j++) m[j] = c_mds_row[(j + 12 - (own ? l : 0)) % 12];
+    for (int j = 0; j < 12; j++) m[j] = c_mds_row[(j + 12 - li) % 12];
     u64 x = 0;  // s_l, non-canonical in [0, 2^64) between rounds
     if (count <= 4) {
         if (l < count) x = __ldg(cb + l);
@@ -152,31 +163,26 @@ __global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb
             if (l < len) x = next;  // overwrite lanes 0 .. len-1
             if (st + 8 < count)     // prefetch the next chunk during the permutation
                 next = l < 8 && st + 8 + l < count ? __ldg(cb + st + 8 + l) : 0;
+            x = gl::add_nc_small(x, own ? pos::c_rc[0][li] : 0);  // round 0's constant; later ones ride the MDS
             for (int r = 0; r < 30; r++) {
                 const bool full = r < 4 || r >= 26;
-                const u64 rc = pos::c_rc[r][own ? l : 0];  // always an in-bounds read
-                x = gl::add_nc_small(x, own ? rc : 0);
                 // Every lane computes x^7 without branching.  In a partial round
                 // only lane 0's word takes it: the other 11 gathered words are
                 // the pre-S-box ones, so their products overlap the S-box chain.
                 const u64 y = sbox7_nc(x);
                 const u64 v = full ? y : x;
-                // Three independent 128-bit sums (j mod 3) shorten the dependency chain.
-                u64 lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+                const uint4 k = s_rc[r + 1][li];
+                u32 A = own ? k.x : 0, B = own ? k.y : 0, C = own ? k.z : 0;
+                const u32 ya = (u32)y & 0x1FFFFFu, yb = (u32)(y >> 21) & 0x1FFFFFu, yc = (u32)(y >> 42);
+                const u32 va = (u32)v & 0x1FFFFFu, vb = (u32)(v >> 21) & 0x1FFFFFu, vc = (u32)(v >> 42);
 #pragma unroll
                 for (int j = 11; j >= 0; j--) {
-                    u64 sj = __shfl_sync(0xffffffffu, j == 0 ? y : v, j);
-                    u64 p0 = (u64)(u32)sj * m[j], p1 = (sj >> 32) * m[j];  // sj m = p0 + p1 2^32
-                    u64 add_lo = p0 + (p1 << 32);
-                    u64 c0 = add_lo < p0;
-                    lo[j % 3] += add_lo;
-                    hi[j % 3] += (p1 >> 32) + c0 + (lo[j % 3] < add_lo);
+                    // The sender's word: lane 0 gives its S-box output.
+                    A += __shfl_sync(0xffffffffu, j == 0 ? ya : va, j) * m[j];
+                    B += __shfl_sync(0xffffffffu, j == 0 ? yb : vb, j) * m[j];
+                    C += __shfl_sync(0xffffffffu, j == 0 ? yc : vc, j) * m[j];
                 }
-                u64 a = lo[0] + lo[1];
-                u64 h = hi[0] + hi[1] + (a < lo[0]);
-                u64 b = a + lo[2];
-                h += hi[2] + (b < a);
-                x = gl::reduce128_ptx(b, h);
+                x = pos::limb_fold21(A, B, C);
             }
         }
     }
