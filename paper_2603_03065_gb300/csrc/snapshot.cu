@@ -122,13 +122,38 @@ __global__ void __launch_bounds__(128) k_snap_centroids(const u64* __restrict__ 
 // non-canonical (in [0, 2^64), congruent mod p) until the digest.
 __constant__ u32 c_mds_row[12] = V3C_MDS_ROW_INIT;
 
+// Products for a latency-bound chain: the reduction written with compares
+// (gl::reduce128) has a shorter dependency chain than the carry-chain form.
+__device__ __forceinline__ u64 mul_lat(u64 a, u64 b) { return gl::reduce128(a * b, __umul64hi(a, b)); }
+
 // x^7 on non-canonical values (inputs and output in [0, 2^64)).
 __device__ __forceinline__ u64 sbox7_nc(u64 x)
 {
-    u64 x2 = gl::mul_nc(x, x);
-    u64 x3 = gl::mul_nc(x2, x);
-    u64 x4 = gl::mul_nc(x2, x2);
-    return gl::mul_nc(x3, x4);
+    u64 x2 = mul_lat(x, x);
+    u64 x3 = mul_lat(x2, x);
+    u64 x4 = mul_lat(x2, x2);
+    return mul_lat(x3, x4);
+}
+
+__device__ __forceinline__ void limbs21(u64 v, u32& a, u32& b, u32& c)
+{
+    a = (u32)v & 0x1FFFFFu;
+    b = (u32)(v >> 21) & 0x1FFFFFu;
+    c = (u32)(v >> 42);
+}
+
+// Accumulates the MDS terms j in [J0, 12) of this lane's row from the
+// senders' limbs into two accumulators per limb (shorter chains).
+template <int J0>
+__device__ __forceinline__ void mds_terms(u32 a, u32 b, u32 c, const u32 (&m)[12], u32 (&A)[2], u32 (&B)[2],
+                                          u32 (&C)[2])
+{
+#pragma unroll
+    for (int j = J0; j < 12; j++) {
+        A[j & 1] += __shfl_sync(0xffffffffu, a, j) * m[j];
+        B[j & 1] += __shfl_sync(0xffffffffu, b, j) * m[j];
+        C[j & 1] += __shfl_sync(0xffffffffu, c, j) * m[j];
+    }
 }
 
 // With `same` non-null, *same == 0 means the codebooks equal the cached ones
@@ -154,6 +179,26 @@ __global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb
 #pragma unroll
     for (int j = 0; j < 12; j++) m[j] = c_mds_row[(j + 12 - li) % 12];
     u64 x = 0;  // s_l, non-canonical in [0, 2^64) between rounds
+    // One round; the accumulators start from the next round's constant limbs.
+    auto round = [&](int r, bool full) {
+        const uint4 k = s_rc[r + 1][li];
+        u32 A[2] = {own ? k.x : 0, 0}, B[2] = {own ? k.y : 0, 0}, C[2] = {own ? k.z : 0, 0};
+        u32 a, b, c;
+        if (full) {
+            limbs21(sbox7_nc(x), a, b, c);
+            mds_terms<0>(a, b, c, m, A, B, C);
+        } else {
+            // Terms j >= 1 use the pre-S-box words and overlap lane 0's S-box.
+            limbs21(x, a, b, c);
+            mds_terms<1>(a, b, c, m, A, B, C);
+            u32 ya, yb, yc;
+            limbs21(sbox7_nc(x), ya, yb, yc);
+            A[0] += __shfl_sync(0xffffffffu, ya, 0) * m[0];
+            B[0] += __shfl_sync(0xffffffffu, yb, 0) * m[0];
+            C[0] += __shfl_sync(0xffffffffu, yc, 0) * m[0];
+        }
+        x = pos::limb_fold21(A[0] + A[1], B[0] + B[1], C[0] + C[1]);
+    };
     if (count <= 4) {
         if (l < count) x = __ldg(cb + l);
     } else {
@@ -164,26 +209,12 @@ __global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb
             if (st + 8 < count)     // prefetch the next chunk during the permutation
                 next = l < 8 && st + 8 + l < count ? __ldg(cb + st + 8 + l) : 0;
             x = gl::add_nc_small(x, own ? pos::c_rc[0][li] : 0);  // round 0's constant; later ones ride the MDS
-            for (int r = 0; r < 30; r++) {
-                const bool full = r < 4 || r >= 26;
-                // Every lane computes x^7 without branching.  In a partial round
-                // only lane 0's word takes it: the other 11 gathered words are
-                // the pre-S-box ones, so their products overlap the S-box chain.
-                const u64 y = sbox7_nc(x);
-                const u64 v = full ? y : x;
-                const uint4 k = s_rc[r + 1][li];
-                u32 A = own ? k.x : 0, B = own ? k.y : 0, C = own ? k.z : 0;
-                const u32 ya = (u32)y & 0x1FFFFFu, yb = (u32)(y >> 21) & 0x1FFFFFu, yc = (u32)(y >> 42);
-                const u32 va = (u32)v & 0x1FFFFFu, vb = (u32)(v >> 21) & 0x1FFFFFu, vc = (u32)(v >> 42);
-#pragma unroll
-                for (int j = 11; j >= 0; j--) {
-                    // The sender's word: lane 0 gives its S-box output.
-                    A += __shfl_sync(0xffffffffu, j == 0 ? ya : va, j) * m[j];
-                    B += __shfl_sync(0xffffffffu, j == 0 ? yb : vb, j) * m[j];
-                    C += __shfl_sync(0xffffffffu, j == 0 ? yc : vc, j) * m[j];
-                }
-                x = pos::limb_fold21(A, B, C);
-            }
+#pragma unroll 1
+            for (int r = 0; r < 4; r++) round(r, true);
+#pragma unroll 1
+            for (int r = 4; r < 26; r++) round(r, false);
+#pragma unroll 1
+            for (int r = 26; r < 30; r++) round(r, true);
         }
     }
     if (l < 4) out[l] = gl::canon(x);
