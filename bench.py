@@ -298,6 +298,14 @@ def run_v3c(args):
 
     step_e2e()
     torch.cuda.synchronize()
+    # The host link's bandwidth on this machine: one pinned copy of the input.
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    d_x.copy_(pinned.view(d_x.dtype).view(d_x.shape), non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = x.nbytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
     barrier()
     e2e_clocks = ClockSampler(local_rank)
     e2e_clocks.start()
@@ -327,7 +335,7 @@ def run_v3c(args):
             "config": dict(workload_config(args.workload, s), autotune=bool(args.autotune)),
             "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(32 << s.cap_height), "ms_per_step": e2e_s * 1e3,
-                    "clocks": e2e_clk},
+                    "clocks": e2e_clk, "h2d_GBps_measured": h2d_gbs},
             "gpu_launches": int(launches),
             "clocks": clk,
             "roofline": {"bound": "alu", "kernel": "k_leaf_hash", "achieved": achieved, "peak": peak,
@@ -371,7 +379,9 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     for tag, flags, tune in (("batched_graph_autotune", 0, True), ("batched_graph", 0, False),
                              ("batched_direct", v3c.FLAG_NO_GRAPH, False)):
-        ctx = v3c.Context(0, flags=flags, autotune=tune)
+        # An explicit budget (the 64 batches hold 19.7 GB resident), so the
+        # line does not depend on the free memory seen at context creation.
+        ctx = v3c.Context(0, hbm_budget_bytes=64 << 30, flags=flags, autotune=tune)
         ds = [v3c.to_device_u64(x) for x in xs]
         items = [(d, s.rate_bits, s.cap_height) for d, s in zip(ds, shapes)]
 
@@ -527,7 +537,7 @@ FRI_CFG = (4, 5, 4)   # arity 2^4, final polynomial 2^5 values, cap height 4 per
 FRI_EXT = 2           # challenges and layers in the quadratic extension (Plonky2's default)
 # DRAM traffic of one k_fri_combine launch on the 135 x 2^20 workload, from an
 # ncu capture of the same kernel.  Drop the entry when the kernel changes.
-FRI_COMBINE_TRAFFIC = {"fri_135x2_20": 9.690e9}
+FRI_COMBINE_TRAFFIC = {"fri_135x2_20": 9.657e9}
 
 
 def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
