@@ -184,21 +184,34 @@ struct Batch {
             fac.push_back(a);
             fbc.push_back(b);
         }
+        // Levels with at most kMerkleWarpMaxNodes nodes take the warp-per-node
+        // form (the latency of one compression sets their time); thread-per-node
+        // launches fold levels until a level is that small.
         fm.clear();
         mgroups.clear();
+        mwarp.clear();
         for (u32 lev0 = 0; lev0 < max_top;) {
             u64 nodes = 0;
             for (auto& j : tree)
                 if (j.log_N - j.h > lev0) nodes += (u64)1 << (j.log_N - lev0 - 1);
-            u32 nlev = nodes >= ((u64)1 << 17) ? 1 : 8;
+            const bool warp = nodes <= kMerkleWarpMaxNodes;
+            u32 nlev = 1;
+            if (warp) {
+                nlev = kMerkleWarpLevels;
+            } else if (nodes < ((u64)1 << 17)) {
+                nlev = 0;
+                for (u64 n = nodes; n > kMerkleWarpMaxNodes && nlev < 8; n >>= 1) nlev++;
+            }
             std::vector<u32> f(1, 0);
-            for (auto& j : tree) f.push_back(f.back() + merkle_items(j, lev0, t));
+            for (auto& j : tree) f.push_back(f.back() + (warp ? merkle_warp_items(j, lev0) : merkle_items(j, lev0, t)));
             fm.push_back(f);
             mgroups.push_back({lev0, nlev});
+            mwarp.push_back(warp);
             lev0 += nlev;
         }
     }
     std::vector<std::pair<u32, u32>> mgroups;  // (first level, levels) of each Merkle launch
+    std::vector<bool> mwarp;                   // warp-per-node form for that launch
     u32 h_threads = 0;                          // leaf-hash CTA size (0 = context default)
     bool leaves_ready = false;                  // level 0 of every tree is already written: no leaf hash
     // Column chunks whose inputs arrive by separate copies: stages A and B

@@ -16,6 +16,7 @@
 #include "gl.cuh"
 #include "internal.h"
 #include "poseidon.cuh"
+#include "poseidon_warp.cuh"
 
 namespace v3c {
 
@@ -206,6 +207,71 @@ cudaError_t launch_merkle(const TreeJob* d_jobs, StageList l, u32 lev0, u32 nlev
     }
     grid = (int)std::min<u32>((u32)grid, l.total);
     k_merkle<<<grid, t.m_threads, 0, s>>>(d_jobs, l, lev0, nlev);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- small levels
+
+u32 merkle_warp_items(const TreeJob& j, u32 lev0)
+{
+    u32 top = j.log_N - j.h;
+    if (top <= lev0) return 0;
+    u64 cnt = (u64)1 << (j.log_N - lev0 - 1);  // nodes at level lev0 + 1
+    return (u32)std::max<u64>(1, cnt / kMerkleWarps);
+}
+
+// Each CTA takes kMerkleWarps nodes of level lev0+1 (fewer at the top of a
+// tree); warp w computes node w, the warp sharing the permutation
+// (poseidon_warp.cuh), and the CTA keeps halving in shared memory.  Every
+// level is written to its place in the level-major tree, or to the cap.
+__global__ void __launch_bounds__(kMerkleWarps * 32) k_merkle_warp(const TreeJob* __restrict__ jobs, StageList L,
+                                                                   u32 lev0, u32 nlev)
+{
+    __shared__ pos::WarpRc s_rc;
+    __shared__ u64 s_dig[kMerkleWarps * 4];
+    pos::warp_rc_init(s_rc, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const u32 w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    u32 m[12];
+    pos::warp_mds_row(m, l);
+    for (u32 item = blockIdx.x; item < L.total; item += gridDim.x) {
+        const u32 jid = find_job_t(L.first, L.njobs, item);
+        const TreeJob& J = jobs[jid];
+        const u32 top = J.log_N - J.h;
+        const u64 cnt_out = (u64)1 << (J.log_N - lev0 - 1);
+        const u32 cnt1 = (u32)min((u64)kMerkleWarps, cnt_out);
+        const u64 base = (u64)(item - L.first[jid]) * kMerkleWarps;
+        u32 levels = min(nlev, top - lev0);
+        levels = min(levels, (u32)(__ffs(cnt1) - 1) + 1);
+        const u64* in = level_ptr(J, lev0);
+        for (u32 lv = 1; lv <= levels; lv++) {
+            const u32 cnt = cnt1 >> (lv - 1);
+            const bool act = w < cnt;  // warp-uniform
+            u64 x = 0;                 // lanes 0-7: the two child digests; 8-11: zero
+            if (act && l < 8) x = lv == 1 ? __ldg(in + (base + w) * 8 + l) : s_dig[8 * w + l];
+            if (act) x = pos::permute_warp(x, s_rc, m, l);
+            __syncthreads();  // every read of s_dig for this level is done
+            if (act && l < 4) {
+                const u64 d = gl::canon(x);
+                level_ptr(J, lev0 + lv)[((base >> (lv - 1)) + w) * 4 + l] = d;
+                s_dig[4 * w + l] = d;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_merkle_warp(const TreeJob* d_jobs, StageList l, u32 lev0, u32 nlev, int grid, cudaStream_t s)
+{
+    if (l.total == 0) return cudaSuccess;
+    if (grid <= 0) {
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_merkle_warp, kMerkleWarps * 32, 0);
+        if (e != cudaSuccess) return e;
+        grid = std::max(nb, 1) * num_sms();
+    }
+    grid = (int)std::min<u32>((u32)grid, l.total);
+    k_merkle_warp<<<grid, kMerkleWarps * 32, 0, s>>>(d_jobs, l, lev0, nlev);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,16 @@ cudaError_t launch_leaf_hash(const TreeJob* d_jobs, StageList l, const Tiles& t,
 u32 merkle_items(const TreeJob& j, u32 lev0, const Tiles& t);
 cudaError_t launch_merkle(const TreeJob* d_jobs, StageList l, u32 lev0, u32 nlev, const Tiles& t, int grid,
                           cudaStream_t s);
+// Warp-per-node form for small levels, where one compression's latency sets
+// the time of a level: one warp per compression, kMerkleWarps nodes of
+// level lev0+1 per CTA, up to kMerkleWarpLevels levels folded in shared
+// memory.  Used once a level has at most kMerkleWarpMaxNodes nodes (one CTA
+// of 1024 threads per SM, one wave).
+constexpr u32 kMerkleWarps = 32;
+constexpr u32 kMerkleWarpLevels = 6;
+constexpr u64 kMerkleWarpMaxNodes = 4096;
+u32 merkle_warp_items(const TreeJob& j, u32 lev0);
+cudaError_t launch_merkle_warp(const TreeJob* d_jobs, StageList l, u32 lev0, u32 nlev, int grid, cudaStream_t s);
 
 cudaError_t launch_validate(const u64* x, u64 count, u32* d_flag, cudaStream_t s);
 cudaError_t launch_int_peak(u64* out, int grid, int threads, u32 iters, cudaStream_t s);

@@ -23,6 +23,7 @@
 #include "gl.cuh"
 #include "internal.h"
 #include "poseidon.cuh"
+#include "poseidon_warp.cuh"
 
 namespace v3c {
 
@@ -110,95 +111,23 @@ __global__ void __launch_bounds__(128) k_snap_centroids(const u64* __restrict__ 
 // root_cb = Hash of the flattened codebooks.  The sponge is sequential
 // (count / 8 permutations, each on the previous state), so its time is the
 // latency of one permutation times their number.  One warp shares each
-// permutation: lane l < 12 holds state word s_l.  A round applies the S-box
-// (every lane in a full round, lane 0 in a partial one) and forms its MDS
-// row plus the next round's constant,
-//   s'_l = sum_j m[(j - l) mod 12] s_j + rc_(r+1)[l],
-// on 21/21/22-bit limbs: every lane splits its word once, each term is three
-// 32-bit shuffles and three 32-bit multiply-adds (no carries: the sums stay
-// below 2^32 since sum m < 2^9 and the constant limbs are below 2^22), and
-// the limb sums are folded once per round.  The constants' limbs sit in
-// shared memory, one 16-byte row per lane and round.  Words stay
-// non-canonical (in [0, 2^64), congruent mod p) until the digest.
-__constant__ u32 c_mds_row[12] = V3C_MDS_ROW_INIT;
-
-// Products for a latency-bound chain: the reduction written with compares
-// (gl::reduce128) has a shorter dependency chain than the carry-chain form.
-__device__ __forceinline__ u64 mul_lat(u64 a, u64 b) { return gl::reduce128(a * b, __umul64hi(a, b)); }
-
-// x^7 on non-canonical values (inputs and output in [0, 2^64)).
-__device__ __forceinline__ u64 sbox7_nc(u64 x)
-{
-    u64 x2 = mul_lat(x, x);
-    u64 x3 = mul_lat(x2, x);
-    u64 x4 = mul_lat(x2, x2);
-    return mul_lat(x3, x4);
-}
-
-__device__ __forceinline__ void limbs21(u64 v, u32& a, u32& b, u32& c)
-{
-    a = (u32)v & 0x1FFFFFu;
-    b = (u32)(v >> 21) & 0x1FFFFFu;
-    c = (u32)(v >> 42);
-}
-
-// Accumulates the MDS terms j in [J0, 12) of this lane's row from the
-// senders' limbs into two accumulators per limb (shorter chains).
-template <int J0>
-__device__ __forceinline__ void mds_terms(u32 a, u32 b, u32 c, const u32 (&m)[12], u32 (&A)[2], u32 (&B)[2],
-                                          u32 (&C)[2])
-{
-#pragma unroll
-    for (int j = J0; j < 12; j++) {
-        A[j & 1] += __shfl_sync(0xffffffffu, a, j) * m[j];
-        B[j & 1] += __shfl_sync(0xffffffffu, b, j) * m[j];
-        C[j & 1] += __shfl_sync(0xffffffffu, c, j) * m[j];
-    }
-}
-
+// permutation (poseidon_warp.cuh): lane l < 12 holds state word s_l.
 // With `same` non-null, *same == 0 means the codebooks equal the cached ones
 // (k_snap_cb_compare) and the cached digest is copied instead.
 __global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb, u32 count, u64* __restrict__ out,
                                                      const u64* __restrict__ same, const u64* __restrict__ cached)
 {
-    __shared__ uint4 s_rc[31][12];  // limbs (a, b, c) of rc_r[l]; row 30 is zero
+    __shared__ pos::WarpRc s_rc;
     const u32 l = threadIdx.x;
     if (same && *same == 0) {
         if (l < 4) out[l] = cached[l];
         return;
     }
-    for (u32 e = l; e < 31 * 12; e += 32) {
-        const u32 r = e / 12, i = e % 12;
-        const u64 v = r < 30 ? pos::c_rc[r][i] : 0;
-        s_rc[r][i] = make_uint4((u32)v & 0x1FFFFFu, (u32)(v >> 21) & 0x1FFFFFu, (u32)(v >> 42), 0);
-    }
+    pos::warp_rc_init(s_rc, l, 32);
     __syncwarp();
-    const bool own = l < 12;
-    const u32 li = own ? l : 0;
-    u32 m[12];  // m[j] = row[(j - l) mod 12]: this lane's MDS row
-#pragma unroll
-    for (int j = 0; j < 12; j++) m[j] = c_mds_row[(j + 12 - li) % 12];
-    u64 x = 0;  // s_l, non-canonical in [0, 2^64) between rounds
-    // One round; the accumulators start from the next round's constant limbs.
-    auto round = [&](int r, bool full) {
-        const uint4 k = s_rc[r + 1][li];
-        u32 A[2] = {own ? k.x : 0, 0}, B[2] = {own ? k.y : 0, 0}, C[2] = {own ? k.z : 0, 0};
-        u32 a, b, c;
-        if (full) {
-            limbs21(sbox7_nc(x), a, b, c);
-            mds_terms<0>(a, b, c, m, A, B, C);
-        } else {
-            // Terms j >= 1 use the pre-S-box words and overlap lane 0's S-box.
-            limbs21(x, a, b, c);
-            mds_terms<1>(a, b, c, m, A, B, C);
-            u32 ya, yb, yc;
-            limbs21(sbox7_nc(x), ya, yb, yc);
-            A[0] += __shfl_sync(0xffffffffu, ya, 0) * m[0];
-            B[0] += __shfl_sync(0xffffffffu, yb, 0) * m[0];
-            C[0] += __shfl_sync(0xffffffffu, yc, 0) * m[0];
-        }
-        x = pos::limb_fold21(A[0] + A[1], B[0] + B[1], C[0] + C[1]);
-    };
+    u32 m[12];
+    pos::warp_mds_row(m, l);
+    u64 x = 0;  // s_l, non-canonical in [0, 2^64) between permutations
     if (count <= 4) {
         if (l < count) x = __ldg(cb + l);
     } else {
@@ -208,13 +137,7 @@ __global__ void __launch_bounds__(32) k_snap_codebook(const u64* __restrict__ cb
             if (l < len) x = next;  // overwrite lanes 0 .. len-1
             if (st + 8 < count)     // prefetch the next chunk during the permutation
                 next = l < 8 && st + 8 + l < count ? __ldg(cb + st + 8 + l) : 0;
-            x = gl::add_nc_small(x, own ? pos::c_rc[0][li] : 0);  // round 0's constant; later ones ride the MDS
-#pragma unroll 1
-            for (int r = 0; r < 4; r++) round(r, true);
-#pragma unroll 1
-            for (int r = 4; r < 26; r++) round(r, false);
-#pragma unroll 1
-            for (int r = 26; r < 30; r++) round(r, true);
+            x = pos::permute_warp(x, s_rc, m, l);
         }
     }
     if (l < 4) out[l] = gl::canon(x);

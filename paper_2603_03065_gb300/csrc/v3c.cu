@@ -297,6 +297,7 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
         for (size_t g = 0; g < b.fm.size(); g++) {
             st = stage(4, [](const Batch& b, const Tiles& t, StageList l, const LdeJob*, const TreeJob* dt,
                              size_t g, cudaStream_t s) {
+                if (b.mwarp[g]) return launch_merkle_warp(dt, l, b.mgroups[g].first, b.mgroups[g].second, 0, s);
                 return launch_merkle(dt, l, b.mgroups[g].first, b.mgroups[g].second, t, 0, s);
             }, list(6 + g, b.fm[g], nt), g);
             if (st) return st;
