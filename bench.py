@@ -290,10 +290,19 @@ def run_v3c(args):
     pinned = torch.from_numpy(x.view(np.int64)).pin_memory()
     x_pinned = pinned.numpy().view(np.uint64)
 
+    host_ms = {"enqueue": 0.0, "cap_wait": 0.0, "release": 0.0}
+
     def step_e2e():
+        t_a = time.perf_counter()
         cid = ctx.commit([(x_pinned, s.rate_bits, s.cap_height)], stream=stream)[0]
+        t_b = time.perf_counter()
         cap = ctx.cap(cid)
+        t_c = time.perf_counter()
         ctx.release(cid)
+        t_d = time.perf_counter()
+        host_ms["enqueue"] += (t_b - t_a) * 1e3
+        host_ms["cap_wait"] += (t_c - t_b) * 1e3
+        host_ms["release"] += (t_d - t_c) * 1e3
         return cap
 
     step_e2e()
@@ -309,6 +318,8 @@ def run_v3c(args):
     barrier()
     e2e_clocks = ClockSampler(local_rank)
     e2e_clocks.start()
+    for k in host_ms:
+        host_ms[k] = 0.0
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step_e2e()
@@ -335,7 +346,8 @@ def run_v3c(args):
             "config": dict(workload_config(args.workload, s), autotune=bool(args.autotune)),
             "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(32 << s.cap_height), "ms_per_step": e2e_s * 1e3,
-                    "clocks": e2e_clk, "h2d_GBps_measured": h2d_gbs},
+                    "clocks": e2e_clk, "h2d_GBps_measured": h2d_gbs,
+                    "host_ms_per_step": {k: v / args.steps for k, v in host_ms.items()}},
             "gpu_launches": int(launches),
             "clocks": clk,
             "roofline": {"bound": "alu", "kernel": "k_leaf_hash", "achieved": achieved, "peak": peak,
