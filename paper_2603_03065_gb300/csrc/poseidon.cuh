@@ -17,7 +17,11 @@
 //   wide   each 32-bit half of a lane times the entry, a 32x32->64
 //          multiply-add into a 42-bit accumulator;
 //   limb   each lane in 22-bit limbs, so that every product and its
-//          12-term sum fit one 32-bit multiply-add (full-rate IMAD).
+//          12-term sum fit one 32-bit multiply-add (full-rate IMAD);
+//   split  limbs of 21, 21 and 22 bits through the block form of the
+//          circulant ([[A, B], [B, A]], two 6x6 products per limb), the two
+//          21-bit limbs through a second 3x3 block split (54 products per
+//          limb instead of 72): 180 32-bit multiply-adds per MDS.
 // Values inside the permutation are non-canonical in [0, 2^64).
 #pragma once
 #include "gl.cuh"
@@ -108,9 +112,9 @@ __device__ __forceinline__ u64 limb_fold3(u32 A, u32 B, u32 Cc)
     return r;
 }
 // The configuration the library's kernels use (fastest measured on GB300:
-// split MDS on 21-bit limbs, round constants merged into the MDS
-// accumulators, PTX carry-chain reduction, compiler 64x64 products, plain
-// round order).
+// split MDS, round constants merged into the MDS accumulators, PTX
+// carry-chain reduction, compiler 64x64 products, plain round order).  The
+// permutation is bound by the IMAD (FMA-heavy) pipe.
 typedef Cfg<MUL_INTRINSIC, MDS_SPLIT, false, false, false, true, false, true> Default;
 
 struct U128 {
