@@ -38,6 +38,7 @@ WORKLOADS = {
     "large_135x2_20": synth.LARGE_135x2_20,
     "trace_135x2_16": synth.TRACE_135x2_16,
     "plain_8x2_10": synth.PLAIN_8x2_10,
+    "profile_8x2_20": synth.PROFILE_8x2_20,  # small capture case with the large commit's stage shapes
 }
 # Algorithmic work per Poseidon permutation in 32x32->64 wide-multiply units
 # (minimal exact form: S-boxes 1888, full-round small MDS 2304, sparse

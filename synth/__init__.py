@@ -162,6 +162,8 @@ class Shape:
 PLAIN_8x2_10 = Shape(c=8, log_n=10, rate_bits=3, cap_height=0, seed=0, mix="uniform")
 TRACE_135x2_16 = Shape(c=135, log_n=16, rate_bits=3, cap_height=4, seed=0)
 LARGE_135x2_20 = Shape(c=135, log_n=20, rate_bits=3, cap_height=4, seed=0)
+# Profiling case: the per-CTA shapes of the 135 x 2^20 commit (n1 = n2 = 2^10) on 8 columns.
+PROFILE_8x2_20 = Shape(c=8, log_n=20, rate_bits=3, cap_height=4, seed=0)
 
 
 def uneven_batches(seed: int = 3, count: int = 64) -> list[Shape]:
