@@ -95,6 +95,19 @@ __host__ __device__ __forceinline__ u64 sub(u64 a, u64 b)
     return d;
 }
 
+// The 128-bit reduction for code that also runs on the host: the carry-chain
+// form on the device (it moves part of the work off the integer ALU pipe),
+// the compare form on the host.  Both return a value below 2^64 congruent
+// to lo + 2^64 hi.
+__host__ __device__ __forceinline__ u64 reduce_any(u64 lo, u64 hi)
+{
+#ifdef __CUDA_ARCH__
+    return reduce128_ptx(lo, hi);
+#else
+    return reduce128(lo, hi);
+#endif
+}
+
 // x 2^e mod p for canonical x and 0 <= e < 96, canonical result; e is a
 // constant wherever this is inlined into unrolled code, so only one branch
 // remains.  With 2^64 = 2^32 - 1 and 2^128 = -2^32 (mod p):
@@ -114,11 +127,11 @@ __host__ __device__ __forceinline__ u64 mul_pow2(u64 x, u32 e)
         if (r < t) r += EPS;    // carry: r + 2^64 = r + EPS, and r < t here
         return canon(r);
     }
-    if (e < 64) return canon(reduce128(x << e, x >> (64 - e)));
+    if (e < 64) return canon(reduce_any(x << e, x >> (64 - e)));
     const u32 f = e - 64;
     const u64 yl = f ? x << f : x;
     const u64 yh = f ? x >> (64 - f) : 0;
-    return sub(canon(reduce128(0, yl)), yh << 32);
+    return sub(canon(reduce_any(0, yl)), yh << 32);
 }
 
 // a in [0, 2^64), k canonical: a + k mod p as a value in [0, 2^64).
