@@ -7,10 +7,12 @@ object) followed by its release.  The default workload is the large commit:
 135 trace columns x 2^20 rows, rate_bits 3 (2^23 LDE rows, 9.06 GB
 resident), cap height 4.  Inputs are resident in HBM when the timed region
 starts; every buffer is larger than L2 (1.13 GB in, 9.06 GB LDE), so no
-flush is needed between steps.
+flush is needed between steps.  A workload whose commit fits in L2 is timed
+step by step, each after an untimed write of a 256 MB buffer.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
-reference arm of this tier) on a bounded sample of the same workload.
+reference arm of this tier) on a bounded sample of the same workload, or on
+the whole workload when it is no larger than that sample.
 Under torchrun each rank commits its own batch of the same shape on its
 own GPU (independent problems: weak scaling, no data-path collective).
 """
@@ -139,20 +141,34 @@ class ClockSampler:
                 "power_w_median": statistics.median(pw) if pw else None}
 
 
-def cpu_baseline(steps: int = 1) -> dict:
+def cpu_baseline(steps: int = 1, shape=None) -> dict:
+    """The oracle on the host cores.  A workload no larger than the bounded
+    sample is timed whole (and on one thread as well); larger ones on the
+    135 x 2^14 sample of the same column mix."""
     import oracle
 
-    s = CPU_SAMPLE
+    whole = shape is not None and shape.lde_elems() <= CPU_SAMPLE.lde_elems()
+    s = shape if whole else CPU_SAMPLE
     x = s.inputs()
+
+    def time_commit(threads):
+        oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)  # warm (constants, pages)
+        n, t0 = 0, time.perf_counter()
+        while n < steps or time.perf_counter() - t0 < (0.5 if whole else 0.0):
+            oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)
+            n += 1
+        return (time.perf_counter() - t0) / n
+
     threads = oracle.default_threads()
-    oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)  # warm (constants, pages)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)
-    dt = (time.perf_counter() - t0) / steps
-    return {"value": s.lde_elems() / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
-            "sample": f"full oracle commit of {s.c} columns x 2^{s.log_n} rows (same column mix), "
-                      f"rate_bits {s.rate_bits}, cap height {s.cap_height}; {dt:.2f} s per commit"}
+    dt = time_commit(threads)
+    what = "the whole workload" if whole else "a bounded sample"
+    out = {"value": s.lde_elems() / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
+           "sample": f"{what}: full oracle commit of {s.c} columns x 2^{s.log_n} rows (same column mix), "
+                     f"rate_bits {s.rate_bits}, cap height {s.cap_height}; {dt * 1e3:.2f} ms per commit"}
+    if whole:
+        dt1 = time_commit(1)
+        out["single_core"] = {"value": s.lde_elems() / dt1 / 1e9, "unit": "Gelem/s", "ms_per_commit": dt1 * 1e3}
+    return out
 
 
 def run_reference(args):
@@ -165,7 +181,9 @@ def run_reference(args):
         return run_reference_other(args)
     import oracle
 
-    s = CPU_SAMPLE
+    w = WORKLOADS.get(args.workload, synth.LARGE_135x2_20)
+    whole = w.lde_elems() <= CPU_SAMPLE.lde_elems()  # small workloads are timed whole
+    s = w if whole else CPU_SAMPLE
     x = s.inputs()
     threads = oracle.default_threads()
     for _ in range(args.warmup):
@@ -175,15 +193,15 @@ def run_reference(args):
         oracle.commit(x, s.rate_bits, s.cap_height, threads=threads)
     dt = (time.perf_counter() - t0) / args.steps
     value = s.lde_elems() / dt / 1e9
-    w = WORKLOADS.get(args.workload, synth.LARGE_135x2_20)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config(args.workload, w),
         "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "Gelem/s",
-                         "sample": f"oracle commit of {s.c} x 2^{s.log_n} rows per step (bounded sample of the "
-                                   f"{args.workload} workload's column mix)"},
+                         "sample": f"oracle commit of {s.c} x 2^{s.log_n} rows per step ("
+                                   + ("the whole workload)" if whole else
+                                      f"bounded sample of the {args.workload} workload's column mix)")},
         "e2e": {"value": value, "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -255,6 +273,14 @@ def run_v3c(args):
         cid = ctx.commit([(d_x, s.rate_bits, s.cap_height)], stream=stream)[0]
         ctx.release(cid)
 
+    # A commit that fits in L2 (129 MB) is timed step by step, each after an
+    # untimed write of a 256 MB buffer that evicts it.
+    small = s.lde_elems() * 8 <= 129e6
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if small else None
+
+    def flush():
+        flush_buf.fill_(1)  # on the current stream, which the commits use
+
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
@@ -271,16 +297,28 @@ def run_v3c(args):
     clocks.start()
     barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
+    pairs = []
+    if small:
+        for _ in range(args.steps):
+            flush()
+            ea = torch.cuda.Event(enable_timing=True)
+            eb = torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            step()
+            eb.record(stream)
+            pairs.append((ea, eb))
+    else:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        pairs.append((e0, e1))
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = sum(a.elapsed_time(b) for a, b in pairs) / args.steps
     launches = ctx.kernel_launches() - l0
     stats = ctx.stage_stats(reset=True)
     ms = max_over_ranks(ms)
@@ -321,11 +359,16 @@ def run_v3c(args):
     e2e_clocks.start()
     for k in host_ms:
         host_ms[k] = 0.0
-    t0 = time.perf_counter()
+    e2e_total = 0.0
     for _ in range(args.steps):
-        step_e2e()
+        if small:
+            flush()
+            torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_e2e()  # ends with the cap read, which waits for the commit
+        e2e_total += time.perf_counter() - t0
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e_s = max_over_ranks(e2e_total / args.steps)
     e2e_clk = e2e_clocks.stop()
     e2e_value = world * s.lde_elems() / e2e_s / 1e9
 
@@ -357,7 +400,7 @@ def run_v3c(args):
             "stages_ms_per_launch": stage_ms,
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(shape=s)
         if args.int_peak:
             rate, _ = ctx.int_peak(10)
             line["int_peak_measured"] = {"value": rate / 1e12, "unit": "T wide-mul/s",
