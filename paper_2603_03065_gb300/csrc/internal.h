@@ -24,10 +24,10 @@ struct Plan {
     const u64* twa;      // [n1][n2]: w_n^-(k1*i2)                     (n1 > 1)
     const u64* scale;    // [n1][n2]: 7^(k1 + n1*bitrev_n2(t)) / n, by position t
     const u64* pw_N;     // [3][512]: w_N^(j * 2^(9 level))              (n1 > 1)
-    const u64* rinv_n1;  // [n1/2]:   w_n1^-j
+    const u64* rinv_n1;  // [n1]:     w_n1^-j
     const u64* rinv_n2;  // [n2/2]:   w_n2^-j
     const u64* rfwd_M;   // [M/2]:    w_M^j
-    const u64* rfwd_n1;  // [n1/2]:   w_n1^j
+    const u64* rfwd_n1;  // [n1]:     w_n1^j
 };
 
 // One LDE job: c columns of one shape.

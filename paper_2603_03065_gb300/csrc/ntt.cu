@@ -35,6 +35,7 @@ void plan_split(u32 log_n, u32 r, u32& log_n1, u32& log_n2)
 }
 
 static inline size_t half_or_one(u32 log_l) { return log_l ? (size_t)1 << (log_l - 1) : 1; }
+static inline size_t full_len(u32 log_l) { return (size_t)1 << log_l; }
 
 // Powers of w_N in three 512-entry tables: w_N^e for any e < 2^27 is
 // pw[e mod 2^9] * pw[512 + (e >> 9) mod 2^9] * pw[1024 + (e >> 18)].
@@ -47,7 +48,7 @@ size_t plan_table_words(u32 log_n, u32 r)
     size_t n = (size_t)1 << log_n;
     size_t w = n;                          // scale
     if (l1) w += n + kPowWords;            // twa, pw_N
-    w += half_or_one(l1) * 2 + half_or_one(l2) + half_or_one(l2 + r);
+    w += full_len(l1) * 2 + half_or_one(l2) + half_or_one(l2 + r);
     return w;
 }
 
@@ -130,20 +131,20 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
     a.pw_N = l1 ? cur : nullptr;
     cur += l1 ? kPowWords : 0;
     a.rinv_n1 = cur;
-    cur += half_or_one(l1);
+    cur += full_len(l1);
     a.rinv_n2 = cur;
     cur += half_or_one(l2);
     a.rfwd_M = cur;
     cur += half_or_one(p.log_M);
     a.rfwd_n1 = cur;
-    cur += half_or_one(l1);
+    cur += full_len(l1);
     a.seg[0] = l1 ? n : 0;
     a.seg[1] = a.seg[0] + n;
     a.seg[2] = a.seg[1] + (l1 ? kPowWords : 0);
-    a.seg[3] = a.seg[2] + half_or_one(l1);
+    a.seg[3] = a.seg[2] + full_len(l1);
     a.seg[4] = a.seg[3] + half_or_one(l2);
     a.seg[5] = a.seg[4] + half_or_one(p.log_M);
-    a.seg[6] = a.seg[5] + half_or_one(l1);
+    a.seg[6] = a.seg[5] + full_len(l1);
     a.w_n_inv = hinv(hroot(p.log_n));
     a.w_N = hroot(p.log_N);
     a.w_n1_inv = hinv(hroot(l1));
@@ -280,16 +281,19 @@ __device__ __forceinline__ void small_dit(u64 (&v)[1 << K])
     }
 }
 
-// v * w_L^e for 0 <= e < L from the half table (w_L^(e + L/2) = -w_L^e).
+// v * w_L^e for 0 <= e < L.  FULL: tw holds all L powers; otherwise the
+// half table (w_L^(e + L/2) = -w_L^e).
+template <bool FULL>
 __device__ __forceinline__ u64 mul_tw(u64 v, const u64* tw, u32 e, u32 logL)
 {
+    if (FULL) return gl::mul(v, tw[sw(e)]);
     const u32 half = (1u << logL) >> 1;
     u64 t = tw[sw(half ? e & (half - 1) : 0)];
     if (half && (e & half)) t = gl::P - t;  // roots of unity are nonzero
     return gl::mul(v, t);
 }
 
-template <int K, bool INV>
+template <int K, bool INV, bool FULL>
 __device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
 {
     const u32 lst = logL - s0 - K;  // log2 of the stride
@@ -306,7 +310,7 @@ __device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const 
         small_dif<K, INV>(v);
         if (lst) {
 #pragma unroll
-            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw(v[j], tw, (lo * (u32)bitrev_c(j, K)) << s0, logL);
+            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw<FULL>(v[j], tw, (lo * (u32)bitrev_c(j, K)) << s0, logL);
         }
 #pragma unroll
         for (int j = 0; j < (1 << K); j++) a[sw(i0 + ((u32)j << lst))] = v[j];
@@ -314,7 +318,7 @@ __device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const 
     __syncthreads();
 }
 
-template <int K, bool INV>
+template <int K, bool INV, bool FULL>
 __device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
 {
     const u32 G = B << (logL - K);
@@ -330,7 +334,7 @@ __device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const 
         if (s0) {
             const u32 sh = logL - s0 - K;
 #pragma unroll
-            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw(v[j], tw, (lo * (u32)bitrev_c(j, K)) << sh, logL);
+            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw<FULL>(v[j], tw, (lo * (u32)bitrev_c(j, K)) << sh, logL);
         }
         small_dit<K, INV>(v);
 #pragma unroll
@@ -350,17 +354,18 @@ __device__ __forceinline__ u32 pass_k(u32 B, u32 logL, u32 kcap)
 }
 
 // INV: tw holds w_L^-i and the in-register DFTs use the inverse roots.
-template <bool INV>
+// FULL: tw holds all L powers (else the first L/2).
+template <bool INV, bool FULL>
 __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, u32 kcap)
 {
     const u32 kmax = pass_k(B, logL, kcap);
     for (u32 s = 0; s < logL;) {
         u32 k = min(kmax, logL - s);
         switch (k) {
-        case 4: dif_pass<4, INV>(a, B, logL, s, tw); break;
-        case 3: dif_pass<3, INV>(a, B, logL, s, tw); break;
-        case 2: dif_pass<2, INV>(a, B, logL, s, tw); break;
-        default: dif_pass<1, INV>(a, B, logL, s, tw); break;
+        case 4: dif_pass<4, INV, FULL>(a, B, logL, s, tw); break;
+        case 3: dif_pass<3, INV, FULL>(a, B, logL, s, tw); break;
+        case 2: dif_pass<2, INV, FULL>(a, B, logL, s, tw); break;
+        default: dif_pass<1, INV, FULL>(a, B, logL, s, tw); break;
         }
         s += k;
     }
@@ -374,11 +379,11 @@ __device__ __forceinline__ void dft_dit(u64* a, u32 B, u32 logL, const u64* tw, 
     for (u32 s = first; s < logL;) {
         u32 k = min(kmax, logL - s);
         switch (k) {
-        case 5: dit_pass<5, INV>(a, B, logL, s, tw); break;
-        case 4: dit_pass<4, INV>(a, B, logL, s, tw); break;
-        case 3: dit_pass<3, INV>(a, B, logL, s, tw); break;
-        case 2: dit_pass<2, INV>(a, B, logL, s, tw); break;
-        default: dit_pass<1, INV>(a, B, logL, s, tw); break;
+        case 5: dit_pass<5, INV, false>(a, B, logL, s, tw); break;
+        case 4: dit_pass<4, INV, false>(a, B, logL, s, tw); break;
+        case 3: dit_pass<3, INV, false>(a, B, logL, s, tw); break;
+        case 2: dit_pass<2, INV, false>(a, B, logL, s, tw); break;
+        default: dit_pass<1, INV, false>(a, B, logL, s, tw); break;
         }
         s += k;
     }
@@ -420,7 +425,7 @@ size_t stage_a_smem(const LdeJob& j, const Tiles&)
 {
     if (!j.plan.log_n1) return 0;
     size_t n1 = (size_t)1 << j.plan.log_n1;
-    return (j.a_cols * n1 + n1 / 2) * sizeof(u64);
+    return (j.a_cols * n1 + n1) * sizeof(u64);
 }
 
 __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs, StageList L)
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
         u64* data = sm;
         u64* tw = sm + ((size_t)T2 << l1);
         if (jid != cur_job) {  // a persistent CTA keeps the tables while the job is the same
-            for (u32 e = threadIdx.x; e < n1 / 2; e += blockDim.x) tw[sw(e)] = J.plan.rinv_n1[e];
+            for (u32 e = threadIdx.x; e < n1; e += blockDim.x) tw[sw(e)] = J.plan.rinv_n1[e];
             cur_job = jid;
         }
         for (u32 e = threadIdx.x; e < (T2 << l1); e += blockDim.x) {
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs
         }
         cp_async_wait_all();
         __syncthreads();
-        dft_dif<true>(data, T2, l1, tw, J.kcap);
+        dft_dif<true, true>(data, T2, l1, tw, J.kcap);
         u64* Y = J.Y + ((size_t)col << J.plan.log_n);
         for (u32 e = threadIdx.x; e < (T2 << l1); e += blockDim.x) {
             u32 u = e & (T2 - 1), t = e >> lT2;
@@ -502,7 +507,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
                             : J.x + ((size_t)col << J.plan.log_n);
         for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[sw(e)] = __ldcs(src + e);
         __syncthreads();
-        dft_dif<true>(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
+        dft_dif<true, false>(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
         const u64* sc = J.plan.scale + ((size_t)k1 << l2);
         // Scale by 7^j / n and spread for the zero-padded size-M transform.
         // In bit-reversed order over log M bits, coefficient k2 sits at
@@ -559,7 +564,7 @@ size_t stage_c_smem(const LdeJob& j, const Tiles&)
 {
     if (!j.plan.log_n1) return 0;
     size_t n1 = (size_t)1 << j.plan.log_n1;
-    return (kStageCCols * j.c_qc * n1 + n1 / 2) * sizeof(u64);
+    return (kStageCCols * j.c_qc * n1 + n1) * sizeof(u64);
 }
 
 __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
@@ -579,9 +584,9 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
         const u32 q0 = qt << lQ;
         const u32 qb = q0 >> lQz, qoff = q0 & (Qz - 1);
         u64* data = sm;                                   // [4][Q][n1]
-        u64* tw = sm + ((size_t)kStageCCols * Q << l1);   // [n1/2]
+        u64* tw = sm + ((size_t)kStageCCols * Q << l1);   // [n1]
         if (jid != cur_job) {  // a persistent CTA keeps the tables while the job is the same
-            for (u32 e = threadIdx.x; e < n1 / 2; e += blockDim.x) tw[sw(e)] = J.plan.rfwd_n1[e];
+            for (u32 e = threadIdx.x; e < n1; e += blockDim.x) tw[sw(e)] = J.plan.rfwd_n1[e];
             cur_job = jid;
         }
         // Block qb of each column is one contiguous run of n1*Qz words, [k1][v];
@@ -600,7 +605,7 @@ __global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs
         }
         cp_async_wait_all();
         __syncthreads();
-        dft_dif<false>(data, kStageCCols * Q, l1, tw, J.kcap);
+        dft_dif<false, true>(data, kStageCCols * Q, l1, tw, J.kcap);
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
