@@ -359,6 +359,7 @@ def run_v3c(args):
     e2e_clocks.start()
     for k in host_ms:
         host_ms[k] = 0.0
+    ctx.stage_stats(reset=True)
     e2e_total = 0.0
     for _ in range(args.steps):
         if small:
@@ -370,6 +371,7 @@ def run_v3c(args):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(e2e_total / args.steps)
     e2e_clk = e2e_clocks.stop()
+    e2e_stats = ctx.stage_stats(reset=True)
     e2e_value = world * s.lde_elems() / e2e_s / 1e9
 
     # roofline of the dominant kernel (leaf hash), timed by events on its stream
@@ -391,7 +393,8 @@ def run_v3c(args):
             "e2e": {"value": e2e_value, "unit": "Gelem/s", "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(32 << s.cap_height), "ms_per_step": e2e_s * 1e3,
                     "clocks": e2e_clk, "h2d_GBps_measured": h2d_gbs,
-                    "host_ms_per_step": {k: v / args.steps for k, v in host_ms.items()}},
+                    "host_ms_per_step": {k: v / args.steps for k, v in host_ms.items()},
+                    "stages_ms_per_step": {k: v[0] / args.steps for k, v in e2e_stats.items() if v[1]}},
             "gpu_launches": int(launches),
             "clocks": clk,
             "roofline": {"bound": "alu", "kernel": "k_leaf_hash", "achieved": achieved, "peak": peak,
