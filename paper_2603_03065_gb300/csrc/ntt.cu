@@ -293,9 +293,26 @@ __device__ __forceinline__ u64 mul_tw(u64 v, const u64* tw, u32 e, u32 logL)
     return gl::mul(v, t);
 }
 
-template <int K, bool INV, bool FULL>
-__device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
+// Shared-memory word of element j of a pass whose first element is i0 and
+// whose stride is 2^st: sw(i0 + j 2^st) = sw(i0) ^ sw(j 2^st), because i0 has
+// no bit in [st, st + K) and sw is linear over XOR.  For st >= 8 the second
+// term is j 2^st and shares no bit with sw(i0), so the XOR is an addition
+// (an immediate offset once st is a compile-time constant).
+template <int LOGL>
+__device__ __forceinline__ u32 pass_word(u32 i0, u32 base, u32 j, u32 st)
 {
+    if (!LOGL) return sw(i0 + (j << st));  // run-time stride: the plain form
+    return st >= 8 ? base + (j << st) : base ^ sw(j << st);
+}
+
+// LOGL > 0: the transform size and the pass's first stage are compile-time
+// constants (the passes of the common plans), so strides, word offsets and
+// twiddle shifts fold; LOGL = 0 takes them at run time.
+template <int K, bool INV, bool FULL, int LOGL = 0, int S0 = 0>
+__device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL_rt, u32 s0_rt, const u64* tw)
+{
+    const u32 logL = LOGL ? (u32)LOGL : logL_rt;
+    const u32 s0 = LOGL ? (u32)S0 : s0_rt;
     const u32 lst = logL - s0 - K;  // log2 of the stride
     const u32 G = B << (logL - K);
     for (u32 g = threadIdx.x; g < G; g += blockDim.x) {
@@ -304,23 +321,26 @@ __device__ __forceinline__ void dif_pass(u64* a, u32 B, u32 logL, u32 s0, const 
         u32 lo = gg & ((1u << lst) - 1);
         u32 hi = gg >> lst;
         const u32 i0 = (tr << logL) + (hi << (lst + K)) + lo;
+        const u32 base = sw(i0);
         u64 v[1 << K];
 #pragma unroll
-        for (int j = 0; j < (1 << K); j++) v[j] = a[sw(i0 + ((u32)j << lst))];
+        for (int j = 0; j < (1 << K); j++) v[j] = a[pass_word<LOGL>(i0, base, (u32)j, lst)];
         small_dif<K, INV>(v);
         if (lst) {
 #pragma unroll
-            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw<FULL>(v[j], tw, (lo * (u32)bitrev_c(j, K)) << s0, logL);
+            for (int j = 1; j < (1 << K); j++) v[j] = mul_tw<FULL>(v[j], tw, (lo * (u32)bitrev_c(j, K)) << s0_rt, logL);
         }
 #pragma unroll
-        for (int j = 0; j < (1 << K); j++) a[sw(i0 + ((u32)j << lst))] = v[j];
+        for (int j = 0; j < (1 << K); j++) a[pass_word<LOGL>(i0, base, (u32)j, lst)] = v[j];
     }
     __syncthreads();
 }
 
-template <int K, bool INV, bool FULL>
-__device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const u64* tw)
+template <int K, bool INV, bool FULL, int LOGL = 0, int S0 = 0>
+__device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL_rt, u32 s0_rt, const u64* tw)
 {
+    const u32 logL = LOGL ? (u32)LOGL : logL_rt;
+    const u32 s0 = LOGL ? (u32)S0 : s0_rt;
     const u32 G = B << (logL - K);
     for (u32 g = threadIdx.x; g < G; g += blockDim.x) {
         u32 tr = g >> (logL - K);
@@ -328,17 +348,18 @@ __device__ __forceinline__ void dit_pass(u64* a, u32 B, u32 logL, u32 s0, const 
         u32 lo = gg & ((1u << s0) - 1);
         u32 hi = gg >> s0;
         const u32 i0 = (tr << logL) + (hi << (s0 + K)) + lo;
+        const u32 base = sw(i0);
         u64 v[1 << K];
 #pragma unroll
-        for (int j = 0; j < (1 << K); j++) v[j] = a[sw(i0 + ((u32)j << s0))];
+        for (int j = 0; j < (1 << K); j++) v[j] = a[pass_word<LOGL>(i0, base, (u32)j, s0)];
         if (s0) {
-            const u32 sh = logL - s0 - K;
+            const u32 sh = logL_rt - s0_rt - K;
 #pragma unroll
             for (int j = 1; j < (1 << K); j++) v[j] = mul_tw<FULL>(v[j], tw, (lo * (u32)bitrev_c(j, K)) << sh, logL);
         }
         small_dit<K, INV>(v);
 #pragma unroll
-        for (int j = 0; j < (1 << K); j++) a[sw(i0 + ((u32)j << s0))] = v[j];
+        for (int j = 0; j < (1 << K); j++) a[pass_word<LOGL>(i0, base, (u32)j, s0)] = v[j];
     }
     __syncthreads();
 }
@@ -361,7 +382,15 @@ __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, 
     const u32 kmax = pass_k(B, logL, kcap);
     for (u32 s = 0; s < logL;) {
         u32 k = min(kmax, logL - s);
-        switch (k) {
+        // 1024-point transforms (n1 = n2 = 2^10 plans) in radix 16 or 4.
+        if (logL == 10 && k == 4 && s == 0) dif_pass<4, INV, FULL, 10, 0>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 4 && s == 4) dif_pass<4, INV, FULL, 10, 4>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 2 && s == 8) dif_pass<2, INV, FULL, 10, 8>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 2 && s == 0) dif_pass<2, INV, FULL, 10, 0>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 2 && s == 2) dif_pass<2, INV, FULL, 10, 2>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 2 && s == 4) dif_pass<2, INV, FULL, 10, 4>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 2 && s == 6) dif_pass<2, INV, FULL, 10, 6>(a, B, logL, s, tw);
+        else switch (k) {
         case 4: dif_pass<4, INV, FULL>(a, B, logL, s, tw); break;
         case 3: dif_pass<3, INV, FULL>(a, B, logL, s, tw); break;
         case 2: dif_pass<2, INV, FULL>(a, B, logL, s, tw); break;
@@ -378,7 +407,10 @@ __device__ __forceinline__ void dft_dit(u64* a, u32 B, u32 logL, const u64* tw, 
     const u32 kmax = pass_k(B, logL, kcap);
     for (u32 s = first; s < logL;) {
         u32 k = min(kmax, logL - s);
-        switch (k) {
+        // The 8192-point forward transform of 2^10 x 2^3 plans in radix 32.
+        if (logL == 13 && k == 5 && s == 3) dit_pass<5, INV, false, 13, 3>(a, B, logL, s, tw);
+        else if (logL == 13 && k == 5 && s == 8) dit_pass<5, INV, false, 13, 8>(a, B, logL, s, tw);
+        else switch (k) {
         case 5: dit_pass<5, INV, false>(a, B, logL, s, tw); break;
         case 4: dit_pass<4, INV, false>(a, B, logL, s, tw); break;
         case 3: dit_pass<3, INV, false>(a, B, logL, s, tw); break;
@@ -428,7 +460,7 @@ size_t stage_a_smem(const LdeJob& j, const Tiles&)
     return (j.a_cols * n1 + n1) * sizeof(u64);
 }
 
-__global__ void __launch_bounds__(256) k_stage_a(const LdeJob* __restrict__ jobs, StageList L)
+__global__ void __launch_bounds__(256, 3) k_stage_a(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
     u32 cur_job = 0xFFFFFFFFu;
@@ -567,7 +599,7 @@ size_t stage_c_smem(const LdeJob& j, const Tiles&)
     return (kStageCCols * j.c_qc * n1 + n1) * sizeof(u64);
 }
 
-__global__ void __launch_bounds__(256) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
+__global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
     u32 cur_job = 0xFFFFFFFFu;
