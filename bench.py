@@ -141,14 +141,25 @@ class ClockSampler:
                 "power_w_median": statistics.median(pw) if pw else None}
 
 
+def cpu_sample(w):
+    """The oracle's shape for workload w: w itself when it is no larger than
+    CPU_SAMPLE, else w's columns, mix, rate and cap height on fewer rows (the
+    largest power of two within CPU_SAMPLE's element count)."""
+    if w.lde_elems() <= CPU_SAMPLE.lde_elems():
+        return w, True
+    budget = CPU_SAMPLE.c << CPU_SAMPLE.log_n
+    log_n = max(1, min(w.log_n, (budget // w.c).bit_length() - 1))
+    cap = min(w.cap_height, log_n + w.rate_bits)
+    return synth.Shape(c=w.c, log_n=log_n, rate_bits=w.rate_bits, cap_height=cap, seed=w.seed, mix=w.mix), False
+
+
 def cpu_baseline(steps: int = 1, shape=None) -> dict:
     """The oracle on the host cores.  A workload no larger than the bounded
     sample is timed whole (and on one thread as well); larger ones on the
-    135 x 2^14 sample of the same column mix."""
+    same columns and mix over fewer rows (cpu_sample)."""
     import oracle
 
-    whole = shape is not None and shape.lde_elems() <= CPU_SAMPLE.lde_elems()
-    s = shape if whole else CPU_SAMPLE
+    s, whole = cpu_sample(shape if shape is not None else synth.LARGE_135x2_20)
     x = s.inputs()
 
     def time_commit(threads):
@@ -182,8 +193,7 @@ def run_reference(args):
     import oracle
 
     w = WORKLOADS.get(args.workload, synth.LARGE_135x2_20)
-    whole = w.lde_elems() <= CPU_SAMPLE.lde_elems()  # small workloads are timed whole
-    s = w if whole else CPU_SAMPLE
+    s, whole = cpu_sample(w)  # small workloads are timed whole
     x = s.inputs()
     threads = oracle.default_threads()
     for _ in range(args.warmup):
