@@ -8,8 +8,10 @@
 // contraction, so it runs on the integer pipes.  One thread owns one 12-lane
 // state in registers (poseidon.cuh).  The leaf kernel reads each LDE row
 // once, in 16-byte loads.  Large tree levels get one launch each with one
-// compression per thread.  The last levels of a tree are folded inside one
-// CTA in shared memory.
+// compression per thread; middle levels are folded several per CTA in
+// shared memory.  Levels of at most a few thousand nodes, whose time is the
+// latency of one compression, take one warp per compression
+// (poseidon_warp.cuh) and fold six levels per CTA.
 #include <cuda_runtime.h>
 #include <algorithm>
 
