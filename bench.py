@@ -412,6 +412,10 @@ def run_v3c(args):
                          "work_per_launch": W_PER_PERM * perms_leaf, "ms_per_launch": leaf_ms_per},
             "stages_ms_per_launch": stage_ms,
         }
+        try:  # the whole path against its roofline (reported only; never fails the line)
+            line["path_roofline"] = path_roofline(s, ms, float(measured_peaks().get("hbm_gbs") or 6789.0))
+        except Exception as e:  # pragma: no cover
+            line["path_roofline"] = {"error": str(e)}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(shape=s)
         if args.int_peak:
@@ -980,6 +984,24 @@ def run_seteq(args):
     print(json.dumps(line))
     ctx.close()
     return 0
+
+
+def path_roofline(s, ms: float, hbm_gbs: float) -> dict:
+    """T_roof = max(bytes_alg / HBM, W_alg / R_int) for one commit of shape s
+    against the measured step time ms.  W_alg: 6792 wide multiplies per
+    permutation (leaves and nodes) plus 4 per NTT product, the products being
+    c [(n/2) log n + n + 2^r ((n/2) log n + n)] (inverse transform, coset
+    scale, 2^r coset transforms).  bytes_alg: the input read, the LDE written
+    and read back by the leaf hash, the leaf digests written."""
+    n, N = 1 << s.log_n, 1 << s.log_N
+    ntt_muls = s.c * ((n // 2) * s.log_n + n + (1 << s.rate_bits) * ((n // 2) * s.log_n + n))
+    w_alg = W_PER_PERM * s.perms() + W_PER_NTT_MUL * ntt_muls
+    bytes_alg = 8 * (s.c * n + 2 * s.c * N + 4 * N)
+    r_int = SMS * WIDE_MUL_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    t_int, t_hbm = w_alg / r_int * 1e3, bytes_alg / (hbm_gbs * 1e9) * 1e3
+    t_roof = max(t_int, t_hbm)
+    return {"T_roof_ms": t_roof, "T_ms": ms, "fraction": t_roof / ms, "bound": "alu" if t_int >= t_hbm else "hbm",
+            "W_alg": w_alg, "bytes_alg": bytes_alg}
 
 
 def measured_peaks() -> dict:
