@@ -5,6 +5,17 @@ kernels of ``libv3c.so``, and importing this module fails loudly if the
 library has not been built (``python -m paper_2603_03065_gb300.build``).  PyTorch
 provides device memory and streams.  Field elements are carried in int64
 tensors that hold the uint64 bit patterns.
+
+Example (x: canonical uint64 numpy array [c][n], n a power of two)::
+
+    import paper_2603_03065_gb300 as v3c
+    with v3c.Context(0) as ctx:
+        cid = ctx.commit([(v3c.to_device_u64(x), 3, 4)])[0]  # rate_bits 3, cap height 4
+        cap = ctx.cap(cid)                                   # [16][4] digests
+        rows, paths = ctx.open_batch(cid, [0, 7], x.shape[0])
+        fid = ctx.fri_begin([cid], alpha, 4, 5, 4, betas=betas)
+        ...
+        ctx.release(cid)
 """
 from __future__ import annotations
 
