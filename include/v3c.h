@@ -139,12 +139,14 @@ typedef struct {
 /* Batched commit (many uneven shapes in one launch per stage).  For each desc
  * it allocates a resident object that holds the LDE [N][ld] (ld = c rounded
  * up to even) and the tree, and enqueues every stage on `stream`.  The stages
- * run as one persistent launch each over all descs.  The first call with a
- * given batch signature (shapes, tiles) captures the stage launches, together
- * with the copy of the job table, into a CUDA graph.  Later calls with that
- * signature rewrite the job table and replay the graph.  V3C_FLAG_NO_GRAPH
- * or V3C_FLAG_TIMING selects direct launches instead.  ids[i] receives the
- * object id.  Host inputs are copied to the device inside the call.  The
+ * run as one persistent launch each over all descs.  A batch signature
+ * (shapes, tiles) seen a second time is captured, stage launches and the
+ * copy of the job table together, into a CUDA graph; later calls with that
+ * signature rewrite the job table and replay the graph.  V3C_FLAG_NO_GRAPH,
+ * V3C_FLAG_TIMING and large host inputs select direct launches.  ids[i]
+ * receives the object id.  Host inputs are copied to the device inside the
+ * call; large ones (at least 16 columns and 2^22 words) in column chunks on a
+ * copy stream, each chunk's first two stages starting when it lands.  The
  * objects stay resident until v3c_release.  Errors: EINVAL, ENOMEM (the HBM
  * budget would be exceeded; nothing is allocated), ECUDA. */
 v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v3c_commit_id* ids,
