@@ -38,3 +38,25 @@ def test_cpu_sample_rules():
     assert not whole and (s.c, s.log_n, s.rate_bits, s.cap_height, s.mix) == (135, 14, 3, 4, "trace")
     s, whole = bench.cpu_sample(synth.PROFILE_8x2_20)
     assert not whole and s.c == 8 and s.c << s.log_n <= bench.CPU_SAMPLE.c << bench.CPU_SAMPLE.log_n
+
+
+def test_reference_arm_line_contract():
+    """--impl reference runs the oracle on the host and prints one JSON line
+    with the keys of the bench contract."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                        "plain_8x2_10", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       cwd=root, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["workload"] == "plain_8x2_10"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
