@@ -391,6 +391,7 @@ def run_v3c(args):
     leaf_ms_per = leaf_ms / max(leaf_n, 1)
     achieved = W_PER_PERM * perms_leaf / (leaf_ms_per * 1e-3) / 1e12
     peak = SMS * WIDE_MUL_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    peaks = int_peaks(ctx) if rank == 0 else {}
     traffic = LEAF_HASH_TRAFFIC.get(args.workload)
     stage_ms = {k: (v[0] / max(v[1], 1), int(v[1])) for k, v in stats.items()}
 
@@ -409,6 +410,10 @@ def run_v3c(args):
             "clocks": clk,
             "roofline": {"bound": "alu", "kernel": "k_leaf_hash", "achieved": achieved, "peak": peak,
                          "unit": "T wide-mul/s", "frac": achieved / peak, "traffic": traffic,
+                         "frac_uses": "peak_derived (the larger, stricter denominator)",
+                         "peak_derived": peak, **peaks,
+                         "frac_of_measured_wide": achieved / peaks["peak_measured_wide"]
+                         if peaks.get("peak_measured_wide") else None,
                          "work_per_launch": W_PER_PERM * perms_leaf, "ms_per_launch": leaf_ms_per},
             "stages_ms_per_launch": stage_ms,
         }
@@ -418,10 +423,6 @@ def run_v3c(args):
             line["path_roofline"] = {"error": str(e)}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(shape=s)
-        if args.int_peak:
-            rate, _ = ctx.int_peak(10)
-            line["int_peak_measured"] = {"value": rate / 1e12, "unit": "T wide-mul/s",
-                                         "per_sm_clk_at_max": rate / (SMS * SM_MAX_MHZ * 1e6)}
         print(json.dumps(line))
     ctx.close()
     if world > 1:
@@ -986,6 +987,23 @@ def run_seteq(args):
     return 0
 
 
+def int_peaks(ctx) -> dict:
+    """The integer roofline's denominators, measured on this GPU in this run
+    (under a second): 32-bit IMAD lanes per second (halved: a 32x32->64
+    product takes a low and a high lane) and 32x32->64 wide multiply-adds
+    per second, each with the SM clock of its run, beside the derived
+    152 x 32 x 2070 MHz."""
+    try:
+        lanes, mhz_l = ctx.int_pipe_rate(1, 5)
+        wide, mhz_w = ctx.int_pipe_rate(0, 5)
+    except Exception as e:  # pragma: no cover
+        return {"peak_measured_error": str(e)}
+    return {"peak_measured_imad_lanes_half": lanes / 2 / 1e12, "peak_measured_wide": wide / 1e12,
+            "imad_lanes_per_sm_clk": lanes / (SMS * mhz_l * 1e6) if mhz_l else None,
+            "wide_per_sm_clk": wide / (SMS * mhz_w * 1e6) if mhz_w else None,
+            "int_peak_sm_mhz": mhz_w}
+
+
 def path_roofline(s, ms: float, hbm_gbs: float) -> dict:
     """T_roof = max(bytes_alg / HBM, W_alg / R_int) for one commit of shape s
     against the measured step time ms.  W_alg: 6792 wide multiplies per
@@ -1025,7 +1043,6 @@ def main():
                                                                "snapshot_msmarco", "seteq_64x2_17"],
                     default="large_135x2_20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--int-peak", action="store_true", help="also run the integer-pipe microbenchmark")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time its tile choices for the shape during the warm-up")
     ap.add_argument("--rate", type=float, default=200.0, help="serve_poisson: arrivals per second")

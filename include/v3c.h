@@ -231,6 +231,9 @@ v3c_status v3c_serve_stop(v3c_ctx* ctx);
 /* Number of this library's kernel launches enqueued by the context so far. */
 uint64_t v3c_kernel_launches(v3c_ctx* ctx);
 
+/* Number of v3c_commit calls served by replaying a captured CUDA graph. */
+uint64_t v3c_graph_replays(v3c_ctx* ctx);
+
 /* Per-stage timing.  With V3C_FLAG_TIMING in the context's flags, every
  * stage launch is bracketed by two CUDA events recorded on the stream it is
  * launched on.  v3c_stage_stats waits for the pending events and returns
@@ -249,10 +252,17 @@ typedef struct {
 } v3c_stage_stats_t;
 v3c_status v3c_stage_stats(v3c_ctx* ctx, v3c_stage_stats_t* out, int reset);
 
-/* Microbenchmark of the integer multiply pipe: independent chains of
- * 32x32->64 wide multiply-adds on every SM.  Returns wide multiplies per
- * second in *rate (best of `reps`) and the kernel's clock-derived SM MHz in
- * *mhz.  Synchronous. */
+/* Microbenchmarks of the integer multiply pipe (the denominator of the
+ * integer roofline: the measured rate of 32x32->64 wide multiplies).
+ * Independent chains of multiply-adds on every SM, `reps` timed runs after
+ * one warm-up.  kind 0: 32x32->64 wide multiply-adds (mad.wide.u32);
+ * kind 1: 32-bit multiply-adds (mad.lo.u32, one IMAD lane each).  *rate
+ * receives operations per second (best run); *mhz (may be NULL) the SM clock
+ * of that run, from the kernel's clock64() span over its event time.
+ * Synchronous.  Errors: EINVAL (kind), ECUDA. */
+v3c_status v3c_int_pipe_rate(v3c_ctx* ctx, uint32_t kind, uint32_t reps, double* rate, double* mhz);
+
+/* v3c_int_pipe_rate with kind 0. */
 v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz);
 
 /* ---------------- allocation-free LDE ---------------- */
@@ -267,7 +277,9 @@ v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz);
  * routine.
  *
  * Its work space is one file-scope device array of V3C_NOALLOC_SCRATCH_BYTES.
- * Every GPU that loads the library holds that array until the process exits.
+ * The library's modules load lazily, so the array is reserved on a device by
+ * the first call of this entry point there, and held until the process
+ * exits.
  * It needs 8 * (64 + T + c * (n + N)) bytes.  T is the shape's table size,
  * at most 2n + 2^14 words.  The c * (n + N) term is 0 when
  * n <= 2^(13 - rate_bits).
@@ -275,12 +287,18 @@ v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz);
  * 135 x 2^14 rows at rate 3 is too large.  The caller still passes and owns
  * the input and output buffers.
  *
- * The first call on a device looks up the array's device address with that
- * device current.  Make that first call before any stream capture.  All
+ * The first call on a device loads the module (reserving the array and the
+ * stage kernels' code) and looks up the array's device address with that
+ * device current.  Make that first call before any stream capture and
+ * before another allocator takes the device's free memory; a first call
+ * that finds no room for the array returns ENOMEM.  The address is cached
+ * per device ordinal for the device's primary context: it is not valid
+ * across cudaDeviceReset or in another context on the same device.  All
  * calls share the array, which keeps the last call's contents.  Every word
  * is rewritten before it is read, so nothing is cleared.  Calls whose work
  * overlaps on the GPU (different streams, no ordering) race on the array,
- * so order them.  Errors: EINVAL (shape, NULL, or over the limit), ECUDA. */
+ * so order them.  Errors: EINVAL (shape, NULL, or over the limit), ENOMEM
+ * (first call: no room for the array), ECUDA. */
 #define V3C_NOALLOC_SCRATCH_BYTES (32u << 20)
 v3c_status v3c_lde_noalloc(const uint64_t* d_cols, uint32_t c, uint32_t log_n, uint32_t rate_bits,
                            uint64_t* d_lde, uint32_t ld, void* stream);

@@ -124,9 +124,12 @@ SIGNATURES = {
     "v3c_serve_poll": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int), _u64p, ctypes.POINTER(ReqTimes)]),
     "v3c_serve_stop": (ctypes.c_int, [_vp]),
     "v3c_kernel_launches": (_u64, [_vp]),
+    "v3c_graph_replays": (_u64, [_vp]),
     "v3c_stage_stats": (ctypes.c_int, [_vp, ctypes.c_void_p, ctypes.c_int]),
     "v3c_lde_noalloc": (ctypes.c_int, [_vp, _u32, _u32, _u32, _vp, _u32, _vp]),
     "v3c_int_peak": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "v3c_int_pipe_rate": (ctypes.c_int, [_vp, _u32, _u32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
     # include/v3c_fri.h
     "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64p, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
     "v3c_fri_fold": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _vp]),
@@ -214,9 +217,23 @@ def lde_noalloc(cols, rate_bits: int, out, ld: int | None = None, stream=None) -
     """v3c_lde_noalloc on the current device: the LDE of ``cols`` into the
     caller's preallocated ``out`` [N][ld].  The library allocates nothing;
     its work space is a fixed device array, for callers that cannot allocate.
-    Returns the v3c status (0 = ok)."""
+    Returns the v3c status (0 = ok).  The shapes are checked here, since
+    the kernels write into ``out`` without knowing its size."""
+    import torch
+
     c, n = cols.shape
+    if n < 1 or n & (n - 1):
+        raise ValueError(f"lde_noalloc: row count {n} is not a power of two")
     ld = out.shape[1] if ld is None else ld
+    for name, t in (("cols", cols), ("out", out)):
+        if t.dtype != torch.int64 or not t.is_contiguous() or t.device.type != "cuda":
+            raise ValueError(f"lde_noalloc: {name} must be a contiguous int64 CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"lde_noalloc: {name} is not on the current CUDA device")
+    if out.dim() != 2 or out.shape[0] != n << rate_bits:
+        raise ValueError(f"lde_noalloc: out must have {n << rate_bits} rows, has {tuple(out.shape)}")
+    if not c <= ld <= out.shape[1]:
+        raise ValueError(f"lde_noalloc: need c <= ld <= out.shape[1] (c={c}, ld={ld}, out={tuple(out.shape)})")
     return load().v3c_lde_noalloc(_ptr(cols), c, n.bit_length() - 1, rate_bits, _ptr(out), ld, _stream(stream))
 
 
@@ -518,6 +535,10 @@ class Context:
     def kernel_launches(self) -> int:
         return self.lib.v3c_kernel_launches(self.h)
 
+    def graph_replays(self) -> int:
+        """v3c_commit calls served by replaying a captured CUDA graph."""
+        return self.lib.v3c_graph_replays(self.h)
+
     def stage_stats(self, reset: bool = False) -> dict:
         """Device time (ms) and launches per stage, from CUDA events the library
         records around each stage launch on its stream (needs FLAG_TIMING)."""
@@ -526,8 +547,13 @@ class Context:
         return {name: (st.ms[i], st.launches[i]) for i, name in enumerate(STAGES)}
 
     def int_peak(self, reps: int = 10) -> tuple[float, float]:
+        """Measured 32x32->64 wide multiply-adds per second and the SM MHz of that run."""
+        return self.int_pipe_rate(0, reps)
+
+    def int_pipe_rate(self, kind: int, reps: int = 10) -> tuple[float, float]:
+        """v3c_int_pipe_rate: kind 0 = wide multiply-adds, 1 = 32-bit multiply-adds."""
         rate, mhz = ctypes.c_double(), ctypes.c_double()
-        self._check(self.lib.v3c_int_peak(self.h, reps, ctypes.byref(rate), ctypes.byref(mhz)))
+        self._check(self.lib.v3c_int_pipe_rate(self.h, kind, reps, ctypes.byref(rate), ctypes.byref(mhz)))
         return rate.value, mhz.value
 
 

@@ -120,7 +120,7 @@ u32 merkle_warp_items(const TreeJob& j, u32 lev0);
 cudaError_t launch_merkle_warp(const TreeJob* d_jobs, StageList l, u32 lev0, u32 nlev, int grid, cudaStream_t s);
 
 cudaError_t launch_validate(const u64* x, u64 count, u32* d_flag, cudaStream_t s);
-cudaError_t launch_int_peak(u64* out, int grid, int threads, u32 iters, cudaStream_t s);
+cudaError_t launch_int_peak(u64* out, int grid, int threads, u32 iters, int wide, cudaStream_t s);
 
 int max_smem_optin();
 int num_sms();

@@ -31,7 +31,10 @@ static __device__ __align__(256) u64 g_noalloc_scratch[V3C_NOALLOC_SCRATCH_BYTES
 
 // Device address of g_noalloc_scratch per device.  In host code the array's
 // name is only a host-side stand-in, so it is looked up once per device with
-// that device current.
+// that device current.  The modules of this library load lazily: the first
+// lookup on a device loads this file's module and so reserves the array
+// there.  The cached address belongs to the device's primary context and
+// goes stale after cudaDeviceReset.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 u64* g_addr[kMaxDevices] = {nullptr};
@@ -45,7 +48,9 @@ v3c_status scratch_address(int dev, u64** out)
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
-            return V3C_ECUDA;
+            // Loading the module reserves the array; with the HBM already
+            // taken by another allocator that reservation is what fails.
+            return e == cudaErrorMemoryAllocation ? V3C_ENOMEM : V3C_ECUDA;
         }
         g_addr[dev] = (u64*)p;
     }

@@ -755,29 +755,51 @@ cudaError_t launch_validate(const u64* x, u64 count, u32* d_flag, cudaStream_t s
 }
 
 // Integer-pipe microbenchmark: each thread runs 8 independent chains of
-// 32x32->64 multiply-adds (mad.wide.u32), `iters` steps each.
+// multiply-adds, `iters` x 4 steps each.  WIDE: 32x32->64 products with a
+// 64-bit addend (mad.wide.u32); otherwise 32-bit multiply-adds (mad.lo.u32,
+// one IMAD lane each).  Block 0 records its clock64() span in out[0] so the
+// host can derive the SM clock of the run.
+template <bool WIDE>
 __global__ void k_int_peak(u64* out, u32 iters)
 {
+    const long long c0 = clock64();
     u32 a = threadIdx.x * 2654435761u + blockIdx.x;
-    u64 acc[8];
-#pragma unroll
-    for (int k = 0; k < 8; k++) acc[k] = (u64)(a + k) * 0x9E3779B9u;
-    for (u32 i = 0; i < iters; i++) {
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-#pragma unroll
-            for (int rep = 0; rep < 4; rep++) acc[k] = (u64)(u32)acc[k] * (a | 1u) + acc[k];
-        }
-    }
     u64 x = 0;
+    if (WIDE) {
+        u64 acc[8];
 #pragma unroll
-    for (int k = 0; k < 8; k++) x ^= acc[k];
-    if (x == 0x123456789ull) out[blockIdx.x] = x;
+        for (int k = 0; k < 8; k++) acc[k] = (u64)(a + k) * 0x9E3779B9u;
+        for (u32 i = 0; i < iters; i++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+#pragma unroll
+                for (int rep = 0; rep < 4; rep++) acc[k] = (u64)(u32)acc[k] * (a | 1u) + acc[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) x ^= acc[k];
+    } else {
+        u32 acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc[k] = (a + k) * 0x9E3779B9u;
+        for (u32 i = 0; i < iters; i++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+#pragma unroll
+                for (int rep = 0; rep < 4; rep++) acc[k] = acc[k] * (a | 1u) + (u32)k;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) x ^= acc[k];
+    }
+    if (x == 0x123456789ull) out[1 + blockIdx.x] = x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = (u64)(clock64() - c0);
 }
 
-cudaError_t launch_int_peak(u64* out, int grid, int threads, u32 iters, cudaStream_t s)
+cudaError_t launch_int_peak(u64* out, int grid, int threads, u32 iters, int wide, cudaStream_t s)
 {
-    k_int_peak<<<grid, threads, 0, s>>>(out, iters);
+    if (wide) k_int_peak<true><<<grid, threads, 0, s>>>(out, iters);
+    else k_int_peak<false><<<grid, threads, 0, s>>>(out, iters);
     return cudaGetLastError();
 }
 

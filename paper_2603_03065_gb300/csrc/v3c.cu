@@ -1097,6 +1097,8 @@ v3c_status v3c_release(v3c_ctx* ctx, v3c_commit_id id)
 
 uint64_t v3c_kernel_launches(v3c_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
+uint64_t v3c_graph_replays(v3c_ctx* ctx) { return ctx ? ctx->graph_replays.load() : 0; }
+
 v3c_status v3c_stage_stats(v3c_ctx* ctx, v3c_stage_stats_t* out, int reset)
 {
     if (!ctx || !out) return V3C_EINVAL;
@@ -1130,41 +1132,47 @@ v3c_status v3c_stage_stats(v3c_ctx* ctx, v3c_stage_stats_t* out, int reset)
     return V3C_OK;
 }
 
-v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz)
+v3c_status v3c_int_pipe_rate(v3c_ctx* ctx, uint32_t kind, uint32_t reps, double* rate, double* mhz)
 {
-    if (!ctx || !rate) return V3C_EINVAL;
+    if (!ctx || !rate || kind > 1) return V3C_EINVAL;
     v3c_status st = use_device(ctx);
     if (st) return st;
     int sms = num_sms();
     int grid = sms * 8, threads = 256;
     u32 iters = 4096;
     u64* out = nullptr;
-    CK(cudaMalloc(&out, (size_t)grid * 8));
+    CK(cudaMalloc(&out, (size_t)(grid + 1) * 8));
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
-    double best = 0;
+    double best = 0, best_mhz = 0;
     for (u32 r = 0; r < std::max(reps, 1u) + 1; r++) {
         CK(cudaEventRecord(a, 0));
-        CK(launch_int_peak(out, grid, threads, iters, 0));
+        CK(launch_int_peak(out, grid, threads, iters, kind == 0, 0));
         ctx->launches++;
         CK(cudaEventRecord(b, 0));
         CK(cudaEventSynchronize(b));
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, a, b));
+        u64 cycles = 0;
+        CK(cudaMemcpy(&cycles, out, 8, cudaMemcpyDeviceToHost));
         double ops = (double)grid * threads * iters * 8 * 4;
-        if (r > 0) best = std::max(best, ops / (ms * 1e-3));
+        if (r > 0 && ops / (ms * 1e-3) > best) {
+            best = ops / (ms * 1e-3);
+            best_mhz = (double)cycles / (ms * 1e3);
+        }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(out);
     *rate = best;
-    if (mhz) {
-        int khz = 0;
-        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
-        *mhz = khz / 1000.0;
-    }
+    if (mhz) *mhz = best_mhz;
     return V3C_OK;
+}
+
+v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz)
+{
+    return v3c_int_pipe_rate(ctx, 0, reps, rate, mhz);
 }
 
 }  // extern "C"

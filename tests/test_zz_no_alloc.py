@@ -47,6 +47,39 @@ def test_noalloc_lde_matches_v3c_lde_on_two_calls(v3c):
             assert torch.equal(out, want)
 
 
+def test_noalloc_call_allocates_no_device_memory(v3c):
+    """The property the entry point exists for: once its array is reserved
+    (the first call on the device), a call changes the device's free memory
+    by nothing."""
+    import torch
+
+    torch.cuda.set_device(0)
+    x = synth.columns(seed=47, c=9, log_n=13, mix="trace")
+    d = v3c.to_device_u64(x)
+    out = torch.empty((1 << 16, 10), dtype=torch.int64, device="cuda")
+    assert v3c.lde_noalloc(d, 3, out) == v3c.V3C_OK               # warm: module and array in place
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert v3c.lde_noalloc(d, 3, out) == v3c.V3C_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_binding_checks_the_output_shape(v3c):
+    import torch
+
+    torch.cuda.set_device(0)
+    d = v3c.to_device_u64(synth.columns(seed=48, c=4, log_n=10, mix="trace"))
+    with pytest.raises(ValueError):
+        v3c.lde_noalloc(d, 3, torch.empty((1 << 12, 4), dtype=torch.int64, device="cuda"))   # rows for rate 1
+    with pytest.raises(ValueError):
+        v3c.lde_noalloc(d, 3, torch.empty((1 << 13, 3), dtype=torch.int64, device="cuda"))   # fewer than c columns
+    with pytest.raises(ValueError):
+        v3c.lde_noalloc(d[:, :1000], 3, torch.empty((8000, 4), dtype=torch.int64, device="cuda"))  # n not 2^k
+
+
 def test_noalloc_refuses_shapes_over_the_limit(v3c):
     import torch
 
