@@ -13,8 +13,14 @@ step by step, each after an untimed write of a 256 MB buffer.
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
 reference arm of this tier) on a bounded sample of the same workload, or on
 the whole workload when it is no larger than that sample.
-Under torchrun each rank commits its own batch of the same shape on its
-own GPU (independent problems: weak scaling, no data-path collective).
+Under torchrun the ranks split the one commit by LDE row blocks (strong
+scaling): each computes the coefficients of its share of the columns, one
+NCCL all-gather assembles them, and each commits its coset block (a whole
+subtree, whose top is its slice of the cap).  --replicas instead has each
+rank commit its own independent request (weak scaling, no data-path
+collective).  The default single-GPU line also carries the serving block
+(latency at load against the serial path) and the batched block (64 uneven
+batches in one commit against one commit per batch).
 """
 from __future__ import annotations
 
@@ -423,6 +429,17 @@ def run_v3c(args):
             line["path_roofline"] = {"error": str(e)}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(shape=s)
+        if world == 1 and args.workload == "large_135x2_20" and not args.no_extras:
+            # The other half of the metric (latency at load) and the batched
+            # form, measured after the timed region of the line's value.
+            try:
+                line["serving"] = serving_block(None, args.serve_duration, load=args.serve_load)
+            except Exception as e:  # pragma: no cover
+                line["serving"] = {"error": str(e)}
+            try:
+                line["batched"] = batched_block(3, 2, autotune_variants=False)
+            except Exception as e:  # pragma: no cover
+                line["batched"] = {"error": str(e)}
         print(json.dumps(line))
     ctx.close()
     if world > 1:
@@ -432,29 +449,143 @@ def run_v3c(args):
     return 0
 
 
-def run_batched(args):
-    """64 uneven column-batches (seed 3): one v3c_commit over all of them
-    (one persistent launch per stage, replayed from a CUDA graph) against 64
-    one-batch commits (per-batch launches), on the same device-resident
-    inputs.  Not the default bench line."""
+def run_split(args):
+    """One commit split over the ranks by LDE row blocks (strong scaling):
+    each rank computes the coefficients of its share of the columns
+    (v3c_coeffs), one NCCL all-gather assembles the coefficient table on
+    every rank, each rank commits its part (v3c_commit_part: its coset block,
+    a whole subtree) and rank 0 gathers the cap slices.  The value is the
+    whole commit's LDE elements over the slowest rank's time per step."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2603_03065_gb300 as v3c
+    from paper_2603_03065_gb300 import split
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if not dist.is_initialized():
+        if world == 1:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29533")
+            os.environ.setdefault("RANK", "0")
+            os.environ.setdefault("WORLD_SIZE", "1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    s = WORKLOADS[args.workload]
+    log_parts = split.log_parts_for(world, s.rate_bits, s.cap_height)
+    c0, c1 = split.column_shard(s.c, world, rank)
+    x = s.inputs()[c0:c1]
+    ctx = v3c.Context(local_rank, flags=v3c.FLAG_TIMING)
+    stream = torch.cuda.current_stream()
+    d_x = v3c.to_device_u64(x) if c1 > c0 else None
+    held = []
+
+    def new_table(rows, cols):
+        return torch.empty((rows, cols), dtype=torch.int64, device="cuda")
+
+    def commit_part(coeffs, lp, q):
+        cid = ctx.commit_part(coeffs, s.rate_bits, s.cap_height, lp, q, stream=stream)
+        b = ctx.buffers(cid)
+        cap = new_table(1 << (s.cap_height - lp), 4)
+        cap.copy_(_device_words(b["cap"], cap.numel()).view(cap.shape))
+        return cid, cap
+
+    def step():
+        cid, cap = split.commit_split(d_x, s.c, s.log_n, s.rate_bits, s.cap_height,
+                                      coeffs_of=lambda t: ctx.coeffs(t, stream=stream),
+                                      commit_part=commit_part, new_table=new_table)
+        ctx.release(cid)
+        return cap
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    ctx.stage_stats(reset=True)
+    l0 = ctx.kernel_launches()
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    launches = ctx.kernel_launches() - l0
+    stats = ctx.stage_stats(reset=True)
+    # end to end: each rank's pinned host shard copied in, the cap read back on rank 0
+    pinned = torch.from_numpy(x.view(np.int64)).pin_memory() if c1 > c0 else None
+    dist.barrier()
+    t_total = 0.0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        if pinned is not None:
+            d_x.copy_(pinned, non_blocking=True)
+        cap = step()
+        if rank == 0:
+            cap.cpu()
+        torch.cuda.synchronize()
+        t_total += time.perf_counter() - t0
+    e2e_s = max_over_ranks(t_total / args.steps)
+    if rank == 0:
+        value = s.lde_elems() / (ms * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": dict(workload_config(args.workload, s), parallelism=f"row split over {world} GPUs "
+                           f"(2^{log_parts} cosets blocks, one all-gather of coefficients)"),
+            "e2e": {"value": s.lde_elems() / e2e_s / 1e9, "unit": "Gelem/s",
+                    "h2d_bytes_per_step": int(s.c << s.log_n) * 8, "d2h_bytes_per_step": int(32 << s.cap_height),
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": int(launches) * world,
+            "clocks": clk,
+            "stages_ms_per_launch": {k: (v[0] / max(v[1], 1), int(v[1])) for k, v in stats.items()},
+        }
+        print(json.dumps(line))
+    ctx.close()
+    dist.destroy_process_group()
+    return 0
+
+
+def _device_words(ptr: int, words: int):
+    import torch
+
+    class _A:
+        __cuda_array_interface__ = {"shape": (words,), "typestr": "<i8", "data": (ptr, False), "version": 3}
+
+    return torch.as_tensor(_A(), device="cuda")
+
+
+def batched_block(steps: int, warmup: int, autotune_variants: bool = True) -> dict:
+    """C4: the 64 uneven column-batches of seed 3 committed by one v3c_commit
+    (one persistent launch per stage, replayed from a CUDA graph, tiles from
+    the autotuner) against one commit per batch (per-batch launches, the
+    same context and tiles), on the same device-resident inputs."""
     import torch
 
     import paper_2603_03065_gb300 as v3c
 
-    torch.cuda.set_device(0)
     shapes = synth.uneven_batches(3)
     xs = [s.inputs() for s in shapes]
     elems = sum(s.lde_elems() for s in shapes)
-    out = {"metric": METRIC, "unit": "Gelem/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "dtype": "u64", "data": "synthetic", "vs_baseline": None,
-           "config": {"workload": "uneven_64", "batches": len(shapes), "lde_elems": elems,
-                      "log_rows": [s.log_n for s in shapes], "columns": [s.c for s in shapes],
-                      "rate_bits": [s.rate_bits for s in shapes], "cap_height": 4, "seed": 3}}
+    out = {"workload": "uneven_64", "batches": len(shapes), "lde_elems": elems, "seed": 3, "cap_height": 4,
+           "log_rows": [s.log_n for s in shapes], "columns": [s.c for s in shapes],
+           "rate_bits": [s.rate_bits for s in shapes]}
     stream = torch.cuda.current_stream()
-    for tag, flags, tune in (("batched_graph_autotune", 0, True), ("batched_graph", 0, False),
-                             ("batched_direct", v3c.FLAG_NO_GRAPH, False)):
+    variants = (("batched_graph_autotune", 0, True), ("batched_graph", 0, False),
+                ("batched_direct", v3c.FLAG_NO_GRAPH, False)) if autotune_variants else \
+        (("batched_graph_autotune", 0, True),)
+    for tag, flags, tune in variants:
         # An explicit budget (the 64 batches hold 19.7 GB resident), so the
-        # line does not depend on the free memory seen at context creation.
+        # result does not depend on the free memory seen at context creation.
         ctx = v3c.Context(0, hbm_budget_bytes=64 << 30, flags=flags, autotune=tune)
         ds = [v3c.to_device_u64(x) for x in xs]
         items = [(d, s.rate_bits, s.cap_height) for d, s in zip(ds, shapes)]
@@ -469,63 +600,107 @@ def run_batched(args):
                 ctx.release(ctx.commit([it], stream=stream)[0])
 
         for name, fn in (("all_in_one", batched), ("one_per_commit", per_batch)):
-            if tag != "batched_graph" and name == "one_per_commit":
+            if tag == "batched_direct" and name == "one_per_commit":
                 continue
-            for _ in range(max(args.warmup, 1)):
+            for _ in range(max(warmup, 2)):       # the second sighting of a signature is captured
                 fn()
             torch.cuda.synchronize()
             l0 = ctx.kernel_launches()
+            r0 = ctx.graph_replays()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 fn()
             e1.record(stream)
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
+            ms = e0.elapsed_time(e1) / steps
             out[f"{tag}.{name}"] = {"ms_per_step": ms, "Gelem/s": elems / (ms * 1e-3) / 1e9,
-                                    "launches_per_step": (ctx.kernel_launches() - l0) / args.steps}
+                                    "launches_per_step": (ctx.kernel_launches() - l0) / steps,
+                                    "graph_replays_per_step": (ctx.graph_replays() - r0) / steps}
         ctx.close()
+        del ds
     best = out["batched_graph_autotune.all_in_one"]
-    out["value"] = best["Gelem/s"]
+    base = out["batched_graph_autotune.one_per_commit"]
     out["ms_per_step"] = best["ms_per_step"]
-    out["vs_per_batch_launches"] = best["Gelem/s"] / out["batched_graph.one_per_commit"]["Gelem/s"]
+    out["Gelem/s"] = best["Gelem/s"]
+    out["vs_one_per_commit"] = base["ms_per_step"] / best["ms_per_step"]
+    return out
+
+
+def run_batched(args):
+    """C4 as its own bench line (the default line carries the same block)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    b = batched_block(args.steps, args.warmup)
+    out = {"metric": METRIC, "unit": "Gelem/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "dtype": "u64", "data": "synthetic", "vs_baseline": None,
+           "value": b["Gelem/s"], "ms_per_step": b["ms_per_step"],
+           "config": {k: b[k] for k in ("workload", "batches", "lde_elems", "log_rows", "columns", "rate_bits",
+                                       "cap_height", "seed")},
+           "batched": b}
     print(json.dumps(out))
     return 0
 
 
-def run_serving(args):
-    """Poisson arrivals (rate --rate, --duration s, seed 5) of commits drawn
-    from the mixture 50 % 2^14 x 80, 35 % 2^16 x 135, 15 % 2^18 x 135 (rate 3,
-    cap 4), served by the continuous-batching loop from pinned host inputs
-    (borrowed, copied at admission), each released as soon as it is done.
-    Reports p50/p99 submit->done latency after a 5 s warm-up and Gelem/s, and
-    the same trace through the serial one-at-a-time commit path.  Not the
-    default bench line."""
+SERVE_WARM_S = 3.0
+
+
+def serving_block(rate: float | None, duration: float, max_batch: int = 32, inflight: int = 4,
+                  load: float = 1.1) -> dict:
+    """C5: Poisson arrivals (seed 5) of commits drawn from the mixture 50 %
+    2^14 x 80, 35 % 2^16 x 135, 15 % 2^18 x 135 (rate 3, cap 4), served by
+    the continuous-batching loop from pinned host inputs (borrowed, copied at
+    admission), each released as soon as it is done; then the same trace
+    through the serial one-at-a-time commit path (commit, cap read, release).
+    Latency is submit -> done; p50/p99 over the requests that arrive after a
+    warm-up, throughput over the elements completed after it.
+
+    rate None: the arrival rate is ``load`` times the serial path's capacity,
+    measured here first (the inverse of its mean service time over the
+    mixture, each shape timed warm through the serial path)."""
     import torch
 
     import paper_2603_03065_gb300 as v3c
 
-    torch.cuda.set_device(0)
-    trace = synth.poisson_trace(rate=args.rate, duration=args.duration, seed=5)
-    # A pool of two distinct inputs per mixture shape, pinned on the host.
     pool = {}
     for k, (_, log_n, c) in enumerate(synth.SERVE_MIX):
         for b in range(2):
             s = synth.Shape(c=c, log_n=log_n, rate_bits=3, cap_height=4, batch=1000 + 2 * k + b, seed=5)
             t = torch.from_numpy(s.inputs().view(np.int64)).pin_memory()
             pool[(log_n, c, b)] = t.numpy().view(np.uint64)
+    ctx = v3c.Context(0, hbm_budget_bytes=150 << 30, max_inflight=inflight)
+    stream = torch.cuda.current_stream()
+
+    def serial_one(a):
+        cid = ctx.commit([(a, 3, 4)], stream=stream)[0]
+        ctx.cap(cid)
+        ctx.release(cid)
+
+    service_ms = {}
+    for (log_n, c, b), a in pool.items():
+        if b:
+            continue
+        for _ in range(3):
+            serial_one(a)
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            serial_one(a)
+            ts.append(time.perf_counter() - t0)
+        service_ms[f"{c}x2^{log_n}"] = statistics.median(ts) * 1e3
+    mean_s = sum(p * service_ms[f"{c}x2^{ln}"] for p, ln, c in synth.SERVE_MIX) / 1e3
+    serial_capacity = 1.0 / mean_s
+    if rate is None:
+        rate = load * serial_capacity
+    trace = synth.poisson_trace(rate=rate, duration=duration, seed=5)
+    warm = SERVE_WARM_S if duration > 2 * SERVE_WARM_S else 0.0
 
     def src(i, req):
         return pool[(req.shape.log_n, req.shape.c, i % 2)]
 
-    warm = 5.0 if args.duration > 5.0 else 0.0
-
     def summarize(lat, done):
-        """lat: latencies of requests that arrived after the warm-up; done:
-        (completion time since the trace start, elements) of every request.
-        Throughput counts the elements completed after the warm-up over the
-        time from the end of the warm-up to the last completion."""
         lat = sorted(lat)
         q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None  # noqa: E731
         t_end = max((t for t, _ in done), default=warm)
@@ -534,13 +709,10 @@ def run_serving(args):
                 "p99_ms": q(0.99) * 1e3 if lat else None,
                 "Gelem/s": elems / max(t_end - warm, 1e-9) / 1e9}
 
-    ctx = v3c.Context(0, hbm_budget_bytes=150 << 30, max_inflight=args.inflight)
-    # warm plans and graphs for the three shapes
-    for (log_n, c, b), a in pool.items():
-        if b == 0:
-            ctx.release(ctx.commit([(a, 3, 4)])[0])
-    torch.cuda.synchronize()
-    ctx.serve_start(max_batch=args.max_batch)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = ctx.kernel_launches()
+    ctx.serve_start(max_batch=max_batch)
     pending = {}
     lat, done = [], []
     t0 = time.perf_counter()
@@ -573,34 +745,52 @@ def run_serving(args):
     ctx.serve_stop()
     served = summarize(lat, done)
     served["wall_s"] = wall
+    served["launches"] = ctx.kernel_launches() - l0
 
     # Serial path: one commit at a time, in arrival order, from the same pinned
     # inputs; latency = done - arrival.
-    stream = torch.cuda.current_stream()
     lat_s, done_s = [], []
+    l0 = ctx.kernel_launches()
     t0 = time.perf_counter()
     for k, req in enumerate(trace):
         now = time.perf_counter() - t0
         if req.t_arrive > now:
             time.sleep(req.t_arrive - now)
-        cid = ctx.commit([(src(k, req), 3, 4)], stream=stream)[0]
-        ctx.cap(cid)
-        ctx.release(cid)
+        serial_one(src(k, req))
         t_done = time.perf_counter() - t0
         done_s.append((t_done, req.shape.lde_elems()))
         if req.t_arrive >= warm:
             lat_s.append(t_done - req.t_arrive)
     serial = summarize(lat_s, done_s)
+    serial["wall_s"] = time.perf_counter() - t0
+    serial["launches"] = ctx.kernel_launches() - l0
+    clk = clocks.stop()
     ctx.close()
     mean_elems = sum(r.shape.lde_elems() for r in trace) / max(len(trace), 1)
-    out = {"metric": METRIC, "unit": "Gelem/s", "value": served["Gelem/s"], "higher_is_better": True,
+    return {"workload": "serve_poisson", "rate_rps": rate, "duration_s": duration, "warmup_s": warm,
+            "requests": len(trace), "mix": [list(m) for m in synth.SERVE_MIX], "rate_bits": 3, "cap_height": 4,
+            "hbm_budget_gb": 150, "max_batch": max_batch, "max_inflight": inflight,
+            "offered_Gelem_per_s": rate * mean_elems / 1e9,
+            "serial_service_ms": service_ms, "serial_capacity_rps": serial_capacity,
+            "rate_vs_serial_capacity": rate / serial_capacity,
+            "served": served, "serial": serial,
+            "served_vs_serial_throughput": served["Gelem/s"] / max(serial["Gelem/s"], 1e-12),
+            "served_vs_serial_p99": (serial["p99_ms"] / served["p99_ms"]) if served["p99_ms"] else None,
+            "clocks": clk}
+
+
+def run_serving(args):
+    """C5 as its own bench line (the default line carries the same block at
+    a rate set from the serial path's measured capacity)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    b = serving_block(args.rate, args.duration, args.max_batch, args.inflight)
+    out = {"metric": METRIC, "unit": "Gelem/s", "value": b["served"]["Gelem/s"], "higher_is_better": True,
            "n_gpus": 1, "dtype": "u64", "data": "synthetic", "vs_baseline": None,
-           "config": {"workload": "serve_poisson", "rate_rps": args.rate, "duration_s": args.duration,
-                      "requests": len(trace), "mix": [list(m) for m in synth.SERVE_MIX], "rate_bits": 3,
-                      "cap_height": 4, "hbm_budget_gb": 150, "max_batch": args.max_batch,
-                      "max_inflight": args.inflight, "offered_Gelem_per_s": args.rate * mean_elems / 1e9},
-           "served": served, "serial": serial,
-           "vs_serial_throughput": served["Gelem/s"] / max(serial["Gelem/s"], 1e-12)}
+           "config": {k: v for k, v in b.items() if k not in ("served", "serial", "clocks")},
+           "served": b["served"], "serial": b["serial"], "clocks": b["clocks"],
+           "vs_serial_throughput": b["served_vs_serial_throughput"]}
     print(json.dumps(out))
     return 0
 
@@ -1045,6 +1235,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time its tile choices for the shape during the warm-up")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: each rank commits its own independent request (weak scaling) "
+                         "instead of splitting one commit by row blocks")
+    ap.add_argument("--split", action="store_true", help="run the row-split path even on one GPU")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the serving and batched blocks after the timed region")
+    ap.add_argument("--serve-duration", type=float, default=20.0, help="default line's serving block: seconds")
+    ap.add_argument("--serve-load", type=float, default=1.1,
+                    help="default line's serving block: arrival rate as a multiple of the serial capacity")
     ap.add_argument("--rate", type=float, default=200.0, help="serve_poisson: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve_poisson: trace length in seconds")
     ap.add_argument("--max-batch", type=int, default=32, help="serve_poisson: requests per batched pass")
@@ -1062,6 +1261,8 @@ def main():
         return run_snapshot(args)
     if args.workload == "seteq_64x2_17":
         return run_seteq(args)
+    if args.split or (dist_env()[2] > 1 and not args.replicas):
+        return run_split(args)
     return run_v3c(args)
 
 

@@ -152,6 +152,47 @@ typedef struct {
 v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v3c_commit_id* ids,
                       void* stream);
 
+/* ---------------- a commit split over several GPUs ----------------
+ *
+ * In bit-reversed row order, LDE rows [q N/G, (q+1) N/G) (G = 2^log_parts,
+ * q < G) are the evaluations on the coset 7 w_N^kappa <w_{N/G}>, with
+ * kappa = bitrev_{log G}(q), again in bit-reversed order: the LDE of rate
+ * rate_bits - log_parts on a shifted coset, and a whole subtree of the
+ * commit's Merkle tree.  With cap_height >= log_parts its top level is the
+ * part's slice [q 2^h / G, (q+1) 2^h / G) of the cap, so G devices commit
+ * one request with a single exchange: the coefficients (each device computes
+ * those of its share of the columns with v3c_coeffs, then all gather them),
+ * after which each device commits its part with v3c_commit_part and the cap
+ * is the concatenation of the parts' caps in order of q.  (Scope: the
+ * multi-GPU split of the LDE + Merkle commit; the paper's prover is one CPU
+ * process, Sec. 5, evaluation environment.) */
+
+/* Coefficients of the interpolant of each column, a = iNTT_n(col), natural
+ * order, n^-1 applied: the first half of the LDE (the inverse transform)
+ * without the coset shift.
+ *   d_cols    device, column-major [c][n], n = 2^log_n
+ *   d_coeffs  device, column-major [c][n]
+ * Scratch c * n words from the context's arena when n > 2^10.  Errors:
+ * EINVAL (shape, NULL), ENOMEM (arena), ECUDA. */
+v3c_status v3c_coeffs(v3c_ctx* ctx, const uint64_t* d_cols, uint32_t c, uint32_t log_n, uint64_t* d_coeffs,
+                      void* stream);
+
+typedef struct {
+    const uint64_t* coeffs;  /* device [c][n]: v3c_coeffs of all c columns (kept alive until the
+                                call's work is done) */
+    uint32_t c, log_n, rate_bits, cap_height;  /* the whole commit's shape */
+    uint32_t log_parts;      /* G = 2^log_parts parts; log_parts <= min(rate_bits, cap_height) */
+    uint32_t part;           /* q < G */
+} v3c_part_desc;
+
+/* Commits part q of the split above as a resident object: its N/G LDE rows
+ * [N/G][ld] (object row t' is the commit's row q N/G + t'), its subtree
+ * levels and its cap slice [2^(h - log_parts)][4]; v3c_commit_buffers
+ * reports log_rows = log N - log_parts and cap_height = h - log_parts, and
+ * v3c_open takes object row numbers.  Scratch c * N/G words from the arena.
+ * Errors: EINVAL (shape, part, log_parts), ENOMEM (budget or arena), ECUDA. */
+v3c_status v3c_commit_part(v3c_ctx* ctx, const v3c_part_desc* desc, v3c_commit_id* id, void* stream);
+
 /* Device pointers and shape of a resident object (valid until release).
  * Any output pointer may be NULL. */
 v3c_status v3c_commit_buffers(v3c_ctx* ctx, v3c_commit_id id, uint64_t** d_lde, uint32_t* ld,
@@ -199,11 +240,17 @@ typedef struct {
     double t_submit, t_admit, t_start, t_done;  /* seconds, steady clock of the context */
 } v3c_req_times;
 
-/* Starts the scheduler thread.  Requests are admitted in arrival order while
- * their footprint fits the HBM budget minus what is resident.  All requests
- * admitted by one scheduler pass form one batched launch, and up to
- * max_inflight batches run at once on separate streams.  A request that
- * arrives while others are on the device joins the next pass. */
+/* Starts the scheduler thread.  Requests are grouped by size class (LDE
+ * elements c * 2^(log_n + rate_bits): up to 2^24, up to 2^27, above) and
+ * admitted in arrival order within a class while their footprint fits the
+ * HBM budget minus what is resident.  Each scheduler pass fuses the queued
+ * requests of one class (the class whose oldest request arrived first) into
+ * one batched launch on a free slot; up to max_inflight batches run at once
+ * on separate streams, the small class's streams at the highest priority.
+ * The last free slot goes to the class that has waited longest, and a
+ * request that has waited more than 0.25 s for memory holds back newer
+ * requests of the other classes.  A request that arrives while others are on
+ * the device joins the next pass of its class. */
 v3c_status v3c_serve_start(v3c_ctx* ctx, const v3c_serve_cfg* cfg);
 
 /* Non-blocking submit.  desc->on_device says where desc->cols lives:

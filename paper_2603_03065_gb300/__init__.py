@@ -56,6 +56,11 @@ class CommitDesc(ctypes.Structure):
                 ("rate_bits", _u32), ("cap_height", _u32)]
 
 
+class PartDesc(ctypes.Structure):
+    _fields_ = [("coeffs", _vp), ("c", _u32), ("log_n", _u32), ("rate_bits", _u32), ("cap_height", _u32),
+                ("log_parts", _u32), ("part", _u32)]
+
+
 class ServeCfg(ctypes.Structure):
     _fields_ = [("queue_capacity", _u32), ("max_batch", _u32), ("max_inflight", _u32), ("flags", _u32),
                 ("slot_scratch_bytes", _u64)]
@@ -112,6 +117,8 @@ SIGNATURES = {
     "v3c_lde": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _vp, _u32, _vp]),
     "v3c_merkle": (ctypes.c_int, [_vp, _vp, _u32, _u32, _u32, _u32, _vp, _vp, _vp]),
     "v3c_commit": (ctypes.c_int, [_vp, ctypes.POINTER(CommitDesc), _u32, _u64p, _vp]),
+    "v3c_coeffs": (ctypes.c_int, [_vp, _vp, _u32, _u32, _vp, _vp]),
+    "v3c_commit_part": (ctypes.c_int, [_vp, ctypes.POINTER(PartDesc), _u64p, _vp]),
     "v3c_commit_buffers": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(_vp), ctypes.POINTER(_u32),
                                           ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u32),
                                           ctypes.POINTER(_u32)]),
@@ -320,6 +327,31 @@ class Context:
         ids = (_u64 * len(items))()
         self._check(self.lib.v3c_commit(self.h, descs, len(items), ids, _stream(stream)))
         return list(ids)
+
+    def coeffs(self, cols, out=None, stream=None):
+        """v3c_coeffs: int64 CUDA tensor [c][n] of columns -> [c][n] natural-order
+        coefficients of each column's interpolant (n^-1 applied)."""
+        torch = _torch()
+        c, n = cols.shape
+        if n < 1 or n & (n - 1):
+            raise ValueError(f"coeffs: row count {n} is not a power of two")
+        if out is None:
+            out = torch.empty((c, n), dtype=torch.int64, device=cols.device)
+        elif tuple(out.shape) != (c, n) or not out.is_contiguous():
+            raise ValueError("coeffs: out must be a contiguous [c][n] int64 tensor")
+        self._check(self.lib.v3c_coeffs(self.h, _ptr(cols), c, n.bit_length() - 1, _ptr(out), _stream(stream)))
+        return out
+
+    def commit_part(self, coeffs, rate_bits: int, cap_height: int, log_parts: int, part: int, stream=None) -> int:
+        """v3c_commit_part: part ``part`` of 2^log_parts of the commit whose
+        coefficients are ``coeffs`` (int64 CUDA tensor [c][n]); returns the
+        resident object's id (its rows are the commit's row block of the part)."""
+        c, n = coeffs.shape
+        d = PartDesc(coeffs.data_ptr(), c, n.bit_length() - 1, rate_bits, cap_height, log_parts, part)
+        cid = _u64()
+        self._check(self.lib.v3c_commit_part(self.h, ctypes.byref(d), ctypes.byref(cid), _stream(stream)))
+        self._borrowed[cid.value] = coeffs
+        return cid.value
 
     def buffers(self, cid: int):
         lde, tree, cap = _vp(), _vp(), _vp()

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -81,7 +82,8 @@ struct v3c_ctx {
     int device = 0;
     v3c_config cfg{};
     std::mutex mu;
-    std::map<std::pair<u32, u32>, PlanEntry> plans;
+    // Plan tables by (log_n, rate_bits, coset multiplier, scale factor).
+    std::map<std::tuple<u32, u32, u64, u64>, PlanEntry> plans;
     Arena arena;
     std::vector<UploadSlot> ring;
     u32 ring_next = 0;

@@ -79,20 +79,50 @@ __device__ __forceinline__ u64 mul_nc(u64 a, u64 b) { return reduce128_ptx(a * b
 // Canonical product: inputs in [0, 2^64), output in [0, p).
 __device__ __forceinline__ u64 mul(u64 a, u64 b) { return canon(mul_nc(a, b)); }
 
-// Canonical add/sub: inputs and outputs in [0, p).
+// Canonical sub: a in [0, 2^64), b canonical; the result is canonical when
+// a is.  On a borrow the wrapped d = a - b + 2^64 stands for d - EPS, and
+// d >= 2^64 - (p - 1) > EPS, so d - EPS neither wraps nor reaches p.  On the
+// device this is one borrow chain: the borrow, as a 0 / 0xFFFFFFFF mask, is
+// EPS itself, subtracted from the low word.
+__host__ __device__ __forceinline__ u64 sub(u64 a, u64 b)
+{
+#ifdef __CUDA_ARCH__
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 a0, a1, b0, b1, d0, d1, m;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\t"
+        "mov.b64 {b0, b1}, %2;\n\t"
+        "sub.cc.u32 d0, a0, b0;\n\t"
+        "subc.cc.u32 d1, a1, b1;\n\t"
+        "subc.u32 m, 0, 0;\n\t"
+        "sub.cc.u32 d0, d0, m;\n\t"
+        "subc.u32 d1, d1, 0;\n\t"
+        "mov.b64 %0, {d0, d1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(a), "l"(b));
+    return r;
+#else
+    u64 d = a - b;
+    if (a < b) d += P;  // wrapped a - b + 2^64, plus p (mod 2^64) = a - b + p
+    return d;
+#endif
+}
+
+// Canonical add: a + b = a - (p - b) for canonical b (with b = 0 the
+// subtrahend is p: a - p borrows, and the borrow's correction brings it back
+// to a), so the device form is two more instructions in front of the borrow
+// chain of sub.
 __host__ __device__ __forceinline__ u64 add(u64 a, u64 b)
 {
+#ifdef __CUDA_ARCH__
+    return sub(a, P - b);
+#else
     u64 s = a + b;
     // On carry the true sum is s + 2^64 < 2p, and s - p (mod 2^64) = s + EPS.
     if (s < a || s >= P) s -= P;
     return s;
-}
-
-__host__ __device__ __forceinline__ u64 sub(u64 a, u64 b)
-{
-    u64 d = a - b;
-    if (a < b) d += P;  // wrapped a - b + 2^64, plus p (mod 2^64) = a - b + p
-    return d;
+#endif
 }
 
 // The 128-bit reduction for code that also runs on the host: the carry-chain
@@ -111,27 +141,65 @@ __host__ __device__ __forceinline__ u64 reduce_any(u64 lo, u64 hi)
 // x 2^e mod p for canonical x and 0 <= e < 96, canonical result; e is a
 // constant wherever this is inlined into unrolled code, so only one branch
 // remains.  With 2^64 = 2^32 - 1 and 2^128 = -2^32 (mod p):
-//   e <= 32:      x 2^e = lo + 2^64 h (h < 2^32) = lo + h (2^32 - 1);
-//   32 < e < 64:  lo + 2^64 hi, the 128-bit reduction;
-//   64 <= e < 96: y = x 2^(e-64) = yl + 2^64 yh (yh < 2^31), and
-//                 x 2^e = y 2^64 = yl 2^64 + yh 2^128 = (yl 2^64 mod p) - yh 2^32.
 // Multiplying by 2^(e+96) is the negation of this (2^96 = -1 mod p).
+//   e < 32:       x 2^e = lo + 2^64 h (h < 2^32) = lo + h (2^32 - 1);
+//   32 <= e < 64: lo + 2^64 hi, the 128-bit reduction;
+//   64 <= e < 96: x 2^e = -x 2^-k with k = 96 - e in (0, 32].  Since
+//                 2^32 - 2^64 = 1 (mod p), 2^-k = 2^(32-k) - 2^(64-k); with
+//                 x = q 2^k + r (r < 2^k) this gives x 2^e = A - B, where
+//                 A = r 2^(64-k) = (r 2^(32-k)) 2^32 <= 2^64 - 2^32 < p and
+//                 B = q + r 2^(32-k) < 2^63 + 2^32 < p, so one conditional
+//                 addition of p makes it canonical.
 __host__ __device__ __forceinline__ u64 mul_pow2(u64 x, u32 e)
 {
     if (e == 0) return x;
-    if (e <= 32) {
+    if (e < 32) {
+#ifdef __CUDA_ARCH__
+        // lo = x 2^e mod 2^64 and h = x >> (64 - e) < 2^32; x 2^e = lo + h 2^64
+        // = lo - h + h 2^32 (mod p).  That sum is V = r + c 2^64 with
+        // c in {-1, 0, 1}; V = r + c EPS (mod p) stays within [0, p) for
+        // c != 0, and a final compare-subtract handles c = 0.
+        u64 r;
+        asm("{\n\t"
+            ".reg .u32 x0, x1, l0, l1, h, r0, r1, b, c, nc, sc;\n\t"
+            ".reg .pred q;\n\t"
+            "mov.b64 {x0, x1}, %1;\n\t"
+            "shl.b32 l0, x0, %2;\n\t"
+            "shf.l.wrap.b32 l1, x0, x1, %2;\n\t"
+            "shr.b32 h, x1, %3;\n\t"
+            "sub.cc.u32 r0, l0, h;\n\t"
+            "subc.cc.u32 r1, l1, 0;\n\t"
+            "subc.u32 b, 0, 0;\n\t"
+            "add.cc.u32 r1, r1, h;\n\t"
+            "addc.u32 c, b, 0;\n\t"
+            "neg.s32 nc, c;\n\t"
+            "shr.s32 sc, c, 31;\n\t"
+            "add.cc.u32 r0, r0, nc;\n\t"
+            "addc.u32 r1, r1, sc;\n\t"
+            "setp.eq.u32 q, r1, 0xFFFFFFFF;\n\t"
+            "setp.ne.and.u32 q, r0, 0, q;\n\t"
+            "@q add.u32 r0, r0, 0xFFFFFFFF;\n\t"
+            "@q mov.u32 r1, 0;\n\t"
+            "mov.b64 %0, {r0, r1};\n\t"
+            "}"
+            : "=l"(r)
+            : "l"(x), "r"(e), "r"(32 - e));
+        return r;
+#else
         u64 lo = x << e;
         u64 h = x >> (64 - e);
         u64 t = (h << 32) - h;  // < 2^64 - 2^32
         u64 r = lo + t;
         if (r < t) r += EPS;    // carry: r + 2^64 = r + EPS, and r < t here
         return canon(r);
+#endif
     }
     if (e < 64) return canon(reduce_any(x << e, x >> (64 - e)));
-    const u32 f = e - 64;
-    const u64 yl = f ? x << f : x;
-    const u64 yh = f ? x >> (64 - f) : 0;
-    return sub(canon(reduce_any(0, yl)), yh << 32);
+    const u32 k = 96 - e;
+    const u64 q = x >> k;
+    const u64 ah = (k == 32 ? (x & 0xFFFFFFFFull) : ((x & ((1ull << k) - 1)) << (32 - k)));
+    const u64 A = ah << 32, B = q + ah;
+    return A >= B ? A - B : A - B + P;
 }
 
 // a in [0, 2^64), k canonical: a + k mod p as a value in [0, 2^64).

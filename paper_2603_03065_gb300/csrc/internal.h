@@ -21,8 +21,11 @@ typedef uint32_t u32;
 // With n1 = 1, stages A and C vanish and B writes the rows itself.
 struct Plan {
     u32 log_n, r, log_n1, log_n2, log_M, log_N;
+    // The coset is g * <w_N> with g = 7 * gshift, and the scale table holds
+    // g^j * sfac: gshift = 1, sfac = n^-1 for the LDE of columns.
+    u64 gshift, sfac;
     const u64* twa;      // [n1][n2]: w_n^-(k1*i2)                     (n1 > 1)
-    const u64* scale;    // [n1][n2]: 7^(k1 + n1*bitrev_n2(t)) / n, by position t
+    const u64* scale;    // [n1][n2]: g^(k1 + n1*bitrev_n2(t)) * sfac, by position t
     const u64* pw_N;     // [3][512]: w_N^(j * 2^(9 level))              (n1 > 1)
     const u64* rinv_n1;  // [n1]:     w_n1^-j
     const u64* rinv_n2;  // [n2/2]:   w_n2^-j
@@ -44,7 +47,19 @@ struct LdeJob {
     u32 c_qc;      // stage C: q values per CTA (power of two, <= c_q)
     u32 kcap;      // largest radix exponent of the in-register DFT passes (1..4)
     u32 wcols;     // columns writable from lde: ld for a whole matrix, fewer for a column chunk
+    u32 mode;      // kLdeFromColumns, kCoeffsOut or kLdeFromCoeffs
+    u64 cscale;    // kCoeffsOut: n^-1, applied to the unnormalised inverse DFT
 };
+
+// LdeJob.mode.  kLdeFromColumns: the LDE of the input columns x (stages A,
+// B, C).  kCoeffsOut: the interpolant's coefficients a = iNTT_n(x), written
+// in natural order to `lde` as [c][n] (stage A and the inverse half of
+// stage B).  kLdeFromCoeffs: x holds coefficients [c][n] in natural order and
+// the LDE is evaluated from them (the forward half of stage B, and stage
+// C); the plan's scale table then carries no n^-1.
+constexpr u32 kLdeFromColumns = 0;
+constexpr u32 kCoeffsOut = 1;
+constexpr u32 kLdeFromCoeffs = 2;
 
 // Tile choice of one (log_n, rate_bits) shape, from the autotuner.
 struct TuneEntry {

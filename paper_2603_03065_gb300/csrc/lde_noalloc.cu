@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "../../include/v3c.h"
+#include "gl.cuh"
 #include "internal.h"
 
 namespace v3c {
@@ -104,6 +105,8 @@ extern "C" v3c_status v3c_lde_noalloc(const uint64_t* d_cols, uint32_t c, uint32
     memset(&j, 0, sizeof j);
     j.plan.log_n = log_n;
     j.plan.r = rate_bits;
+    j.plan.gshift = 1;
+    j.plan.sfac = gl::h_inv(n % gl::P);
     if (build_plan_tables(j.plan, base + kHeaderWords, s) != cudaSuccess) return V3C_ECUDA;
     j.x = d_cols;
     j.c = c;

@@ -74,7 +74,7 @@ struct TableArgs {
     u64* rinv_n2;
     u64* rfwd_M;
     u64* rfwd_n1;
-    u64 w_n_inv, w_N, w_n1_inv, w_n2_inv, w_M, w_n1, n_inv;
+    u64 w_n_inv, w_N, w_n1_inv, w_n2_inv, w_M, w_n1, g, sfac;
     u32 log_n, log_n1, log_n2, log_M, log_N;
     u64 seg[8];  // cumulative segment ends
 };
@@ -92,7 +92,7 @@ __global__ void k_plan_tables(TableArgs a)
             u64 i = e - a.seg[0];
             u64 k1 = i >> a.log_n2, t = i & (n2 - 1);
             u64 j = k1 + (u64)n1 * gl::bitrev((u32)t, a.log_n2);
-            a.scale[i] = gl::mul(gl::pow(7, j), a.n_inv);
+            a.scale[i] = gl::mul(gl::pow(a.g, j), a.sfac);
         } else if (e < a.seg[2]) {  // pw_N[level][j] = w_N^(j * 2^(9 level))
             u64 i = e - a.seg[1];
             u64 level = i >> 9, j = i & 511;
@@ -151,7 +151,8 @@ cudaError_t build_plan_tables(Plan& p, u64* base, cudaStream_t s)
     a.w_n2_inv = hinv(hroot(l2));
     a.w_M = hroot(p.log_M);
     a.w_n1 = hroot(l1);
-    a.n_inv = hinv(n % gl::P);
+    a.g = hmul(7, p.gshift);
+    a.sfac = p.sfac;
     a.log_n = p.log_n;
     a.log_n1 = l1;
     a.log_n2 = l2;
@@ -449,7 +450,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 u32 stage_a_items(const LdeJob& j, const Tiles&)
 {
-    if (!j.plan.log_n1) return 0;
+    if (!j.plan.log_n1 || j.mode == kLdeFromCoeffs) return 0;
     return j.c * ((1u << j.plan.log_n2) / j.a_cols);
 }
 
@@ -535,11 +536,28 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
             for (u32 e = threadIdx.x; e < M / 2; e += blockDim.x) twf[sw(e)] = J.plan.rfwd_M[e];
             cur_job = jid;
         }
-        const u64* src = l1 ? J.Y + ((size_t)col << J.plan.log_n) + ((size_t)k1 << l2)
-                            : J.x + ((size_t)col << J.plan.log_n);
-        for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[sw(e)] = __ldcs(src + e);
-        __syncthreads();
-        dft_dif<true, false>(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
+        if (J.mode == kLdeFromCoeffs) {
+            // Position t takes the coefficient a_{k1 + n1*bitrev(t)} (stride n1
+            // in the natural-order table; the CTAs of neighbouring k1 share
+            // its sectors through L2).
+            const u64* src = J.x + ((size_t)col << J.plan.log_n) + k1;
+            for (u32 t = threadIdx.x; t < n2; t += blockDim.x)
+                stage[sw(t)] = __ldg(src + ((size_t)gl::bitrev(t, l2) << l1));
+            __syncthreads();
+        } else {
+            const u64* src = l1 ? J.Y + ((size_t)col << J.plan.log_n) + ((size_t)k1 << l2)
+                                : J.x + ((size_t)col << J.plan.log_n);
+            for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[sw(e)] = __ldcs(src + e);
+            __syncthreads();
+            dft_dif<true, false>(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
+            if (J.mode == kCoeffsOut) {
+                u64* dst = J.lde + ((size_t)col << J.plan.log_n) + k1;
+                for (u32 t = threadIdx.x; t < n2; t += blockDim.x)
+                    dst[(size_t)gl::bitrev(t, l2) << l1] = gl::mul(stage[sw(t)], J.cscale);
+                __syncthreads();
+                continue;
+            }
+        }
         const u64* sc = J.plan.scale + ((size_t)k1 << l2);
         // Scale by 7^j / n and spread for the zero-padded size-M transform.
         // In bit-reversed order over log M bits, coefficient k2 sits at
@@ -587,7 +605,7 @@ constexpr u32 kStageCCols = 4;
 
 u32 stage_c_items(const LdeJob& j, const Tiles&)
 {
-    if (!j.plan.log_n1) return 0;
+    if (!j.plan.log_n1 || j.mode == kCoeffsOut) return 0;
     u32 groups = (j.c + kStageCCols - 1) / kStageCCols;
     return groups * ((1u << j.plan.log_M) / j.c_qc);
 }
@@ -755,25 +773,35 @@ cudaError_t launch_validate(const u64* x, u64 count, u32* d_flag, cudaStream_t s
 }
 
 // Integer-pipe microbenchmark: each thread runs 8 independent chains of
-// multiply-adds, `iters` x 4 steps each.  WIDE: 32x32->64 products with a
+// multiply-adds, `iters` x 4 steps each, as inline PTX so that the compiler
+// cannot fold the chains algebraically.  WIDE: 32x32->64 products with a
 // 64-bit addend (mad.wide.u32); otherwise 32-bit multiply-adds (mad.lo.u32,
-// one IMAD lane each).  Block 0 records its clock64() span in out[0] so the
-// host can derive the SM clock of the run.
+// one IMAD lane each).  Block 0 records its SM clock rate (clock64 cycles
+// over globaltimer nanoseconds) in out[0] as cycles per 2^20 ns.
+__device__ __forceinline__ u64 global_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <bool WIDE>
 __global__ void k_int_peak(u64* out, u32 iters)
 {
     const long long c0 = clock64();
-    u32 a = threadIdx.x * 2654435761u + blockIdx.x;
+    const u64 t0 = global_ns();
+    const u32 m = (threadIdx.x * 2654435761u + blockIdx.x) | 1u;
     u64 x = 0;
     if (WIDE) {
         u64 acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; k++) acc[k] = (u64)(a + k) * 0x9E3779B9u;
+        for (int k = 0; k < 8; k++) acc[k] = (u64)(m + k) * 0x9E3779B9u;
         for (u32 i = 0; i < iters; i++) {
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
+            for (int rep = 0; rep < 4; rep++) {
 #pragma unroll
-                for (int rep = 0; rep < 4; rep++) acc[k] = (u64)(u32)acc[k] * (a | 1u) + acc[k];
+                for (int k = 0; k < 8; k++)
+                    asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[k]) : "r"((u32)acc[k]), "r"(m));
             }
         }
 #pragma unroll
@@ -781,19 +809,22 @@ __global__ void k_int_peak(u64* out, u32 iters)
     } else {
         u32 acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; k++) acc[k] = (a + k) * 0x9E3779B9u;
+        for (int k = 0; k < 8; k++) acc[k] = (m + k) * 0x9E3779B9u;
         for (u32 i = 0; i < iters; i++) {
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
+            for (int rep = 0; rep < 4; rep++) {
 #pragma unroll
-                for (int rep = 0; rep < 4; rep++) acc[k] = acc[k] * (a | 1u) + (u32)k;
+                for (int k = 0; k < 8; k++) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(acc[k]) : "r"(m), "r"(k));
             }
         }
 #pragma unroll
         for (int k = 0; k < 8; k++) x ^= acc[k];
     }
     if (x == 0x123456789ull) out[1 + blockIdx.x] = x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = (u64)(clock64() - c0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const u64 ns = global_ns() - t0;
+        out[0] = ns ? (u64)(clock64() - c0) * (1ull << 20) / ns : 0;
+    }
 }
 
 cudaError_t launch_int_peak(u64* out, int grid, int threads, u32 iters, int wide, cudaStream_t s)

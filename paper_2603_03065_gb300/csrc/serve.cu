@@ -1,11 +1,16 @@
 // Serving loop (continuous batching) for audit-commit requests.
 //
-// A scheduler thread admits queued requests in arrival order while their
-// footprint fits the HBM budget minus what is resident.  Each scheduler
-// pass fuses the admitted requests into one batched launch (one launch per
-// stage over all of them) on a free slot stream.  Up to max_inflight
-// batches overlap on the device.  Finished requests keep their LDE and tree
-// resident until v3c_release, for the later FRI and opening phases.
+// A scheduler thread admits queued requests while their footprint fits the
+// HBM budget minus what is resident.  Requests are batched by size class
+// (LDE elements): each scheduler pass takes the class whose oldest request
+// arrived first, fuses that class's queued requests (in arrival order) into
+// one batched launch (one launch per stage over all of them) and runs it on
+// a free slot, on the slot's stream for that class.  Small requests thus
+// never wait for the stages of large ones admitted beside them, and their
+// streams have the higher priority.  Up to max_inflight batches overlap on
+// the device; a class takes the last free slot only when no other class is
+// waiting.  Finished requests keep their LDE and tree resident until
+// v3c_release, for the later FRI and opening phases.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +24,12 @@ using namespace v3c::detail;
 using serve::Request;
 using serve::Server;
 using serve::Slot;
+
+int v3c::serve::size_class(const v3c_commit_desc& d)
+{
+    const u64 e = (u64)d.c << (d.log_n + d.rate_bits);
+    return e <= (16ull << 20) ? 0 : e <= (128ull << 20) ? 1 : 2;
+}
 
 namespace {
 
@@ -58,48 +69,17 @@ void reap(Server* S, bool wait)
             r.state = e == cudaSuccess ? V3C_REQ_DONE : V3C_REQ_FAILED;
             r.status = e == cudaSuccess ? V3C_OK : V3C_ECUDA;
             r.times.t_done = t;
-            S->reserved -= std::min(S->reserved, r.footprint);
         }
         sl.tickets.clear();
         sl.busy = false;
     }
 }
 
-// One scheduler pass: admit a batch into a free slot.  Returns true if a
-// batch was launched.  Caller holds S->mu.
-bool admit_and_launch(Server* S)
+// Stages the batch's inputs and launches it on `slot`, on the slot's stream
+// of size class k.  Caller holds S->mu.
+void launch_batch_on(Server* S, Slot* slot, int k, const std::vector<u64>& batch, size_t scratch, size_t staged,
+                     size_t copied)
 {
-    Slot* slot = nullptr;
-    for (auto& sl : S->slots)
-        if (!sl.busy) {
-            slot = &sl;
-            break;
-        }
-    if (!slot || S->queue.empty()) return false;
-    const v3c_config& cfg = ctx_config(S->ctx);
-    u64 budget = cfg.hbm_budget_bytes;
-    u64 resident = ctx_resident(S->ctx);
-    std::vector<u64> batch;
-    size_t scratch = 0, staged = 0, copied = 0;
-    u64 reserve = 0;
-    u32 max_batch = S->cfg.max_batch ? S->cfg.max_batch : 32;
-    const u64 slot_cap = S->cfg.slot_scratch_bytes ? S->cfg.slot_scratch_bytes : (16ull << 30);
-    while (!S->queue.empty() && batch.size() < max_batch) {
-        Request& r = S->reqs[S->queue.front()];
-        if (resident + S->reserved + reserve + r.footprint > budget) break;  // FIFO: wait for memory
-        size_t sw = lde_scratch_words_s(r.desc.c, r.desc.log_n, r.desc.rate_bits);
-        size_t iw = r.desc.on_device == V3C_INPUT_DEVICE ? 0 : (size_t)r.desc.c << r.desc.log_n;
-        // A pass takes at least one request; more only while its scratch
-        // and staged inputs stay within the slot cap.
-        if (!batch.empty() && (scratch + staged + sw + iw) * 8 > slot_cap) break;
-        reserve += r.footprint;
-        scratch += sw;
-        staged += iw;
-        if (r.desc.on_device == V3C_INPUT_HOST_COPY) copied += iw;
-        batch.push_back(r.ticket);
-        S->queue.pop_front();
-    }
-    if (batch.empty()) return false;
     double t = now_s();
     // Slot buffers grow on demand while the slot is idle.
     size_t need = scratch + staged;
@@ -143,12 +123,13 @@ bool admit_and_launch(Server* S)
         if (d.on_device == V3C_INPUT_HOST_BORROW) d.on_device = V3C_INPUT_HOST_COPY;  // caller's pinned memory
         descs.push_back(d);
     }
+    cudaStream_t stream = slot->streams[k];
     if (!st) {
         std::vector<u64> ids(batch.size());
         std::lock_guard<std::mutex> g(ctx_mutex(S->ctx));
-        st = commit_locked(S->ctx, descs.data(), (u32)descs.size(), ids.data(), slot->stream, slot->arena,
+        st = commit_locked(S->ctx, descs.data(), (u32)descs.size(), ids.data(), stream, slot->arena,
                            slot->arena_words, batch.data(), /*allow_graph=*/false);  // mixes rarely repeat
-        if (!st && cudaEventRecord(slot->done, slot->stream) != cudaSuccess) st = V3C_ECUDA;
+        if (!st && cudaEventRecord(slot->done, stream) != cudaSuccess) st = V3C_ECUDA;
     }
     double t2 = now_s();
     for (u64 tk : batch) {
@@ -165,12 +146,89 @@ bool admit_and_launch(Server* S)
         }
     }
     if (!st) {
+        // Footprint is counted as resident by the context from here on.
         slot->busy = true;
+        slot->stream = stream;
+        slot->cls = k;
         slot->tickets = batch;
-        // Footprint is now counted as resident by the context.
     }
-    (void)reserve;
-    return true;
+}
+
+// A request older than this that does not fit the budget stops the
+// admission of newer requests of the other classes, so that a stream of
+// small requests cannot keep a large one waiting for memory forever.
+constexpr double kStarveS = 0.25;
+
+// One scheduler pass: admit one batch into a free slot.  Returns true if a
+// batch was launched.  Caller holds S->mu.
+bool admit_and_launch(Server* S)
+{
+    int nfree = 0;
+    Slot* slot = nullptr;
+    for (auto& sl : S->slots)
+        if (!sl.busy) {
+            nfree++;
+            if (!slot) slot = &sl;
+        }
+    if (!slot || S->queue.empty()) return false;
+    const v3c_config& cfg = ctx_config(S->ctx);
+    const u64 budget = cfg.hbm_budget_bytes;
+    const u64 resident = ctx_resident(S->ctx);
+    // Classes in the order of their oldest queued request.
+    int order[serve::kSizeClasses], norder = 0;
+    bool seen[serve::kSizeClasses] = {false, false, false};
+    for (u64 tk : S->queue) {
+        const int k = serve::size_class(S->reqs[tk].desc);
+        if (!seen[k]) {
+            seen[k] = true;
+            order[norder++] = k;
+            if (norder == serve::kSizeClasses) break;
+        }
+    }
+    const Request& head = S->reqs[S->queue.front()];
+    const int head_cls = serve::size_class(head.desc);
+    const bool head_starved = resident + head.footprint > budget &&
+                              now_s() - head.times.t_submit > kStarveS;
+    const u32 max_batch = S->cfg.max_batch ? S->cfg.max_batch : 32;
+    const u64 slot_cap = S->cfg.slot_scratch_bytes ? S->cfg.slot_scratch_bytes : (16ull << 30);
+    for (int oi = 0; oi < norder; oi++) {
+        const int k = order[oi];
+        if (head_starved && k != head_cls) continue;
+        // The last free slot goes to the class that has waited longest.
+        if (nfree == 1 && oi > 0) continue;
+        std::vector<u64> batch;
+        size_t scratch = 0, staged = 0, copied = 0;
+        u64 reserve = 0;
+        for (u64 tk : S->queue) {
+            if (batch.size() >= max_batch) break;
+            Request& r = S->reqs[tk];
+            if (serve::size_class(r.desc) != k) continue;
+            if (resident + reserve + r.footprint > budget) break;  // FIFO within the class
+            size_t sw = lde_scratch_words_s(r.desc.c, r.desc.log_n, r.desc.rate_bits);
+            size_t iw = r.desc.on_device == V3C_INPUT_DEVICE ? 0 : (size_t)r.desc.c << r.desc.log_n;
+            // A pass takes at least one request; more only while its scratch
+            // and staged inputs stay within the slot cap.
+            if (!batch.empty() && (scratch + staged + sw + iw) * 8 > slot_cap) break;
+            reserve += r.footprint;
+            scratch += sw;
+            staged += iw;
+            if (r.desc.on_device == V3C_INPUT_HOST_COPY) copied += iw;
+            batch.push_back(tk);
+        }
+        if (batch.empty()) continue;
+        {   // take the batch out of the queue, keeping the rest in order
+            std::deque<u64> rest;
+            size_t bi = 0;
+            for (u64 tk : S->queue) {
+                if (bi < batch.size() && tk == batch[bi]) bi++;
+                else rest.push_back(tk);
+            }
+            S->queue.swap(rest);
+        }
+        launch_batch_on(S, slot, k, batch, scratch, staged, copied);
+        return true;
+    }
+    return false;
 }
 
 void run(Server* S)
@@ -218,13 +276,26 @@ v3c_status v3c_serve_start(v3c_ctx* ctx, const v3c_serve_cfg* cfg)
     if (!srv->cfg.max_batch) srv->cfg.max_batch = 32;
     u32 inflight = srv->cfg.max_inflight ? srv->cfg.max_inflight : ctx_config(ctx).max_inflight;
     srv->slots.resize(std::max(inflight, 1u));
+    // Stream priorities by size class: class 0 (small) the greatest, class 2
+    // the least (numerically larger is lower priority).
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    const int prio[serve::kSizeClasses] = {greatest, (least + greatest) / 2, least};
+    bool ok = true;
     for (auto& sl : srv->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            delete srv;
-            return ctx_fail(ctx, V3C_ECUDA, "serve: stream creation failed");
+        for (int k = 0; k < serve::kSizeClasses; k++)
+            ok = ok && cudaStreamCreateWithPriority(&sl.streams[k], cudaStreamNonBlocking, prio[k]) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        for (auto& sl : srv->slots) {
+            for (auto st : sl.streams)
+                if (st) cudaStreamDestroy(st);
+            if (sl.done) cudaEventDestroy(sl.done);
         }
+        delete srv;
+        return ctx_fail(ctx, V3C_ECUDA, "serve: stream creation failed");
     }
     S = srv;
     srv->th = std::thread(run, srv);
@@ -306,11 +377,13 @@ v3c_status v3c_serve_stop(v3c_ctx* ctx)
     }
     if (S->th.joinable()) S->th.join();
     for (auto& sl : S->slots) {
-        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        for (auto st : sl.streams)
+            if (st) cudaStreamSynchronize(st);
         if (sl.arena) cudaFree(sl.arena);
         if (sl.pinned) cudaFreeHost(sl.pinned);
         if (sl.done) cudaEventDestroy(sl.done);
-        if (sl.stream) cudaStreamDestroy(sl.stream);
+        for (auto st : sl.streams)
+            if (st) cudaStreamDestroy(st);
     }
     delete S;
     S = nullptr;

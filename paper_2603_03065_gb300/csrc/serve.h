@@ -29,8 +29,18 @@ struct Request {
     u64 footprint = 0;
 };
 
+// Requests are batched within size classes (LDE elements c * 2^(log_n + r):
+// class 0 up to 2^24, class 1 up to 2^27, class 2 above), so that a batch of
+// small requests completes apart from the large ones admitted beside it.
+constexpr int kSizeClasses = 3;
+int size_class(const v3c_commit_desc& d);
+
 struct Slot {
-    cudaStream_t stream = nullptr;
+    // One stream per size class, with the class's priority (small requests
+    // highest); a batch runs on the stream of its class.
+    cudaStream_t streams[kSizeClasses] = {nullptr, nullptr, nullptr};
+    cudaStream_t stream = nullptr;  // stream of the batch in flight
+    int cls = -1;                   // its size class
     cudaEvent_t done = nullptr;
     u64* arena = nullptr;        // device scratch + staged inputs of the batch
     size_t arena_words = 0;
@@ -51,7 +61,6 @@ struct Server {
     std::vector<Slot> slots;
     bool stop = false;
     bool crashed = false;
-    u64 reserved = 0;  // footprint of admitted but not yet resident requests
 };
 
 }  // namespace serve

@@ -16,6 +16,7 @@
 
 #include "../../include/v3c.h"
 #include "ctx.h"
+#include "gl.cuh"
 #include "internal.h"
 #include "serve.h"
 
@@ -104,10 +105,13 @@ cudaEvent_t pool_event(v3c_ctx* ctx)
     return e;
 }
 
-// Plan tables of a shape, built once and kept.  Caller holds ctx->mu.
-v3c_status get_plan(v3c_ctx* ctx, u32 log_n, u32 r, cudaStream_t s, Plan* out)
+// Plan tables of a shape, built once and kept.  The coset is 7 * gshift *
+// <w_N> and the scale table carries sfac (0 = n^-1, the LDE of columns).
+// Caller holds ctx->mu.
+v3c_status get_plan(v3c_ctx* ctx, u32 log_n, u32 r, cudaStream_t s, Plan* out, u64 gshift = 1, u64 sfac = 0)
 {
-    auto key = std::make_pair(log_n, r);
+    if (!sfac) sfac = gl::h_inv(((u64)1 << log_n) % gl::P);
+    auto key = std::make_tuple(log_n, r, gshift, sfac);
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         *out = it->second.plan;
@@ -118,6 +122,8 @@ v3c_status get_plan(v3c_ctx* ctx, u32 log_n, u32 r, cudaStream_t s, Plan* out)
     CK(cudaMalloc(&pe.mem, words * sizeof(u64)));
     pe.plan.log_n = log_n;
     pe.plan.r = r;
+    pe.plan.gshift = gshift;
+    pe.plan.sfac = sfac;
     cudaError_t e = build_plan_tables(pe.plan, pe.mem, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -337,8 +343,8 @@ static std::string batch_signature(const Batch& b, const Tiles& t)
              b.h_threads ? b.h_threads : t.h_threads, t.m_threads, (int)b.leaves_ready);
     k += buf;
     for (auto& j : b.lde) {
-        snprintf(buf, sizeof buf, "L%u.%u.%u.%u.%u.%u.%u.%u.%u|", j.c, j.ld, j.plan.log_n, j.plan.r, j.vec_ok, j.a_cols,
-                 j.c_q, j.c_qc, j.kcap);
+        snprintf(buf, sizeof buf, "L%u.%u.%u.%u.%u.%u.%u.%u.%u.%u|", j.c, j.ld, j.plan.log_n, j.plan.r, j.vec_ok,
+                 j.a_cols, j.c_q, j.c_qc, j.kcap, j.mode);
         k += buf;
     }
     for (auto& j : b.tree) {
@@ -1011,6 +1017,142 @@ v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v
     return commit_locked(ctx, descs, nb, ids, (cudaStream_t)stream, nullptr, 0, nullptr);
 }
 
+v3c_status v3c_coeffs(v3c_ctx* ctx, const uint64_t* d_cols, uint32_t c, uint32_t log_n, uint64_t* d_coeffs,
+                      void* stream)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (!d_cols || !d_coeffs) return fail(ctx, V3C_EINVAL, "v3c_coeffs: NULL pointer");
+    if (!shape_ok(c, log_n, 0)) return fail(ctx, V3C_EINVAL, "v3c_coeffs: bad shape c=%u log_n=%u", c, log_n);
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    // The inverse stages of the rate-3 plan of this size (its split keeps
+    // stage B's inverse transform at n2 <= 2^10).
+    const u32 r = std::min(3u, (u32)V3C_MAX_LOG_LDE - log_n);
+    u32 l1, l2;
+    plan_split(log_n, r, l1, l2);
+    const size_t words = l1 ? (size_t)c << log_n : 0;  // Y only
+    u64* scratch = nullptr;
+    if (words) {
+        st = arena_acquire(ctx, words, s, &scratch);
+        if (st) return st;
+    }
+    LdeJob j;
+    memset(&j, 0, sizeof j);
+    st = get_plan(ctx, log_n, r, s, &j.plan);
+    if (st) return st;
+    j.x = d_cols;
+    j.c = c;
+    j.ld = c;
+    j.wcols = c;
+    j.lde = d_coeffs;
+    j.Y = scratch;
+    j.mode = kCoeffsOut;
+    j.cscale = gl::h_inv(((u64)1 << log_n) % gl::P);
+    job_tiles(j);
+    Batch b;
+    b.lde.push_back(j);
+    st = launch_batch(ctx, b, s);
+    if (st) return st;
+    if (words) return arena_release(ctx, s);
+    return V3C_OK;
+}
+
+v3c_status v3c_commit_part(v3c_ctx* ctx, const v3c_part_desc* d, v3c_commit_id* id, void* stream)
+{
+    if (!ctx) return V3C_EINVAL;
+    if (!d || !id || !d->coeffs) return fail(ctx, V3C_EINVAL, "v3c_commit_part: NULL pointer");
+    if (!shape_ok(d->c, d->log_n, d->rate_bits) || d->log_parts > d->rate_bits || d->log_parts > d->cap_height ||
+        (d->part >> d->log_parts) || d->cap_height > d->log_n + d->rate_bits)
+        return fail(ctx, V3C_EINVAL, "v3c_commit_part: bad desc (c=%u log_n=%u r=%u h=%u log_parts=%u part=%u)", d->c,
+                    d->log_n, d->rate_bits, d->cap_height, d->log_parts, d->part);
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    // Part q holds rows [q N/G, (q+1) N/G): the evaluations on the coset
+    // 7 w_N^kappa <w_{N/G}>, kappa = bitrev_{log G}(q), in bit-reversed order.
+    const u32 rp = d->rate_bits - d->log_parts, hp = d->cap_height - d->log_parts;
+    const u32 logN = d->log_n + d->rate_bits, logNp = d->log_n + rp;
+    const u64 kappa = gl::bitrev(d->part, d->log_parts);
+    const u64 gshift = gl::h_pow(gl::h_root(logN), kappa);
+    const size_t need = v3c_commit_footprint(d->c, d->log_n, rp, hp);
+    if (ctx->resident + need > ctx->cfg.hbm_budget_bytes)
+        return fail(ctx, V3C_ENOMEM, "v3c_commit_part: %zu bytes requested, %zu resident, budget %llu", need,
+                    ctx->resident, (unsigned long long)ctx->cfg.hbm_budget_bytes);
+    u32 l1, l2;
+    plan_split(d->log_n, rp, l1, l2);
+    const size_t words = l1 ? (size_t)d->c << logNp : 0;  // Z only
+    u64* scratch = nullptr;
+    if (words) {
+        st = arena_acquire(ctx, words, s, &scratch);
+        if (st) return st;
+    }
+    Object o;
+    o.c = d->c;
+    o.ld = d->c + (d->c & 1);
+    o.log_n = d->log_n;
+    o.r = rp;
+    o.h = hp;
+    o.bytes = need;
+    const size_t Np = (size_t)1 << logNp;
+    const size_t tw = (2 * Np - ((size_t)2 << hp)) * 4;
+    cudaError_t e = cudaMallocAsync((void**)&o.lde, Np * o.ld * 8, s);
+    if (e == cudaSuccess && tw) e = cudaMallocAsync((void**)&o.tree, tw * 8, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&o.cap, ((size_t)4 << hp) * 8, s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&o.done, cudaEventDisableTiming);
+    auto rollback = [&]() {
+        if (o.lde) cudaFreeAsync(o.lde, s);
+        if (o.tree) cudaFreeAsync(o.tree, s);
+        if (o.cap) cudaFreeAsync(o.cap, s);
+        if (o.done) cudaEventDestroy(o.done);
+    };
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rollback();
+        return fail(ctx, V3C_ENOMEM, "v3c_commit_part: allocation of %zu bytes failed: %s", need,
+                    cudaGetErrorString(e));
+    }
+    LdeJob j;
+    memset(&j, 0, sizeof j);
+    st = get_plan(ctx, d->log_n, rp, s, &j.plan, gshift, 1);
+    if (st) {
+        rollback();
+        return st;
+    }
+    j.x = d->coeffs;
+    j.c = d->c;
+    j.ld = o.ld;
+    j.wcols = o.ld;
+    j.lde = o.lde;
+    j.vec_ok = 1;
+    j.Z = scratch;
+    j.mode = kLdeFromCoeffs;
+    job_tiles(j);
+    auto it = ctx->tuned.find(std::make_pair(d->log_n, rp));
+    if (it != ctx->tuned.end()) lde_job_apply_tune(j, it->second);
+    Batch b;
+    b.lde.push_back(j);
+    b.tree.push_back(make_tree_job(o.lde, o.ld, d->c, logNp, hp, o.tree, o.cap));
+    st = launch_batch(ctx, b, s);
+    if (st) {
+        rollback();
+        return st;
+    }
+    if (words) {
+        st = arena_release(ctx, s);
+        if (st) return st;
+    }
+    CK(cudaEventRecord(o.done, s));
+    o.stream = s;
+    o.id = ctx->next_id++;
+    ctx->resident += o.bytes;
+    *id = o.id;
+    ctx->objects[o.id] = o;
+    return V3C_OK;
+}
+
 v3c_status v3c_commit_buffers(v3c_ctx* ctx, v3c_commit_id id, uint64_t** d_lde, uint32_t* ld, uint64_t** d_tree,
                               uint64_t** d_cap, uint32_t* log_rows, uint32_t* cap_height)
 {
@@ -1154,12 +1296,12 @@ v3c_status v3c_int_pipe_rate(v3c_ctx* ctx, uint32_t kind, uint32_t reps, double*
         CK(cudaEventSynchronize(b));
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, a, b));
-        u64 cycles = 0;
-        CK(cudaMemcpy(&cycles, out, 8, cudaMemcpyDeviceToHost));
+        u64 rate20 = 0;  // SM cycles per 2^20 ns, seen by block 0
+        CK(cudaMemcpy(&rate20, out, 8, cudaMemcpyDeviceToHost));
         double ops = (double)grid * threads * iters * 8 * 4;
         if (r > 0 && ops / (ms * 1e-3) > best) {
             best = ops / (ms * 1e-3);
-            best_mhz = (double)cycles / (ms * 1e3);
+            best_mhz = (double)rate20 / (double)(1u << 20) * 1e3;
         }
     }
     cudaEventDestroy(a);
