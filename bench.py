@@ -648,7 +648,7 @@ SERVE_WARM_S = 3.0
 
 
 def serving_block(rate: float | None, duration: float, max_batch: int = 32, inflight: int = 4,
-                  load: float = 1.1) -> dict:
+                  load: float = 1.0) -> dict:
     """C5: Poisson arrivals (seed 5) of commits drawn from the mixture 50 %
     2^14 x 80, 35 % 2^16 x 135, 15 % 2^18 x 135 (rate 3, cap 4), served by
     the continuous-batching loop from pinned host inputs (borrowed, copied at
@@ -1242,7 +1242,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the serving and batched blocks after the timed region")
     ap.add_argument("--serve-duration", type=float, default=20.0, help="default line's serving block: seconds")
-    ap.add_argument("--serve-load", type=float, default=1.1,
+    ap.add_argument("--serve-load", type=float, default=1.0,
                     help="default line's serving block: arrival rate as a multiple of the serial capacity")
     ap.add_argument("--rate", type=float, default=200.0, help="serve_poisson: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve_poisson: trace length in seconds")

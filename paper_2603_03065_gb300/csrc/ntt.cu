@@ -384,7 +384,9 @@ __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, 
     for (u32 s = 0; s < logL;) {
         u32 k = min(kmax, logL - s);
         // 1024-point transforms (n1 = n2 = 2^10 plans) in radix 16 or 4.
-        if (logL == 10 && k == 4 && s == 0) dif_pass<4, INV, FULL, 10, 0>(a, B, logL, s, tw);
+        if (logL == 10 && k == 5 && s == 0) dif_pass<5, INV, FULL, 10, 0>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 5 && s == 5) dif_pass<5, INV, FULL, 10, 5>(a, B, logL, s, tw);
+        else if (logL == 10 && k == 4 && s == 0) dif_pass<4, INV, FULL, 10, 0>(a, B, logL, s, tw);
         else if (logL == 10 && k == 4 && s == 4) dif_pass<4, INV, FULL, 10, 4>(a, B, logL, s, tw);
         else if (logL == 10 && k == 2 && s == 8) dif_pass<2, INV, FULL, 10, 8>(a, B, logL, s, tw);
         else if (logL == 10 && k == 2 && s == 0) dif_pass<2, INV, FULL, 10, 0>(a, B, logL, s, tw);
@@ -392,6 +394,7 @@ __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, 
         else if (logL == 10 && k == 2 && s == 4) dif_pass<2, INV, FULL, 10, 4>(a, B, logL, s, tw);
         else if (logL == 10 && k == 2 && s == 6) dif_pass<2, INV, FULL, 10, 6>(a, B, logL, s, tw);
         else switch (k) {
+        case 5: dif_pass<5, INV, FULL>(a, B, logL, s, tw); break;
         case 4: dif_pass<4, INV, FULL>(a, B, logL, s, tw); break;
         case 3: dif_pass<3, INV, FULL>(a, B, logL, s, tw); break;
         case 2: dif_pass<2, INV, FULL>(a, B, logL, s, tw); break;
@@ -570,18 +573,14 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
         dft_dit<false>(data, 1, lM, twf, r, J.kcap + 1);  // the forward M-point transform may use radix 2^5
         if (l1) {
             // Z is q-blocked: block q >> lQ holds [k1][q & (Q-1)], so that
-            // stage C reads one contiguous run per column.
+            // stage C reads one contiguous run per column.  The four-step
+            // twiddle w_N^(k1 q) is applied by stage C, where one twiddle
+            // serves the four columns of a CTA.
             u64* Z = J.Z + ((size_t)col << J.plan.log_N);
             const u32 Q = J.c_q, lQ = __ffs(Q) - 1;
-            // Twiddle w_N^(k1 q) for q = tid + i * blockDim: start at
-            // w_N^(k1 tid) and step by w_N^(k1 blockDim), exact in F_p.
-            const u64 N_mask = ((u64)1 << J.plan.log_N) - 1;
-            u64 tw = pow_wN(J.plan.pw_N, ((u64)k1 * threadIdx.x) & N_mask);
-            const u64 step = pow_wN(J.plan.pw_N, ((u64)k1 * blockDim.x) & N_mask);
             for (u32 q = threadIdx.x; q < M; q += blockDim.x) {
                 size_t idx = ((size_t)(q >> lQ) << (l1 + lQ)) + ((size_t)k1 << lQ) + (q & (Q - 1));
-                __stcs(Z + idx, gl::mul(data[sw(q)], tw));
-                tw = gl::mul(tw, step);
+                __stcs(Z + idx, data[sw(q)]);
             }
         } else {
             // n1 = 1: this CTA holds the whole column; write committed rows.
@@ -617,7 +616,56 @@ size_t stage_c_smem(const LdeJob& j, const Tiles&)
     return (kStageCCols * j.c_qc * n1 + n1) * sizeof(u64);
 }
 
-__global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
+// Stage C load with the four-step twiddle, for n1 = JN * blockDim (256) and
+// Q = 8 / JN q values per CTA (the default tiles of n1 >= 256).  Thread t
+// takes k1 = t + 256 j (j < JN) and every v < Q, so it needs the eight
+// twiddles w_N^(k1 (q0 + v)): per v a start w_N^(t (q0 + v)) and a step
+// w_N^(256 (q0 + v)), then a multiplicative chain over j, exact in F_p
+// (1.75 products per twiddle; each twiddle serves the CTA's four columns).
+// Pairs of adjacent v are read as one 16-byte load.
+template <u32 JN>
+__device__ __forceinline__ void stage_c_load(const LdeJob& J, u64* data, u32 cg, u32 q0, u32 qb, u32 qoff)
+{
+    constexpr u32 Q = 8 / JN;
+    const u32 l1 = J.plan.log_n1, lQz = __ffs(J.c_q) - 1;
+    const u64 N_mask = ((u64)1 << J.plan.log_N) - 1;
+    u64 tz[8];  // tz[v * JN + j]
+#pragma unroll
+    for (u32 v = 0; v < Q; v++) {
+        const u64 q = q0 + v;
+        u64 t = pow_wN(J.plan.pw_N, ((u64)threadIdx.x * q) & N_mask);
+        const u64 step = JN > 1 ? pow_wN(J.plan.pw_N, ((u64)blockDim.x * q) & N_mask) : 0;
+#pragma unroll
+        for (u32 j = 0; j < JN; j++) {
+            tz[v * JN + j] = t;
+            if (j + 1 < JN) t = gl::mul(t, step);
+        }
+    }
+#pragma unroll
+    for (u32 w = 0; w < kStageCCols; w++) {
+        const u32 col = kStageCCols * cg + w;
+        const bool live = col < J.c;
+        const u64* src = J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQz)) + qoff;
+#pragma unroll
+        for (u32 j = 0; j < JN; j++) {
+            const u32 k1 = threadIdx.x + blockDim.x * j;
+            const u64* p = src + ((size_t)k1 << lQz);
+            if (Q == 1) {
+                const u64 x = live ? __ldcs(p) : 0;
+                data[sw((w << l1) + k1)] = gl::mul(x, tz[j]);
+            } else {
+#pragma unroll
+                for (u32 v = 0; v < Q; v += 2) {
+                    ulonglong2 x = live ? __ldcs(reinterpret_cast<const ulonglong2*>(p + v)) : make_ulonglong2(0, 0);
+                    data[sw(((w * Q + v) << l1) + k1)] = gl::mul(x.x, tz[v * JN + j]);
+                    data[sw(((w * Q + v + 1) << l1) + k1)] = gl::mul(x.y, tz[(v + 1) * JN + j]);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
     u32 cur_job = 0xFFFFFFFFu;
@@ -640,22 +688,36 @@ __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ j
             cur_job = jid;
         }
         // Block qb of each column is one contiguous run of n1*Qz words, [k1][v];
-        // this CTA takes v in [qoff, qoff + Q).
+        // this CTA takes v in [qoff, qoff + Q), times the four-step twiddle
+        // w_N^(k1 (q0 + v)).
         const u32 per = Q << l1;
-        for (u32 e = threadIdx.x; e < kStageCCols * per; e += blockDim.x) {
-            u32 w = e >> (l1 + lQ), rem = e & (per - 1);
-            u32 v = rem & (Q - 1), k1 = rem >> lQ;
-            u32 col = kStageCCols * cg + w;
-            u64* dst = data + sw(((w * Q + v) << l1) + k1);
-            if (col < J.c)
-                cp_async8(dst, J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQz)) +
-                                   ((size_t)k1 << lQz) + qoff + v);
-            else
-                *dst = 0;
+        const u64 N_mask = ((u64)1 << J.plan.log_N) - 1;
+        const u32 Jn = n1 / blockDim.x;
+        // The fast path's 16-byte loads need Z 16-byte aligned (every offset
+        // added to it is an even number of words).
+        if (n1 >= blockDim.x && per == 8 * blockDim.x && blockDim.x == 256 && ((uintptr_t)J.Z & 15) == 0) {
+            switch (Jn) {
+            case 1: stage_c_load<1>(J, data, cg, q0, qb, qoff); break;
+            case 2: stage_c_load<2>(J, data, cg, q0, qb, qoff); break;
+            case 4: stage_c_load<4>(J, data, cg, q0, qb, qoff); break;
+            default: stage_c_load<8>(J, data, cg, q0, qb, qoff); break;
+            }
+        } else {
+            for (u32 e = threadIdx.x; e < kStageCCols * per; e += blockDim.x) {
+                u32 w = e >> (l1 + lQ), rem = e & (per - 1);
+                u32 v = rem & (Q - 1), k1 = rem >> lQ;
+                u32 col = kStageCCols * cg + w;
+                u64 x = 0;
+                if (col < J.c) {
+                    x = __ldcs(J.Z + ((size_t)col << J.plan.log_N) + ((size_t)qb << (l1 + lQz)) +
+                               ((size_t)k1 << lQz) + qoff + v);
+                    x = gl::mul(x, pow_wN(J.plan.pw_N, ((u64)k1 * (q0 + v)) & N_mask));
+                }
+                data[sw(((w * Q + v) << l1) + k1)] = x;
+            }
         }
-        cp_async_wait_all();
         __syncthreads();
-        dft_dif<false, true>(data, kStageCCols * Q, l1, tw, J.kcap);
+        dft_dif<false, true>(data, kStageCCols * Q, l1, tw, min(J.kcap + 1, 5u));
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
@@ -807,14 +869,20 @@ __global__ void k_int_peak(u64* out, u32 iters)
 #pragma unroll
         for (int k = 0; k < 8; k++) x ^= acc[k];
     } else {
+        // new[k] = old[k] * old[k+1] + m: a product of two chain values, so
+        // no step can be folded into the next.
         u32 acc[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) acc[k] = (m + k) * 0x9E3779B9u;
         for (u32 i = 0; i < iters; i++) {
 #pragma unroll
             for (int rep = 0; rep < 4; rep++) {
+                u32 nxt[8];
 #pragma unroll
-                for (int k = 0; k < 8; k++) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(acc[k]) : "r"(m), "r"(k));
+                for (int k = 0; k < 8; k++)
+                    asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nxt[k]) : "r"(acc[k]), "r"(acc[(k + 1) & 7]), "r"(m));
+#pragma unroll
+                for (int k = 0; k < 8; k++) acc[k] = nxt[k];
             }
         }
 #pragma unroll

@@ -225,7 +225,7 @@ bool admit_and_launch(Server* S)
             }
             S->queue.swap(rest);
         }
-        launch_batch_on(S, slot, k, batch, scratch, staged, copied);
+        launch_batch_on(S, slot, k, batch, scratch + arena_padding((u32)batch.size()), staged, copied);
         return true;
     }
     return false;

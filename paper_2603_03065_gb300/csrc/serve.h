@@ -66,6 +66,14 @@ struct Server {
 }  // namespace serve
 
 namespace detail {
+}  // namespace detail
+}  // namespace v3c
+
+// Arena words a batched commit of nb descs adds for block alignment.
+size_t arena_padding(v3c::u32 nb);
+
+namespace v3c {
+namespace detail {
 v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64* ids, cudaStream_t s,
                          u64* arena_override, size_t arena_words, const u64* preassigned_ids,
                          bool allow_graph = true);

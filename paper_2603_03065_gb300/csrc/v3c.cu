@@ -414,6 +414,19 @@ static bool shape_ok(u32 c, u32 log_n, u32 r)
     return c >= 1 && log_n <= V3C_MAX_LOG_N && r <= V3C_MAX_RATE_BITS && log_n + r <= V3C_MAX_LOG_LDE;
 }
 
+constexpr size_t kArenaAlign = 32;  // words (256 bytes)
+static size_t align_words(size_t w) { return (w + kArenaAlign - 1) & ~(kArenaAlign - 1); }
+
+}  // namespace detail
+}  // namespace v3c
+
+// Alignment slack of a batch's arena: each desc takes at most two blocks
+// per column chunk (staged input, scratch) plus two unchunked.
+size_t arena_padding(v3c::u32 nb) { return (size_t)nb * (2 * kCopyChunks + 2) * v3c::detail::kArenaAlign; }
+
+namespace v3c {
+namespace detail {
+
 static size_t lde_scratch_words(u32 c, u32 log_n, u32 r)
 {
     u32 l1, l2;
@@ -812,7 +825,9 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         }
     }
     u64* arena = nullptr;
-    size_t arena_need = scratch + staged;
+    // Every staged input and scratch block starts on a 256-byte boundary
+    // (kArenaAlign words), so the kernels' vector accesses stay aligned.
+    size_t arena_need = scratch + staged + arena_padding(nb);
     v3c_status st;
     if (arena_need) {
         if (arena_override) {
@@ -879,10 +894,10 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
             for (u32 c0 = 0; c0 < d.c; c0 += per) {
                 const u32 ck = std::min(per, d.c - c0);
                 u64* dst = arena + aoff;
-                aoff += (size_t)ck * n;
+                aoff = align_words(aoff + (size_t)ck * n);
                 size_t sw = lde_scratch_words(ck, d.log_n, d.rate_bits);
                 u64* scr = sw ? arena + aoff : nullptr;
-                aoff += sw;
+                aoff = align_words(aoff + sw);
                 cudaError_t e = cudaMemcpyAsync(dst, d.cols + (size_t)c0 * n, (size_t)ck * n * 8,
                                                 cudaMemcpyHostToDevice, ctx->copy_stream);
                 const size_t g = b.chunks.size();
@@ -920,7 +935,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         }
         if (d.on_device != V3C_INPUT_DEVICE) {
             u64* dst = arena + aoff;
-            aoff += d.c * n;
+            aoff = align_words(aoff + d.c * n);
             cudaError_t e = cudaMemcpyAsync(dst, d.cols, d.c * n * 8, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) {
                 rollback(nb);
@@ -930,7 +945,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         }
         size_t sw = lde_scratch_words(d.c, d.log_n, d.rate_bits);
         u64* scr = sw ? arena + aoff : nullptr;
-        aoff += sw;
+        aoff = align_words(aoff + sw);
         LdeJob j;
         st = make_lde_job(ctx, x, d.c, d.log_n, d.rate_bits, o.lde, o.ld, scr, s, &j);
         if (st) {
