@@ -376,16 +376,17 @@ __device__ __forceinline__ u32 pass_k(u32 B, u32 logL, u32 kcap)
 }
 
 // INV: tw holds w_L^-i and the in-register DFTs use the inverse roots.
-// FULL: tw holds all L powers (else the first L/2).
-template <bool INV, bool FULL>
+// FULL: tw holds all L powers (else the first L/2).  MAXK: the largest
+// radix exponent compiled in (5 needs 32 values per thread in registers).
+template <bool INV, bool FULL, int MAXK = 4>
 __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, u32 kcap)
 {
-    const u32 kmax = pass_k(B, logL, kcap);
+    const u32 kmax = pass_k(B, logL, min(kcap, (u32)MAXK));
     for (u32 s = 0; s < logL;) {
         u32 k = min(kmax, logL - s);
-        // 1024-point transforms (n1 = n2 = 2^10 plans) in radix 16 or 4.
-        if (logL == 10 && k == 5 && s == 0) dif_pass<5, INV, FULL, 10, 0>(a, B, logL, s, tw);
-        else if (logL == 10 && k == 5 && s == 5) dif_pass<5, INV, FULL, 10, 5>(a, B, logL, s, tw);
+        // 1024-point transforms (n1 = n2 = 2^10 plans) in radix 32, 16 or 4.
+        if (MAXK >= 5 && logL == 10 && k == 5 && s == 0) dif_pass<(MAXK >= 5 ? 5 : 1), INV, FULL, 10, 0>(a, B, logL, s, tw);
+        else if (MAXK >= 5 && logL == 10 && k == 5 && s == 5) dif_pass<(MAXK >= 5 ? 5 : 1), INV, FULL, 10, 5>(a, B, logL, s, tw);
         else if (logL == 10 && k == 4 && s == 0) dif_pass<4, INV, FULL, 10, 0>(a, B, logL, s, tw);
         else if (logL == 10 && k == 4 && s == 4) dif_pass<4, INV, FULL, 10, 4>(a, B, logL, s, tw);
         else if (logL == 10 && k == 2 && s == 8) dif_pass<2, INV, FULL, 10, 8>(a, B, logL, s, tw);
@@ -394,7 +395,7 @@ __device__ __forceinline__ void dft_dif(u64* a, u32 B, u32 logL, const u64* tw, 
         else if (logL == 10 && k == 2 && s == 4) dif_pass<2, INV, FULL, 10, 4>(a, B, logL, s, tw);
         else if (logL == 10 && k == 2 && s == 6) dif_pass<2, INV, FULL, 10, 6>(a, B, logL, s, tw);
         else switch (k) {
-        case 5: dif_pass<5, INV, FULL>(a, B, logL, s, tw); break;
+        case 5: dif_pass<(MAXK >= 5 ? 5 : 4), INV, FULL>(a, B, logL, s, tw); break;
         case 4: dif_pass<4, INV, FULL>(a, B, logL, s, tw); break;
         case 3: dif_pass<3, INV, FULL>(a, B, logL, s, tw); break;
         case 2: dif_pass<2, INV, FULL>(a, B, logL, s, tw); break;
@@ -717,7 +718,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_c(const LdeJob* __restrict__ j
             }
         }
         __syncthreads();
-        dft_dif<false, true>(data, kStageCCols * Q, l1, tw, min(J.kcap + 1, 5u));
+        dft_dif<false, true, 5>(data, kStageCCols * Q, l1, tw, J.kcap + 1);
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
