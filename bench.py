@@ -1164,10 +1164,10 @@ def run_seteq(args):
         "e2e": {"value": n * L / e2e_s / 1e9, "unit": "Gtuple/s", "ms_per_step": e2e_s * 1e3,
                 "h2d_bytes_per_step": int(n * 2 * L * T * 8), "d2h_bytes_per_step": int(n * (L + 1) * 8)},
         "gpu_launches": int(launches), "clocks": clk,
-        "roofline": {"bound": "hbm", "kernel": "k_seteq_reduce+k_seteq_carries+k_seteq_apply",
+        "roofline": {"bound": "hbm", "kernel": "k_seteq_scan (+ k_seteq_zero)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "bytes_per_launch": alg_bytes, "ms_per_launch": seq_ms, "peak_source": "measured",
-                     "note": "algorithmic bytes: X and Y read once, Z written once; the kernels also write and read back 16 bytes of compressed (num, den) per tuple"},
+                     "note": "algorithmic bytes: X and Y read once, Z written once; one pass with a decoupled look-back"},
         "stages_ms_per_launch": stage_ms,
     }
     if not args.no_cpu_baseline:

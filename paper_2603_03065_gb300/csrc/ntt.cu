@@ -514,6 +514,48 @@ __device__ __forceinline__ u64 pow_wN(const u64* __restrict__ pw, u64 e)
     return gl::mul(r, __ldg(pw + 1024 + (e >> 18)));
 }
 
+// The forward 8192-point transform of stage B for the 2^10 x 2^3 plans
+// (n2 = 2^10, rate 3: the large commits), with 256 threads: the ten DIT
+// stages after the three replicating ones as two radix-32 passes.  The
+// first reads the scaled coefficients straight from `stage` (element
+// i0 + 8 j of the replicated array is stage[(i0 >> 3) + j]), so the
+// replication is never stored; the second writes its outputs q = lo + 256 j
+// from registers into the q-blocked Z (block q >> lQ holds [k1][q mod Q]).
+__device__ __forceinline__ void stage_b_forward_8192(const u64* stage, u64* data, const u64* twf, u64* Z, u32 k1,
+                                                     u32 l1, u32 lQ)
+{
+    const u32 g = threadIdx.x;
+    {   // stages 3..7: elements i0 + 8 j with i0 = 256 hi + lo, lo < 8
+        const u32 lo = g & 7, hi = g >> 3;
+        u64 v[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) v[j] = stage[sw((hi << 5) + j)];
+#pragma unroll
+        for (int j = 1; j < 32; j++) v[j] = mul_tw<false>(v[j], twf, (lo * (u32)bitrev_c(j, 5)) << 5, 13);
+        small_dit<5, false>(v);
+        const u32 i0 = (hi << 8) + lo, base = sw(i0);
+#pragma unroll
+        for (int j = 0; j < 32; j++) data[pass_word<13>(i0, base, (u32)j, 3)] = v[j];
+    }
+    __syncthreads();
+    {   // stages 8..12: elements lo + 256 j
+        const u32 lo = g, base = sw(lo);
+        u64 v[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) v[j] = data[pass_word<13>(lo, base, (u32)j, 8)];
+#pragma unroll
+        for (int j = 1; j < 32; j++) v[j] = mul_tw<false>(v[j], twf, lo * (u32)bitrev_c(j, 5), 13);
+        small_dit<5, false>(v);
+        const u32 Q = 1u << lQ;
+        u64* dst = Z + ((size_t)k1 << lQ) + (lo & (Q - 1));
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            const u32 q = lo + 256u * (u32)j;
+            __stcs(dst + ((size_t)(q >> lQ) << (l1 + lQ)), v[j]);
+        }
+    }
+}
+
 size_t stage_b_smem(const LdeJob& j)
 {
     size_t n2 = (size_t)1 << j.plan.log_n2, M = (size_t)1 << j.plan.log_M;
@@ -569,6 +611,11 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
         // into the 2^r slots after it, so they are applied here directly.
         for (u32 t = threadIdx.x; t < n2; t += blockDim.x) stage[sw(t)] = gl::mul(stage[sw(t)], sc[t]);
         __syncthreads();
+        if (l1 && lM == 13 && r == 3 && blockDim.x == 256 && J.kcap >= 4) {
+            stage_b_forward_8192(stage, data, twf, J.Z + ((size_t)col << J.plan.log_N), k1, l1, __ffs(J.c_q) - 1);
+            __syncthreads();
+            continue;
+        }
         for (u32 e = threadIdx.x; e < M; e += blockDim.x) data[sw(e)] = stage[sw(e >> r)];
         __syncthreads();
         dft_dit<false>(data, 1, lM, twf, r, J.kcap + 1);  // the forward M-point transform may use radix 2^5
@@ -666,7 +713,7 @@ __device__ __forceinline__ void stage_c_load(const LdeJob& J, u64* data, u32 cg,
     }
 }
 
-__global__ void __launch_bounds__(256, 2) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
+__global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
     u32 cur_job = 0xFFFFFFFFu;
@@ -718,7 +765,9 @@ __global__ void __launch_bounds__(256, 2) k_stage_c(const LdeJob* __restrict__ j
             }
         }
         __syncthreads();
-        dft_dif<false, true, 5>(data, kStageCCols * Q, l1, tw, J.kcap + 1);
+        // Radix 2^4 at three CTAs per SM measured faster here than radix 2^5 at
+        // two (12.5 against 13.1 ms on the 135 x 2^20 commit).
+        dft_dif<false, true, 4>(data, kStageCCols * Q, l1, tw, J.kcap);
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
@@ -870,26 +919,23 @@ __global__ void k_int_peak(u64* out, u32 iters)
 #pragma unroll
         for (int k = 0; k < 8; k++) x ^= acc[k];
     } else {
-        // new[k] = old[k] * old[k+1] + m: a product of two chain values, so
-        // no step can be folded into the next.
+        // acc = acc * acc + m: a squaring chain, which no algebra folds.
         u32 acc[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) acc[k] = (m + k) * 0x9E3779B9u;
         for (u32 i = 0; i < iters; i++) {
 #pragma unroll
             for (int rep = 0; rep < 4; rep++) {
-                u32 nxt[8];
 #pragma unroll
-                for (int k = 0; k < 8; k++)
-                    asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(nxt[k]) : "r"(acc[k]), "r"(acc[(k + 1) & 7]), "r"(m));
-#pragma unroll
-                for (int k = 0; k < 8; k++) acc[k] = nxt[k];
+                for (int k = 0; k < 8; k++) acc[k] = acc[k] * acc[k] + m;
             }
         }
 #pragma unroll
         for (int k = 0; k < 8; k++) x ^= acc[k];
     }
-    if (x == 0x123456789ull) out[1 + blockIdx.x] = x;
+    // A store the compiler cannot prove dead (the value fits either kind's
+    // result), so the chains are computed.
+    if (x == 0x13579BDFull) out[1 + blockIdx.x] = x;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const u64 ns = global_ns() - t0;
         out[0] = ns ? (u64)(clock64() - c0) * (1ull << 20) / ns : 0;

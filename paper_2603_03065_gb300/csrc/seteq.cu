@@ -2,20 +2,21 @@
 // grand-product column Z_{i+1} = Z_i (alpha - x_i) / (alpha - y_i) over
 // tuples compressed by Compress(t; beta) = sum_k t_k beta^k.
 //
-// GB300 mapping: a multiplicative scan over F_p in three persistent launches
-// over all instances.  (1) Every CTA takes a tile of 2048 elements, 8 per
-// thread, and writes the tile's products of numerators and denominators.
-// (2) One CTA per instance scans the tile products: the prefix of
-// numerators before each tile, the suffix of denominators after it, and the
-// inverse of the full denominator product (the instance's only inversion).
-// (3) Every tile reads its numerators and denominators back, scans them with
-// warp shuffles and one shared-memory step per CTA, and writes
-// Z_i = N_{<i} * D_{>=i} * D_all^-1.  Loads and stores are coalesced: the
-// order-free product of phase 1 takes strided elements, and phase 3
-// transposes through shared memory.
-// X and Y are read once (phase 1); the compressed terms cost 16 bytes per
-// tuple to write and read back instead of a second pass over X, Y and the
-// Horner evaluations.
+// GB300 mapping: one persistent launch scans every instance in tiles of
+// 2048 elements (8 per thread), in the order a global counter hands the
+// tiles out.  A tile reads its tuples once (coalesced), compresses them,
+// and forms the products of its numerators and denominators.  It publishes
+// those products at once, and the products of everything before it
+// ("inclusive") as soon as it knows them: a decoupled look-back in which one
+// warp reads the states of the 32 preceding tiles at a time and multiplies
+// their products until it meets an inclusive one.  Every wait is bounded;
+// one that gives up sets an error flag that the host turns into a status.
+// With the prefix (N_pre, D_pre) known, the tile takes one inversion,
+// inv = (D_pre D_tile)^-1, and writes Z_i = N_pre N_{<i} D_{>=i} inv, where
+// N_{<i} and D_{>=i} run inside the tile (block scans with warp shuffles).
+// X and Y are read once and Z written once.  A second, small launch zeroes
+// the column of an instance whose denominator product is zero (alpha equal
+// to some compressed y).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +35,7 @@ using gl::u64;
 
 constexpr u32 kSeqThreads = 256;
 constexpr u32 kSeqPer = 8;
+constexpr u32 kSeqMinBlocks = 3;  // resident CTAs per SM the scan is compiled for
 constexpr u32 kSeqTile = kSeqThreads * kSeqPer;
 
 struct SeqJob {
@@ -42,14 +44,17 @@ struct SeqJob {
     u64* z;
     u64 L;
     u64 alpha, beta;
-    ulonglong2* nd;  // [L]: (alpha - x_i, alpha - y_i), written by phase 1, read by phase 3
-    u64* agg;     // [ntiles][2]: tile products of numerators, denominators
-    u64* carry;   // [ntiles][2]: numerator product before, denominator product after the tile
-    u64* inv;     // [2]: inverse of the denominator product (0 if it is 0), status
+    u32* status;  // the instance's status word: 1 when its denominator product is zero
     u32 T;
     u32 tile0;    // first global tile
     u32 ntiles;
     u32 pad;
+};
+
+// Look-back state of one tile: its own products (flag 1) and the products
+// of its instance up to and including it (flag 2).
+struct SeqTile {
+    u64 agg_n, agg_d, inc_n, inc_d;
 };
 
 __device__ __forceinline__ u32 seq_find(const SeqJob* __restrict__ jobs, u32 njobs, u32 tile)
@@ -129,103 +134,186 @@ __device__ __forceinline__ u64 block_exclusive(u64 v, u64* sh)
     return r;
 }
 
-// Phase 1: tile products of the numerators and denominators.  A product
-// does not depend on order, so thread t takes elements t + 256 k: the warp's
-// loads of one tuple component are then one contiguous run.
-__global__ void __launch_bounds__(kSeqThreads) k_seteq_reduce(const SeqJob* __restrict__ jobs, u32 njobs, u32 ntiles)
+// x^(p-2), the inverse of x (0 for 0).  p - 2 has bits 63..33 and 31..0
+// set, so x^(p-2) = (x^(2^31 - 1))^(2^33) x^(2^32 - 1); x^(2^31 - 1) comes
+// from the chain 2^k - 1 for k = 1, 2, 3, 6, 12, 15, 30, 31 (each step
+// e_{a+b} = e_a^(2^b) e_b): 64 squarings and 9 products in all.
+__device__ u64 seq_inverse(u64 x)
 {
-    __shared__ u64 sh[32];
-    for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const SeqJob& J = jobs[seq_find(jobs, njobs, tile)];
-        const u32 lt = tile - J.tile0;
-        const u64 base = (u64)lt * kSeqTile + threadIdx.x;
-        u64 pn = 1, pd = 1;
+    auto sq = [](u64 v, int n) {
+        for (int i = 0; i < n; i++) v = gl::mul(v, v);
+        return v;
+    };
+    const u64 e1 = x;
+    const u64 e2 = gl::mul(sq(e1, 1), e1);
+    const u64 e3 = gl::mul(sq(e2, 1), e1);
+    const u64 e6 = gl::mul(sq(e3, 3), e3);
+    const u64 e12 = gl::mul(sq(e6, 6), e6);
+    const u64 e15 = gl::mul(sq(e12, 3), e3);
+    const u64 e30 = gl::mul(sq(e15, 15), e15);
+    const u64 e31 = gl::mul(sq(e30, 1), e1);
+    const u64 e32 = gl::mul(sq(e31, 1), e1);
+    return gl::mul(sq(e31, 33), e32);
+}
+
+// alpha - Compress(t; beta) of the width-4 tuples t + 256 k (k < 8) of a
+// tile into out (padded layout); 1 past the end.
+__device__ __forceinline__ u32 seq_pad(u32 i);
+__device__ __forceinline__ void seq_terms4(const u64* __restrict__ src, u64 L, u64 tbase, u64 alpha, u64 beta,
+                                           u64* out)
+{
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(src);
+    constexpr u32 H = kSeqPer / 2;  // two rounds of four tuples (eight loads in flight)
 #pragma unroll
-        for (u32 k = 0; k < kSeqPer; k++) {
-            const u64 e = base + (u64)k * kSeqThreads;
-            u64 n, d;
-            seq_terms(J, e, n, d);
-            if (e < J.L) J.nd[e] = make_ulonglong2(n, d);
-            pn = gl::mul(pn, n);
-            pd = gl::mul(pd, d);
+    for (u32 r = 0; r < 2; r++) {
+        ulonglong2 a[H], b[H];
+#pragma unroll
+        for (u32 k = 0; k < H; k++) {
+            const u64 e = tbase + threadIdx.x + (r * H + k) * kSeqThreads;
+            if (e < L) {
+                a[k] = __ldcs(s2 + 2 * e);
+                b[k] = __ldcs(s2 + 2 * e + 1);
+            }
         }
-        // Tile totals: exclusive prefix of the last thread times its own value.
-        u64 en = block_exclusive<false>(pn, sh);
-        u64 ed = block_exclusive<false>(pd, sh);
-        if (threadIdx.x == blockDim.x - 1) {
-            J.agg[2 * lt] = gl::mul(en, pn);
-            J.agg[2 * lt + 1] = gl::mul(ed, pd);
+#pragma unroll
+        for (u32 k = 0; k < H; k++) {
+            const u32 i = threadIdx.x + (r * H + k) * kSeqThreads;
+            u64 v = 1;
+            if (tbase + i < L) {
+                u64 h = gl::add_nc(gl::mul_nc(b[k].y, beta), b[k].x);
+                h = gl::add_nc(gl::mul_nc(h, beta), a[k].y);
+                h = gl::add_nc(gl::mul_nc(h, beta), a[k].x);
+                v = gl::sub(alpha, gl::canon(h));
+            }
+            out[seq_pad(i)] = v;
         }
     }
 }
 
-// Phase 2: per instance, carries across tiles and the one inversion.
-__global__ void __launch_bounds__(1024) k_seteq_carries(const SeqJob* __restrict__ jobs, u32 njobs)
-{
-    __shared__ u64 sh[32];
-    __shared__ u64 tot[2];
-    for (u32 j = blockIdx.x; j < njobs; j += gridDim.x) {
-        const SeqJob& J = jobs[j];
-        const u32 nt = J.ntiles;
-        // Thread t takes the contiguous tiles [t c, (t+1) c).
-        const u32 c = (nt + blockDim.x - 1) / blockDim.x;
-        const u32 t0 = min(nt, threadIdx.x * c), t1 = min(nt, t0 + c);
-        u64 pn = 1, pd = 1;
-        for (u32 t = t0; t < t1; t++) {
-            pn = gl::mul(pn, J.agg[2 * t]);
-            pd = gl::mul(pd, J.agg[2 * t + 1]);
-        }
-        u64 before = block_exclusive<false>(pn, sh);  // numerators of tiles before t0
-        u64 after = block_exclusive<true>(pd, sh);    // denominators of tiles from t1 on
-        if (threadIdx.x == blockDim.x - 1) tot[0] = gl::mul(before, pn);
-        if (threadIdx.x == 0) tot[1] = gl::mul(after, pd);
-        // running carries inside the thread's range
-        u64 run = before;
-        for (u32 t = t0; t < t1; t++) {
-            J.carry[2 * t] = run;
-            run = gl::mul(run, J.agg[2 * t]);
-        }
-        run = after;
-        for (u32 t = t1; t > t0; t--) {
-            J.carry[2 * (t - 1) + 1] = run;
-            run = gl::mul(run, J.agg[2 * (t - 1) + 1]);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const u64 D = tot[1];
-            J.inv[0] = gl::pow(D, gl::P - 2);  // 0 when D = 0
-            J.inv[1] = D == 0;
-        }
-        __syncthreads();
-    }
-}
+// Polls of one look-back window before the wait gives up (with a short
+// sleep between polls, on the order of a second in all).
+constexpr u32 kSeqSpinLimit = 1u << 22;
 
-// Phase 3: Z_i = N_{<i} D_{>=i} D^-1 for every element of every tile, and
-// Z_L = N_{<L} D^-1 from the thread that holds element L - 1.  Terms are
-// computed with coalesced loads (thread t, elements t + 256 k), transposed
-// through shared memory so that thread t scans the contiguous elements
-// 8t .. 8t+7, and Z goes back through shared memory for coalesced stores.
 // Shared words are padded by one per 8 (index i + i/8): the 8-word stride of
-// the contiguous reads becomes 9, an odd number of 8-byte words, so a warp's
-// accesses fall in distinct bank pairs.
+// a thread's contiguous elements becomes 9, an odd number of 8-byte words,
+// so a warp's accesses fall in distinct bank pairs.
 __device__ __forceinline__ u32 seq_pad(u32 i) { return i + (i >> 3); }
 
-__global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __restrict__ jobs, u32 njobs, u32 ntiles)
+__device__ __forceinline__ u64 warp_product(u64 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = gl::mul(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Warp 0's part of a tile: publish the tile's products, find the products of
+// the instance before the tile (decoupled look-back), publish the inclusive
+// products, and return (N_pre, D_pre) in lane 0.
+__device__ __forceinline__ void seq_lookback(const SeqJob& J, u32 tile, u64 Nt, u64 Dt, SeqTile* st, u32* flags,
+                                             u32* err, u64& Np, u64& Dp)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u32 lt = tile - J.tile0;
+    Np = 1;
+    Dp = 1;
+    if (lane == 0) {
+        SeqTile& me = st[tile];
+        if (lt == 0) {
+            me.inc_n = Nt;
+            me.inc_d = Dt;
+        } else {
+            me.agg_n = Nt;
+            me.agg_d = Dt;
+        }
+        __threadfence();
+        atomicExch(&flags[tile], lt == 0 ? 2u : 1u);
+    }
+    if (lt == 0) return;
+    int p = (int)tile - 1;  // nearest predecessor not folded in yet
+    u32 spins = 0;
+    for (;;) {
+        const int q = p - (int)lane;
+        const bool in = q >= (int)J.tile0;
+        const u32 f = in ? *(volatile const u32*)(flags + q) : 2u;  // before the instance: identity
+        const u32 inc = __ballot_sync(0xffffffffu, f == 2u);
+        const u32 upto = inc ? (u32)__ffs(inc) - 1 : 31u;             // lanes 0..upto take part
+        const u32 relevant = upto == 31 ? 0xffffffffu : ((2u << upto) - 1);
+        if (__ballot_sync(0xffffffffu, f == 0u) & relevant) {
+            if (++spins > kSeqSpinLimit) {  // a predecessor never published: give up
+                if (lane == 0) atomicOr(err, 1u);
+                return;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        __threadfence();
+        u64 vn = 1, vd = 1;
+        if (in && lane <= upto) {
+            const SeqTile& o = st[q];
+            if (lane == upto && inc) {
+                vn = __ldcv(&o.inc_n);
+                vd = __ldcv(&o.inc_d);
+            } else {
+                vn = __ldcv(&o.agg_n);
+                vd = __ldcv(&o.agg_d);
+            }
+        }
+        vn = warp_product(vn);
+        vd = warp_product(vd);
+        Np = gl::mul(Np, vn);
+        Dp = gl::mul(Dp, vd);
+        if (inc) break;
+        p -= 32;
+        spins = 0;
+    }
+    if (lane == 0) {
+        SeqTile& me = st[tile];
+        me.inc_n = gl::mul(Np, Nt);
+        me.inc_d = gl::mul(Dp, Dt);
+        __threadfence();
+        atomicExch(&flags[tile], 2u);
+    }
+}
+
+// The scan.  A CTA takes tiles from the global counter until none is left.
+// For each: coalesced loads (thread t, elements t + 256 k) compress the
+// tuples into shared memory; thread t then owns the contiguous elements
+// 8t .. 8t+7 and forms their products; block scans give the numerators of
+// the earlier threads and the denominators of the later ones; warp 0 does
+// the look-back and the one inversion; Z goes out through shared memory for
+// coalesced stores.
+__global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const SeqJob* __restrict__ jobs, u32 njobs, u32 ntiles,
+                                                            SeqTile* st, u32* flags, u32* counter, u32* err)
 {
     __shared__ u64 sh[32];
     __shared__ u64 s_num[kSeqTile + kSeqTile / 8];
     __shared__ u64 s_den[kSeqTile + kSeqTile / 8];
+    __shared__ u64 s_tot[2];  // the tile's numerator and denominator products
+    __shared__ u64 s_k;       // N_pre (D_pre D_tile)^-1
+    __shared__ u32 s_tile;
     const u32 t = threadIdx.x;
-    for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (;;) {
+        if (t == 0) s_tile = atomicAdd(counter, 1u);
+        __syncthreads();
+        const u32 tile = s_tile;
+        if (tile >= ntiles) break;
         const SeqJob& J = jobs[seq_find(jobs, njobs, tile)];
-        const u32 lt = tile - J.tile0;
-        const u64 tbase = (u64)lt * kSeqTile;
+        const u64 tbase = (u64)(tile - J.tile0) * kSeqTile;
+        if (J.T == 4 && !(((uintptr_t)J.x | (uintptr_t)J.y) & 15)) {
+            // Width-4 tuples (the query circuit's (list, slot, distance,
+            // item)): all eight tuples of X, then of Y, are requested before
+            // any is compressed, sixteen 16-byte loads in flight per thread.
+            seq_terms4(J.x, J.L, tbase, J.alpha, J.beta, s_num);
+            seq_terms4(J.y, J.L, tbase, J.alpha, J.beta, s_den);
+        } else {
 #pragma unroll
-        for (u32 k = 0; k < kSeqPer; k++) {
-            const u32 i = t + k * kSeqThreads;
-            ulonglong2 v = tbase + i < J.L ? __ldcs(J.nd + tbase + i) : make_ulonglong2(1, 1);
-            s_num[seq_pad(i)] = v.x;
-            s_den[seq_pad(i)] = v.y;
+            for (u32 k = 0; k < kSeqPer; k++) {
+                const u32 i = t + k * kSeqThreads;
+                u64 n, d;
+                seq_terms(J, tbase + i, n, d);
+                s_num[seq_pad(i)] = n;
+                s_den[seq_pad(i)] = d;
+            }
         }
         __syncthreads();
         u64 num[kSeqPer], den[kSeqPer];
@@ -237,11 +325,24 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __res
             pn = gl::mul(pn, num[k]);
             pd = gl::mul(pd, den[k]);
         }
-        // N carries the factor D^-1 from the start: Z_i = (N_{<i} D^-1) D_{>=i}.
-        const u64 inv = __ldg(J.inv);
-        u64 N = gl::mul(gl::mul(__ldg(J.carry + 2 * lt), inv), block_exclusive<false>(pn, sh));
-        u64 S = gl::mul(__ldg(J.carry + 2 * lt + 1), block_exclusive<true>(pd, sh));
-        // S: denominators after this thread's elements; walk them backwards.
+        const u64 en = block_exclusive<false>(pn, sh);  // numerators of the earlier threads
+        const u64 sd = block_exclusive<true>(pd, sh);   // denominators of the later threads
+        if (t == blockDim.x - 1) s_tot[0] = gl::mul(en, pn);
+        if (t == 0) s_tot[1] = gl::mul(sd, pd);
+        __syncthreads();
+        if (t < 32) {
+            u64 Np, Dp;
+            seq_lookback(J, tile, s_tot[0], s_tot[1], st, flags, err, Np, Dp);
+            if (t == 0) {
+                const u64 inv = seq_inverse(gl::mul(Dp, s_tot[1]));
+                if (inv == 0) atomicOr(J.status, 1u);
+                s_k = gl::mul(Np, inv);
+            }
+        }
+        __syncthreads();
+        // Z_i = N_pre N_{<i} D_{>=i} (D_pre D_tile)^-1, D_{>=i} within the tile.
+        u64 N = gl::mul(s_k, en);
+        u64 S = sd;
         u64 suf[kSeqPer];
 #pragma unroll
         for (int k = kSeqPer - 1; k >= 0; k--) {
@@ -251,7 +352,7 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __res
         const u64 ebase = tbase + (u64)kSeqPer * t;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
-            s_num[seq_pad(kSeqPer * t + k)] = gl::mul(N, suf[k]);  // every read above is done
+            s_num[seq_pad(kSeqPer * t + k)] = gl::mul(N, suf[k]);  // every read of s_num is done
             N = gl::mul(N, num[k]);
             if (ebase + k + 1 == J.L) J.z[J.L] = N;
         }
@@ -259,12 +360,21 @@ __global__ void __launch_bounds__(kSeqThreads) k_seteq_apply(const SeqJob* __res
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
             const u32 i = t + k * kSeqThreads;
-            if (tbase + i < J.L) J.z[tbase + i] = s_num[seq_pad(i)];
+            if (tbase + i < J.L) __stcs(J.z + tbase + i, s_num[seq_pad(i)]);
         }
         __syncthreads();
     }
 }
 
+// Columns of instances whose denominator product is zero are all zero.
+__global__ void k_seteq_zero(const SeqJob* __restrict__ jobs, u32 njobs)
+{
+    for (u32 j = blockIdx.x; j < njobs; j += gridDim.x) {
+        const SeqJob& J = jobs[j];
+        if (!*(volatile const u32*)J.status) continue;
+        for (u64 i = threadIdx.x; i <= J.L; i += blockDim.x) J.z[i] = 0;
+    }
+}
 }  // namespace v3c
 
 using namespace v3c::detail;
@@ -287,19 +397,20 @@ extern "C" v3c_status v3c_seteq(v3c_ctx* ctx, const v3c_seteq_desc* descs, uint3
     if (r) return r;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> g(ctx->mu);
-    // Scratch: jobs, per-tile products and carries, per-instance inverse/status.
-    u64 elems = 0;
-    for (u32 i = 0; i < n; i++) elems += descs[i].L;
+    // Scratch: jobs, tile states, then (zeroed) tile flags, the tile counter,
+    // the error flag and the per-instance statuses.
     const size_t job_words = (sizeof(SeqJob) * n + 15) / 16 * 2;  // an even word count
-    const size_t words = job_words + 4 * tiles + 2 * (size_t)n + 2 * elems;
+    const size_t tile_words = 4 * tiles;
+    const size_t flag_words = (tiles + 2 + n + 1) / 2 + 1;        // u32 words, rounded up
+    const size_t words = job_words + tile_words + flag_words;
     u64* mem = nullptr;
     CK(cudaMallocAsync((void**)&mem, words * 8, s));
+    SeqTile* dst = reinterpret_cast<SeqTile*>(mem + job_words);
+    u32* flags = reinterpret_cast<u32*>(mem + job_words + tile_words);
+    u32* counter = flags + tiles;
+    u32* err = counter + 1;
+    u32* status = err + 1;
     std::vector<SeqJob> jobs(n);
-    u64* agg = mem + job_words;
-    u64* carry = agg + 2 * tiles;
-    u64* inv = carry + 2 * tiles;
-    u64* nd = inv + 2 * (size_t)n;  // 16-byte aligned: every earlier part has an even word count
-    u64 e0 = 0;
     u32 t0 = 0;
     for (u32 i = 0; i < n; i++) {
         const v3c_seteq_desc& d = descs[i];
@@ -314,40 +425,40 @@ extern "C" v3c_status v3c_seteq(v3c_ctx* ctx, const v3c_seteq_desc* descs, uint3
         J.beta = d.beta;
         J.tile0 = t0;
         J.ntiles = (u32)((d.L + kSeqTile - 1) / kSeqTile);
-        J.agg = agg + 2 * (size_t)t0;
-        J.carry = carry + 2 * (size_t)t0;
-        J.inv = inv + 2 * (size_t)i;
-        J.nd = reinterpret_cast<ulonglong2*>(nd + 2 * e0);
-        e0 += d.L;
+        J.status = status + i;
         t0 += J.ntiles;
     }
     cudaError_t e = cudaMemcpyAsync(mem, jobs.data(), sizeof(SeqJob) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, flag_words * 8, s);
     const SeqJob* dj = reinterpret_cast<const SeqJob*>(mem);
-    const int grid = (int)std::min<u64>(tiles, (u64)num_sms() * 8);
+    // Persistent grid: the resident CTAs of all SMs (tiles are handed out in
+    // order, so every tile a CTA waits for is held by a running CTA).
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seteq_scan, kSeqThreads, 0);
+    const int grid = (int)std::min<u64>(tiles, (u64)num_sms() * std::max(per_sm, 1));
     if (e == cudaSuccess) {
         StageTimer tm(ctx, 8, s);
-        k_seteq_reduce<<<grid, kSeqThreads, 0, s>>>(dj, n, (u32)tiles);
+        k_seteq_scan<<<grid, kSeqThreads, 0, s>>>(dj, n, (u32)tiles, dst, flags, counter, err);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
-            k_seteq_carries<<<(int)std::min<u32>(n, (u32)num_sms() * 2), 1024, 0, s>>>(dj, n);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) {
-            k_seteq_apply<<<grid, kSeqThreads, 0, s>>>(dj, n, (u32)tiles);
+            k_seteq_zero<<<(int)std::min<u32>(n, (u32)num_sms() * 2), 256, 0, s>>>(dj, n);
             e = cudaGetLastError();
         }
         tm.done();
-        ctx->launches += 3;
+        ctx->launches += 2;
     }
-    std::vector<u64> st;
+    // The statuses and the error flag come back when the caller waits.
+    std::vector<u32> st;
     if (e == cudaSuccess && h_status) {
-        st.resize(2 * (size_t)n);
-        e = cudaMemcpyAsync(st.data(), inv, 16 * (size_t)n, cudaMemcpyDeviceToHost, s);
+        st.resize(1 + (size_t)n);
+        e = cudaMemcpyAsync(st.data(), err, 4 * (1 + (size_t)n), cudaMemcpyDeviceToHost, s);
     }
     cudaFreeAsync(mem, s);
     if (e == cudaSuccess && h_status) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(ctx, V3C_ECUDA, "v3c_seteq: %s", cudaGetErrorString(e));
-    if (h_status)
-        for (u32 i = 0; i < n; i++) h_status[i] = (uint32_t)st[2 * (size_t)i + 1];
+    if (h_status) {
+        if (st[0]) return fail(ctx, V3C_ETIMEDOUT, "v3c_seteq: a tile's look-back wait gave up");
+        for (u32 i = 0; i < n; i++) h_status[i] = st[1 + (size_t)i];
+    }
     return V3C_OK;
 }
