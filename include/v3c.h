@@ -146,7 +146,9 @@ typedef struct {
  * V3C_FLAG_TIMING and large host inputs select direct launches.  ids[i]
  * receives the object id.  Host inputs are copied to the device inside the
  * call; large ones (at least 16 columns and 2^22 words) in column chunks on a
- * copy stream, each chunk's first two stages starting when it lands.  The
+ * copy stream into a buffer of their own, each chunk's first two stages
+ * starting when it lands; those copies do not wait for earlier work on
+ * `stream`, so they overlap the previous commit's kernels.  The
  * objects stay resident until v3c_release.  Errors: EINVAL, ENOMEM (the HBM
  * budget would be exceeded; nothing is allocated), ECUDA. */
 v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v3c_commit_id* ids,
@@ -199,8 +201,10 @@ v3c_status v3c_commit_buffers(v3c_ctx* ctx, v3c_commit_id id, uint64_t** d_lde, 
                               uint64_t** d_tree, uint64_t** d_cap, uint32_t* log_rows,
                               uint32_t* cap_height);
 
-/* Copies the cap ([2^h][4]) of a resident object to h_cap.  Synchronises
- * with the object's producing stream.  Errors: ENOTFOUND, ECUDA. */
+/* Copies the cap ([2^h][4]) of a resident object to h_cap.  Waits for the
+ * object's own work only (its completion event), not for later work on the
+ * producing stream, so a caller may enqueue the next commit before reading
+ * this one's cap.  Errors: ENOTFOUND, ECUDA. */
 v3c_status v3c_commit_cap(v3c_ctx* ctx, v3c_commit_id id, uint64_t* h_cap);
 
 /* Opening of leaf `leaf` (MerkleOpen, Sec. 4.4).  h_row receives the c
@@ -225,6 +229,10 @@ typedef struct {
     uint32_t max_inflight;      /* batches in flight on separate streams (0 = ctx setting) */
     uint32_t flags;             /* V3C_FLAG_VALIDATE */
     uint64_t slot_scratch_bytes; /* LDE scratch + staged inputs one pass may take (0 = 16 GiB);
+                                    a pass always takes at least one request */
+    uint64_t batch_elems;        /* LDE elements (c * 2^(log_n + rate_bits)) one batched launch may
+                                    take (0 = 2^28; ~45 ms of work on one GB300), so a large
+                                    request is not made to wait for a whole batch of its class;
                                     a pass always takes at least one request */
 } v3c_serve_cfg;
 

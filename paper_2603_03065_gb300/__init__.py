@@ -63,7 +63,7 @@ class PartDesc(ctypes.Structure):
 
 class ServeCfg(ctypes.Structure):
     _fields_ = [("queue_capacity", _u32), ("max_batch", _u32), ("max_inflight", _u32), ("flags", _u32),
-                ("slot_scratch_bytes", _u64)]
+                ("slot_scratch_bytes", _u64), ("batch_elems", _u64)]
 
 
 FLAG_NO_GRAPH = 4
@@ -398,8 +398,9 @@ class Context:
         self._borrowed.pop(cid, None)
 
     # --------------------------------------------------------------- serving
-    def serve_start(self, queue_capacity=0, max_batch=0, max_inflight=0, flags=0, slot_scratch_bytes=0):
-        cfg = ServeCfg(queue_capacity, max_batch, max_inflight, flags, slot_scratch_bytes)
+    def serve_start(self, queue_capacity=0, max_batch=0, max_inflight=0, flags=0, slot_scratch_bytes=0,
+                    batch_elems=0):
+        cfg = ServeCfg(queue_capacity, max_batch, max_inflight, flags, slot_scratch_bytes, batch_elems)
         self._check(self.lib.v3c_serve_start(self.h, ctypes.byref(cfg)))
 
     def serve_submit(self, cols, rate_bits: int, cap_height: int, borrow: bool = False) -> int:

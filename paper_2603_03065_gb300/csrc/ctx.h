@@ -100,6 +100,7 @@ struct v3c_ctx {
     std::unordered_map<u64, SnapState*> snaps;   // snapshot commitments (snapshot.cu)
     SnapCbCache* snap_cb = nullptr;              // codebook-digest cache (snapshot.cu)
     cudaStream_t release_stream = nullptr;  // orders frees of resident objects
+    cudaStream_t readback_stream = nullptr; // cap reads: waits on one object's event only
     // Chunked input copies of large host inputs (commit_locked).
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_fork = nullptr;

@@ -67,7 +67,7 @@ enum MdsKind { MDS_WIDE = 0, MDS_LIMB = 1, MDS_SPLIT = 2 };
 // FOLD3 / RED: the limb fold and the 128-bit reduction written as PTX
 // carry chains (no compares or selects).
 template <int MUL_, int MDS_, bool SQR_, bool FAST_, bool FOLD2_ = false, bool ARCM_ = false,
-          bool FOLD3_ = false, bool RED_ = false, bool SHIFT_ = false>
+          bool FOLD3_ = false, bool RED_ = false, int SHIFT_ = 0>
 struct Cfg {
     static constexpr int MUL = MUL_;
     static constexpr int MDS = MDS_;
@@ -77,7 +77,7 @@ struct Cfg {
     static constexpr bool ARCM = ARCM_;
     static constexpr bool FOLD3 = FOLD3_;
     static constexpr bool RED = RED_;
-    static constexpr bool SHIFT = SHIFT_;
+    static constexpr int SHIFT = SHIFT_;
 };
 
 // A + B 2^22 + C 2^44 (A, B, C < 2^32) to [0, 2^64) with carry chains:
@@ -322,12 +322,16 @@ __host__ __device__ __forceinline__ constexpr int clo(int a)
     return l;
 }
 
-__device__ __forceinline__ u32 mac_const(u32 acc, u32 x, int K, bool shift)
+// shift: 0 never; 1 for constants with one bit set (one shift-add, LEA, in
+// place of one multiply-add); 2 for up to two bits set; 3 also for
+// 2^(hi+1) - 2^lo.
+__device__ __forceinline__ u32 mac_const(u32 acc, u32 x, int K, int shift)
 {
     const int A = K < 0 ? -K : K;
     const int pc = cpop(A), hi = chi(A), lo = clo(A);
     const bool sub_form = pc > 2 && ((1 << (hi + 1)) - (1 << lo)) == A;
-    if (!shift || A == 0 || (pc > 2 && !sub_form)) return acc + x * (u32)K;
+    const bool use = shift >= 3 ? (pc <= 2 || sub_form) : shift >= pc;
+    if (!use || A == 0) return acc + x * (u32)K;
     u32 t;
     if (pc == 1)
         t = x << lo;

@@ -191,6 +191,7 @@ bool admit_and_launch(Server* S)
                               now_s() - head.times.t_submit > kStarveS;
     const u32 max_batch = S->cfg.max_batch ? S->cfg.max_batch : 32;
     const u64 slot_cap = S->cfg.slot_scratch_bytes ? S->cfg.slot_scratch_bytes : (16ull << 30);
+    const u64 elem_cap = S->cfg.batch_elems ? S->cfg.batch_elems : (1ull << 28);
     for (int oi = 0; oi < norder; oi++) {
         const int k = order[oi];
         if (head_starved && k != head_cls) continue;
@@ -198,7 +199,7 @@ bool admit_and_launch(Server* S)
         if (nfree == 1 && oi > 0) continue;
         std::vector<u64> batch;
         size_t scratch = 0, staged = 0, copied = 0;
-        u64 reserve = 0;
+        u64 reserve = 0, elems = 0;
         for (u64 tk : S->queue) {
             if (batch.size() >= max_batch) break;
             Request& r = S->reqs[tk];
@@ -209,6 +210,9 @@ bool admit_and_launch(Server* S)
             // A pass takes at least one request; more only while its scratch
             // and staged inputs stay within the slot cap.
             if (!batch.empty() && (scratch + staged + sw + iw) * 8 > slot_cap) break;
+            const u64 re = (u64)r.desc.c << (r.desc.log_n + r.desc.rate_bits);
+            if (!batch.empty() && elems + re > elem_cap) break;  // the batch's work stays bounded
+            elems += re;
             reserve += r.footprint;
             scratch += sw;
             staged += iw;

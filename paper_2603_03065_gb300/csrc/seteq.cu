@@ -35,7 +35,7 @@ using gl::u64;
 
 constexpr u32 kSeqThreads = 256;
 constexpr u32 kSeqPer = 8;
-constexpr u32 kSeqMinBlocks = 3;  // resident CTAs per SM the scan is compiled for
+constexpr u32 kSeqMinBlocks = 2;  // resident CTAs per SM the scan is compiled for
 constexpr u32 kSeqTile = kSeqThreads * kSeqPer;
 
 struct SeqJob {
@@ -156,36 +156,56 @@ __device__ u64 seq_inverse(u64 x)
     return gl::mul(sq(e31, 33), e32);
 }
 
-// alpha - Compress(t; beta) of the width-4 tuples t + 256 k (k < 8) of a
-// tile into out (padded layout); 1 past the end.
+// The terms alpha - Compress(X_i), alpha - Compress(Y_i) of the tile at
+// tbase into bn, bd (padded layout; 1 past the end), computed by the threads
+// [first, first + nthr) of the CTA, thread j taking elements j + nthr k.
+// Width-4 tuples at 16-byte aligned addresses (the query circuit's (list,
+// slot, distance, item)) are requested two elements at a time, eight
+// 16-byte loads in flight per thread, before any is compressed.
 __device__ __forceinline__ u32 seq_pad(u32 i);
-__device__ __forceinline__ void seq_terms4(const u64* __restrict__ src, u64 L, u64 tbase, u64 alpha, u64 beta,
-                                           u64* out)
+__device__ __forceinline__ void seq_load(const SeqJob& J, u64 tbase, u64* bn, u64* bd, u32 first, u32 nthr)
 {
-    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(src);
-    constexpr u32 H = kSeqPer / 2;  // two rounds of four tuples (eight loads in flight)
+    const u32 j = threadIdx.x - first;
+    if (J.T == 4 && !(((uintptr_t)J.x | (uintptr_t)J.y) & 15)) {
+        const ulonglong2* x2 = reinterpret_cast<const ulonglong2*>(J.x);
+        const ulonglong2* y2 = reinterpret_cast<const ulonglong2*>(J.y);
+        for (u32 i0 = j; i0 < kSeqTile; i0 += 2 * nthr) {
+            ulonglong2 xa[2], xb[2], ya[2], yb[2];
 #pragma unroll
-    for (u32 r = 0; r < 2; r++) {
-        ulonglong2 a[H], b[H];
+            for (u32 k = 0; k < 2; k++) {
+                const u64 e = tbase + i0 + k * nthr;
+                if (i0 + k * nthr < kSeqTile && e < J.L) {
+                    xa[k] = __ldcs(x2 + 2 * e);
+                    xb[k] = __ldcs(x2 + 2 * e + 1);
+                    ya[k] = __ldcs(y2 + 2 * e);
+                    yb[k] = __ldcs(y2 + 2 * e + 1);
+                }
+            }
 #pragma unroll
-        for (u32 k = 0; k < H; k++) {
-            const u64 e = tbase + threadIdx.x + (r * H + k) * kSeqThreads;
-            if (e < L) {
-                a[k] = __ldcs(s2 + 2 * e);
-                b[k] = __ldcs(s2 + 2 * e + 1);
+            for (u32 k = 0; k < 2; k++) {
+                const u32 i = i0 + k * nthr;
+                if (i >= kSeqTile) break;
+                u64 n = 1, d = 1;
+                if (tbase + i < J.L) {
+                    u64 h = gl::add_nc(gl::mul_nc(xb[k].y, J.beta), xb[k].x);
+                    h = gl::add_nc(gl::mul_nc(h, J.beta), xa[k].y);
+                    h = gl::add_nc(gl::mul_nc(h, J.beta), xa[k].x);
+                    n = gl::sub(J.alpha, gl::canon(h));
+                    h = gl::add_nc(gl::mul_nc(yb[k].y, J.beta), yb[k].x);
+                    h = gl::add_nc(gl::mul_nc(h, J.beta), ya[k].y);
+                    h = gl::add_nc(gl::mul_nc(h, J.beta), ya[k].x);
+                    d = gl::sub(J.alpha, gl::canon(h));
+                }
+                bn[seq_pad(i)] = n;
+                bd[seq_pad(i)] = d;
             }
         }
-#pragma unroll
-        for (u32 k = 0; k < H; k++) {
-            const u32 i = threadIdx.x + (r * H + k) * kSeqThreads;
-            u64 v = 1;
-            if (tbase + i < L) {
-                u64 h = gl::add_nc(gl::mul_nc(b[k].y, beta), b[k].x);
-                h = gl::add_nc(gl::mul_nc(h, beta), a[k].y);
-                h = gl::add_nc(gl::mul_nc(h, beta), a[k].x);
-                v = gl::sub(alpha, gl::canon(h));
-            }
-            out[seq_pad(i)] = v;
+    } else {
+        for (u32 i = j; i < kSeqTile; i += nthr) {
+            u64 n, d;
+            seq_terms(J, tbase + i, n, d);
+            bn[seq_pad(i)] = n;
+            bd[seq_pad(i)] = d;
         }
     }
 }
@@ -275,61 +295,51 @@ __device__ __forceinline__ void seq_lookback(const SeqJob& J, u32 tile, u64 Nt, 
     }
 }
 
-// The scan.  A CTA takes tiles from the global counter until none is left.
-// For each: coalesced loads (thread t, elements t + 256 k) compress the
-// tuples into shared memory; thread t then owns the contiguous elements
-// 8t .. 8t+7 and forms their products; block scans give the numerators of
-// the earlier threads and the denominators of the later ones; warp 0 does
-// the look-back and the one inversion; Z goes out through shared memory for
-// coalesced stores.
-__global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const SeqJob* __restrict__ jobs, u32 njobs, u32 ntiles,
-                                                            SeqTile* st, u32* flags, u32* counter, u32* err)
+// The scan.  A CTA takes tiles from the global counter until none is left,
+// one tile ahead: while warp 0 runs the look-back and the inversion of the
+// current tile (a chain of dependent products), warps 1..7 already compute
+// the next tile's terms into the other half of the double buffer.  Per tile:
+// the terms (coalesced loads, thread j taking elements j + 224 k or
+// j + 256 k) land in shared memory; thread t then owns the contiguous
+// elements 8t .. 8t+7 and forms their products; block scans give the
+// numerators of the earlier threads and the denominators of the later ones;
+// Z goes out through shared memory for coalesced stores.
+__global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const SeqJob* __restrict__ jobs, u32 njobs,
+                                                                          u32 ntiles, SeqTile* st, u32* flags,
+                                                                          u32* counter, u32* err)
 {
     __shared__ u64 sh[32];
-    __shared__ u64 s_num[kSeqTile + kSeqTile / 8];
-    __shared__ u64 s_den[kSeqTile + kSeqTile / 8];
+    __shared__ u64 s_num[2][kSeqTile + kSeqTile / 8];
+    __shared__ u64 s_den[2][kSeqTile + kSeqTile / 8];
     __shared__ u64 s_tot[2];  // the tile's numerator and denominator products
     __shared__ u64 s_k;       // N_pre (D_pre D_tile)^-1
-    __shared__ u32 s_tile;
+    __shared__ u32 s_tile[2];
     const u32 t = threadIdx.x;
-    for (;;) {
-        if (t == 0) s_tile = atomicAdd(counter, 1u);
-        __syncthreads();
-        const u32 tile = s_tile;
-        if (tile >= ntiles) break;
+    if (t == 0) s_tile[0] = atomicAdd(counter, 1u);
+    __syncthreads();
+    u32 tile = s_tile[0];
+    u32 b = 0;
+    if (tile < ntiles) {
+        const SeqJob& J = jobs[seq_find(jobs, njobs, tile)];
+        seq_load(J, (u64)(tile - J.tile0) * kSeqTile, s_num[0], s_den[0], 0, blockDim.x);
+    }
+    __syncthreads();
+    while (tile < ntiles) {
         const SeqJob& J = jobs[seq_find(jobs, njobs, tile)];
         const u64 tbase = (u64)(tile - J.tile0) * kSeqTile;
-        if (J.T == 4 && !(((uintptr_t)J.x | (uintptr_t)J.y) & 15)) {
-            // Width-4 tuples (the query circuit's (list, slot, distance,
-            // item)): all eight tuples of X, then of Y, are requested before
-            // any is compressed, sixteen 16-byte loads in flight per thread.
-            seq_terms4(J.x, J.L, tbase, J.alpha, J.beta, s_num);
-            seq_terms4(J.y, J.L, tbase, J.alpha, J.beta, s_den);
-        } else {
-#pragma unroll
-            for (u32 k = 0; k < kSeqPer; k++) {
-                const u32 i = t + k * kSeqThreads;
-                u64 n, d;
-                seq_terms(J, tbase + i, n, d);
-                s_num[seq_pad(i)] = n;
-                s_den[seq_pad(i)] = d;
-            }
-        }
-        __syncthreads();
-        u64 num[kSeqPer], den[kSeqPer];
+        if (t == 0) s_tile[b ^ 1] = atomicAdd(counter, 1u);  // the next tile, seen after the scans' barriers
         u64 pn = 1, pd = 1;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
-            num[k] = s_num[seq_pad(kSeqPer * t + k)];
-            den[k] = s_den[seq_pad(kSeqPer * t + k)];
-            pn = gl::mul(pn, num[k]);
-            pd = gl::mul(pd, den[k]);
+            pn = gl::mul(pn, s_num[b][seq_pad(kSeqPer * t + k)]);
+            pd = gl::mul(pd, s_den[b][seq_pad(kSeqPer * t + k)]);
         }
         const u64 en = block_exclusive<false>(pn, sh);  // numerators of the earlier threads
         const u64 sd = block_exclusive<true>(pd, sh);   // denominators of the later threads
         if (t == blockDim.x - 1) s_tot[0] = gl::mul(en, pn);
         if (t == 0) s_tot[1] = gl::mul(sd, pd);
         __syncthreads();
+        const u32 next = s_tile[b ^ 1];
         if (t < 32) {
             u64 Np, Dp;
             seq_lookback(J, tile, s_tot[0], s_tot[1], st, flags, err, Np, Dp);
@@ -338,9 +348,18 @@ __global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const
                 if (inv == 0) atomicOr(J.status, 1u);
                 s_k = gl::mul(Np, inv);
             }
+        } else if (next < ntiles) {
+            const SeqJob& Jn = jobs[seq_find(jobs, njobs, next)];
+            seq_load(Jn, (u64)(next - Jn.tile0) * kSeqTile, s_num[b ^ 1], s_den[b ^ 1], 32, blockDim.x - 32);
         }
         __syncthreads();
         // Z_i = N_pre N_{<i} D_{>=i} (D_pre D_tile)^-1, D_{>=i} within the tile.
+        u64 num[kSeqPer], den[kSeqPer];
+#pragma unroll
+        for (u32 k = 0; k < kSeqPer; k++) {
+            num[k] = s_num[b][seq_pad(kSeqPer * t + k)];
+            den[k] = s_den[b][seq_pad(kSeqPer * t + k)];
+        }
         u64 N = gl::mul(s_k, en);
         u64 S = sd;
         u64 suf[kSeqPer];
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const
         const u64 ebase = tbase + (u64)kSeqPer * t;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
-            s_num[seq_pad(kSeqPer * t + k)] = gl::mul(N, suf[k]);  // every read of s_num is done
+            s_num[b][seq_pad(kSeqPer * t + k)] = gl::mul(N, suf[k]);  // each thread rewrites only its own words
             N = gl::mul(N, num[k]);
             if (ebase + k + 1 == J.L) J.z[J.L] = N;
         }
@@ -360,9 +379,11 @@ __global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
             const u32 i = t + k * kSeqThreads;
-            if (tbase + i < J.L) __stcs(J.z + tbase + i, s_num[seq_pad(i)]);
+            if (tbase + i < J.L) __stcs(J.z + tbase + i, s_num[b][seq_pad(i)]);
         }
         __syncthreads();
+        tile = next;
+        b ^= 1;
     }
 }
 

@@ -712,6 +712,7 @@ v3c_status v3c_destroy(v3c_ctx* ctx)
     if (ctx->arena.ev) cudaEventDestroy(ctx->arena.ev);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
     if (ctx->release_stream) cudaStreamDestroy(ctx->release_stream);
+    if (ctx->readback_stream) cudaStreamDestroy(ctx->readback_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->copy_fork) cudaEventDestroy(ctx->copy_fork);
     for (auto e : ctx->copy_events) cudaEventDestroy(e);
@@ -799,6 +800,16 @@ namespace detail {
 v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64* ids, cudaStream_t s,
                          u64* arena_override, size_t arena_words, const u64* preassigned_ids, bool allow_graph)
 {
+    // Large host inputs on the direct commit path are copied in column chunks
+    // on the context's copy stream into a buffer of their own (not the shared
+    // arena), so the copies need not wait for earlier work on the stream and
+    // overlap the previous commit's kernels; stages A and B of a chunk start
+    // when its copy lands.
+    const bool may_chunk = !arena_override && allow_graph && !(ctx->cfg.flags & V3C_FLAG_VALIDATE);
+    auto chunked = [&](const v3c_commit_desc& d) {
+        return may_chunk && d.on_device != V3C_INPUT_DEVICE && d.c >= 16 &&
+               ((size_t)d.c << d.log_n) >= ((size_t)1 << 22);
+    };
     size_t need = 0, scratch = 0, staged = 0;
     for (u32 i = 0; i < nb; i++) {
         const v3c_commit_desc& d = descs[i];
@@ -807,7 +818,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
                         d.rate_bits, d.cap_height);
         need += v3c_commit_footprint(d.c, d.log_n, d.rate_bits, d.cap_height);
         scratch += lde_scratch_words(d.c, d.log_n, d.rate_bits);
-        if (d.on_device != V3C_INPUT_DEVICE) staged += (size_t)d.c << d.log_n;
+        if (d.on_device != V3C_INPUT_DEVICE && !chunked(d)) staged += (size_t)d.c << d.log_n;
     }
     if (!arena_override && ctx->resident + need > ctx->cfg.hbm_budget_bytes)
         return fail(ctx, V3C_ENOMEM, "v3c_commit: %zu bytes requested, %zu resident, budget %llu", need,
@@ -871,30 +882,33 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
     }
     Batch b;
     size_t aoff = 0;
-    // Large host inputs on the direct commit path are copied in column chunks
-    // on the context's copy stream; stages A and B of a chunk start when its
-    // copy lands, so the transfer overlaps the first chunks' DFTs.
-    const bool may_chunk = !arena_override && allow_graph && !(ctx->cfg.flags & V3C_FLAG_VALIDATE);
-    bool forked = false;
+    std::vector<u64*> staged_bufs;  // per-commit input buffers, freed on s after the stages
+    auto rollback_all = [&](u32 upto) {
+        for (u64* p : staged_bufs) cudaFreeAsync(p, ctx->copy_stream);
+        staged_bufs.clear();
+        rollback(upto);
+    };
+    if (!ctx->copy_fork) CK(cudaEventCreateWithFlags(&ctx->copy_fork, cudaEventDisableTiming));
+    CK(cudaEventRecord(ctx->copy_fork, s));  // "ready at once" for the groups that wait on no copy
     for (u32 i = 0; i < nb; i++) {
         const v3c_commit_desc& d = descs[i];
         Object& o = objs[i];
         const u64* x = d.cols;
         size_t n = (size_t)1 << d.log_n;
-        if (may_chunk && d.on_device != V3C_INPUT_DEVICE && d.c >= 16 && ((size_t)d.c << d.log_n) >= ((size_t)1 << 22)) {
+        if (chunked(d)) {
             if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-            if (!forked) {
-                // The copies overwrite arena words that earlier work on s may still read.
-                if (!ctx->copy_fork) CK(cudaEventCreateWithFlags(&ctx->copy_fork, cudaEventDisableTiming));
-                CK(cudaEventRecord(ctx->copy_fork, s));
-                CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_fork, 0));
-                forked = true;
+            u64* in = nullptr;
+            cudaError_t ea = cudaMallocAsync((void**)&in, ((size_t)d.c << d.log_n) * 8, ctx->copy_stream);
+            if (ea != cudaSuccess) {
+                cudaGetLastError();
+                rollback_all(nb);
+                return fail(ctx, V3C_ENOMEM, "v3c_commit: input staging buffer: %s", cudaGetErrorString(ea));
             }
+            staged_bufs.push_back(in);
             const u32 per = ((d.c + kCopyChunks - 1) / kCopyChunks + 3) & ~3u;  // columns per chunk, multiple of 4
             for (u32 c0 = 0; c0 < d.c; c0 += per) {
                 const u32 ck = std::min(per, d.c - c0);
-                u64* dst = arena + aoff;
-                aoff = align_words(aoff + (size_t)ck * n);
+                u64* dst = in + (size_t)c0 * n;
                 size_t sw = lde_scratch_words(ck, d.log_n, d.rate_bits);
                 u64* scr = sw ? arena + aoff : nullptr;
                 aoff = align_words(aoff + sw);
@@ -909,13 +923,13 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
                 }
                 if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_events[g], ctx->copy_stream);
                 if (e != cudaSuccess) {
-                    rollback(nb);
+                    rollback_all(nb);
                     return fail(ctx, V3C_ECUDA, "input copy: %s", cudaGetErrorString(e));
                 }
                 LdeJob j;
                 st = make_lde_job(ctx, dst, ck, d.log_n, d.rate_bits, o.lde + c0, o.ld, scr, s, &j);
                 if (st) {
-                    rollback(nb);
+                    rollback_all(nb);
                     return st;
                 }
                 j.wcols = o.ld - c0;
@@ -930,7 +944,6 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         if (!b.chunks.empty()) {
             // Jobs outside the chunked inputs form one more group, ready at once.
             b.chunks.push_back({(u32)b.lde.size(), 1});
-            if (!ctx->copy_fork) CK(cudaEventCreateWithFlags(&ctx->copy_fork, cudaEventDisableTiming));
             b.chunk_ready.push_back(ctx->copy_fork);
         }
         if (d.on_device != V3C_INPUT_DEVICE) {
@@ -938,7 +951,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
             aoff = align_words(aoff + d.c * n);
             cudaError_t e = cudaMemcpyAsync(dst, d.cols, d.c * n * 8, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) {
-                rollback(nb);
+                rollback_all(nb);
                 return fail(ctx, V3C_ECUDA, "input copy: %s", cudaGetErrorString(e));
             }
             x = dst;
@@ -949,7 +962,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         LdeJob j;
         st = make_lde_job(ctx, x, d.c, d.log_n, d.rate_bits, o.lde, o.ld, scr, s, &j);
         if (st) {
-            rollback(nb);
+            rollback_all(nb);
             return st;
         }
         b.lde.push_back(j);
@@ -960,7 +973,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         for (auto& j : b.lde) {
             cudaError_t e = launch_validate(j.x, (u64)j.c << j.plan.log_n, ctx->d_flag, s);
             if (e != cudaSuccess) {
-                rollback(nb);
+                rollback_all(nb);
                 return fail(ctx, V3C_ECUDA, "validate: %s", cudaGetErrorString(e));
             }
             ctx->launches++;
@@ -969,7 +982,7 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         cudaError_t e = cudaMemcpyAsync(&flag, ctx->d_flag, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess || flag) {
-            rollback(nb);
+            rollback_all(nb);
             return e != cudaSuccess ? fail(ctx, V3C_ECUDA, "validate: %s", cudaGetErrorString(e))
                                     : fail(ctx, V3C_EINVAL, "v3c_commit: input not canonical (>= p)");
         }
@@ -989,9 +1002,11 @@ v3c_status commit_locked(v3c_ctx* ctx, const v3c_commit_desc* descs, u32 nb, u64
         st = launch_batch(ctx, b, s);
     else st = launch_batch_graph(ctx, b, s);
     if (st) {
-        rollback(nb);
+        rollback_all(nb);
         return st;
     }
+    // The staged inputs are read only by stages A and B, enqueued above.
+    for (u64* p : staged_bufs) CK(cudaFreeAsync(p, s));
     if (arena_need && !arena_override) {
         st = arena_release(ctx, s);
         if (st) return st;
@@ -1191,14 +1206,20 @@ v3c_status v3c_commit_cap(v3c_ctx* ctx, v3c_commit_id id, uint64_t* h_cap)
     v3c_status st = use_device(ctx);
     if (st) return st;
     Object o;
+    cudaStream_t rb = nullptr;
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         auto it = ctx->objects.find(id);
         if (it == ctx->objects.end()) return fail(ctx, V3C_ENOTFOUND, "commit id %llu", (unsigned long long)id);
         o = it->second;
+        if (!ctx->readback_stream) CK(cudaStreamCreateWithFlags(&ctx->readback_stream, cudaStreamNonBlocking));
+        rb = ctx->readback_stream;
     }
-    CK(cudaEventSynchronize(o.done));
-    CK(cudaMemcpy(h_cap, o.cap, ((size_t)4 << o.h) * 8, cudaMemcpyDeviceToHost));
+    // The copy waits for this object's work only (not for later work the
+    // caller has already enqueued on the producing stream).
+    CK(cudaStreamWaitEvent(rb, o.done, 0));
+    CK(cudaMemcpyAsync(h_cap, o.cap, ((size_t)4 << o.h) * 8, cudaMemcpyDeviceToHost, rb));
+    CK(cudaStreamSynchronize(rb));
     return V3C_OK;
 }
 
