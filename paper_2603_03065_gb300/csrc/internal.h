@@ -112,10 +112,13 @@ size_t stage_c_smem(const LdeJob& j, const Tiles& t);
 
 cudaError_t launch_stage_a(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
                            cudaStream_t s);
+// spec: every job of the launch satisfies lde_job_spec (the specialised kernel).
 cudaError_t launch_stage_b(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
-                           cudaStream_t s);
+                           cudaStream_t s, bool spec = false);
 cudaError_t launch_stage_c(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
-                           cudaStream_t s);
+                           cudaStream_t s, bool spec = false);
+// An LDE of columns with the 2^10 x 2^3 plan and the default tiles.
+bool lde_job_spec(const LdeJob& j);
 
 u32 leaf_items(const TreeJob& j, const Tiles& t);
 cudaError_t launch_leaf_hash(const TreeJob* d_jobs, StageList l, const Tiles& t, int grid, cudaStream_t s);

@@ -562,6 +562,10 @@ size_t stage_b_smem(const LdeJob& j)
     return (M + n2 + std::max<size_t>(n2 / 2, 1) + std::max<size_t>(M / 2, 1)) * sizeof(u64);
 }
 
+// SPEC: every job of the launch is an LDE of columns with the 2^10 x 2^3 plan
+// and the default tiles (lde_job_spec), so the shape is compile-time and
+// only that path is compiled (a smaller instruction footprint).
+template <bool SPEC>
 __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
@@ -570,7 +574,9 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
         u32 jid = find_job(L.first, L.njobs, item);
         const LdeJob& J = jobs[jid];
         u32 local = item - L.first[jid];
-        const u32 l1 = J.plan.log_n1, l2 = J.plan.log_n2, lM = J.plan.log_M, r = J.plan.r;
+        const u32 l1 = SPEC ? 10u : J.plan.log_n1, l2 = SPEC ? 10u : J.plan.log_n2;
+        const u32 lM = SPEC ? 13u : J.plan.log_M, r = SPEC ? 3u : J.plan.r;
+        const u32 kcap = SPEC ? 4u : J.kcap, mode = SPEC ? kLdeFromColumns : J.mode;
         const u32 n1 = 1u << l1, n2 = 1u << l2, M = 1u << lM;
         const u32 col = local >> l1, k1 = local & (n1 - 1);
         u64* data = sm;              // [M]
@@ -582,7 +588,7 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
             for (u32 e = threadIdx.x; e < M / 2; e += blockDim.x) twf[sw(e)] = J.plan.rfwd_M[e];
             cur_job = jid;
         }
-        if (J.mode == kLdeFromCoeffs) {
+        if (mode == kLdeFromCoeffs) {
             // Position t takes the coefficient a_{k1 + n1*bitrev(t)} (stride n1
             // in the natural-order table; the CTAs of neighbouring k1 share
             // its sectors through L2).
@@ -595,8 +601,8 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
                                 : J.x + ((size_t)col << J.plan.log_n);
             for (u32 e = threadIdx.x; e < n2; e += blockDim.x) stage[sw(e)] = __ldcs(src + e);
             __syncthreads();
-            dft_dif<true, false>(stage, 1, l2, twi, J.kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
-            if (J.mode == kCoeffsOut) {
+            dft_dif<true, false>(stage, 1, l2, twi, kcap);  // position t: n * a_{k1 + n1*bitrev(t)}
+            if (mode == kCoeffsOut) {
                 u64* dst = J.lde + ((size_t)col << J.plan.log_n) + k1;
                 for (u32 t = threadIdx.x; t < n2; t += blockDim.x)
                     dst[(size_t)gl::bitrev(t, l2) << l1] = gl::mul(stage[sw(t)], J.cscale);
@@ -611,14 +617,14 @@ __global__ void __launch_bounds__(256, 2) k_stage_b(const LdeJob* __restrict__ j
         // into the 2^r slots after it, so they are applied here directly.
         for (u32 t = threadIdx.x; t < n2; t += blockDim.x) stage[sw(t)] = gl::mul(stage[sw(t)], sc[t]);
         __syncthreads();
-        if (l1 && lM == 13 && r == 3 && blockDim.x == 256 && J.kcap >= 4) {
+        if (SPEC || (l1 && lM == 13 && r == 3 && blockDim.x == 256 && kcap >= 4)) {
             stage_b_forward_8192(stage, data, twf, J.Z + ((size_t)col << J.plan.log_N), k1, l1, __ffs(J.c_q) - 1);
             __syncthreads();
             continue;
         }
         for (u32 e = threadIdx.x; e < M; e += blockDim.x) data[sw(e)] = stage[sw(e >> r)];
         __syncthreads();
-        dft_dit<false>(data, 1, lM, twf, r, J.kcap + 1);  // the forward M-point transform may use radix 2^5
+        dft_dit<false>(data, 1, lM, twf, r, kcap + 1);  // the forward M-point transform may use radix 2^5
         if (l1) {
             // Z is q-blocked: block q >> lQ holds [k1][q & (Q-1)], so that
             // stage C reads one contiguous run per column.  The four-step
@@ -713,6 +719,8 @@ __device__ __forceinline__ void stage_c_load(const LdeJob& J, u64* data, u32 cg,
     }
 }
 
+// SPEC: as for stage B (n1 = 2^10, Z blocks of 4 q values, 2 per CTA).
+template <bool SPEC>
 __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
@@ -721,10 +729,10 @@ __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ j
         u32 jid = find_job(L.first, L.njobs, item);
         const LdeJob& J = jobs[jid];
         u32 local = item - L.first[jid];
-        const u32 l1 = J.plan.log_n1, lM = J.plan.log_M;
+        const u32 l1 = SPEC ? 10u : J.plan.log_n1, lM = SPEC ? 13u : J.plan.log_M;
         const u32 n1 = 1u << l1;
-        const u32 Qz = J.c_q, lQz = __ffs(Qz) - 1;  // Z block size
-        const u32 Q = J.c_qc, lQ = __ffs(Q) - 1;    // q values of this CTA
+        const u32 Qz = SPEC ? 4u : J.c_q, lQz = __ffs(Qz) - 1;  // Z block size
+        const u32 Q = SPEC ? 2u : J.c_qc, lQ = __ffs(Q) - 1;    // q values of this CTA
         const u32 groups = (J.c + kStageCCols - 1) / kStageCCols;
         const u32 cg = local % groups, qt = local / groups;
         const u32 q0 = qt << lQ;
@@ -743,7 +751,9 @@ __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ j
         const u32 Jn = n1 / blockDim.x;
         // The fast path's 16-byte loads need Z 16-byte aligned (every offset
         // added to it is an even number of words).
-        if (n1 >= blockDim.x && per == 8 * blockDim.x && blockDim.x == 256 && ((uintptr_t)J.Z & 15) == 0) {
+        if (SPEC && ((uintptr_t)J.Z & 15) == 0) {
+            stage_c_load<4>(J, data, cg, q0, qb, qoff);
+        } else if (n1 >= blockDim.x && per == 8 * blockDim.x && blockDim.x == 256 && ((uintptr_t)J.Z & 15) == 0) {
             switch (Jn) {
             case 1: stage_c_load<1>(J, data, cg, q0, qb, qoff); break;
             case 2: stage_c_load<2>(J, data, cg, q0, qb, qoff); break;
@@ -767,7 +777,7 @@ __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ j
         __syncthreads();
         // Radix 2^4 at three CTAs per SM measured faster here than radix 2^5 at
         // two (12.5 against 13.1 ms on the 135 x 2^20 commit).
-        dft_dif<false, true, 4>(data, kStageCCols * Q, l1, tw, J.kcap);
+        dft_dif<false, true, 4>(data, kStageCCols * Q, l1, tw, SPEC ? 4u : J.kcap);
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
@@ -853,16 +863,24 @@ cudaError_t launch_stage_a(const LdeJob* d_jobs, StageList l, size_t smem, const
     return launch_persistent(k_stage_a, t.a_threads, smem, grid, s, d_jobs, l);
 }
 
-cudaError_t launch_stage_b(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
-                           cudaStream_t s)
+bool lde_job_spec(const LdeJob& j)
 {
-    return launch_persistent(k_stage_b, t.b_threads, smem, grid, s, d_jobs, l);
+    return j.mode == kLdeFromColumns && j.plan.log_n1 == 10 && j.plan.log_n2 == 10 && j.plan.r == 3 &&
+           j.kcap == 4 && j.c_q == 4 && j.c_qc == 2;
+}
+
+cudaError_t launch_stage_b(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
+                           cudaStream_t s, bool spec)
+{
+    if (spec && t.b_threads == 256) return launch_persistent(k_stage_b<true>, 256, smem, grid, s, d_jobs, l);
+    return launch_persistent(k_stage_b<false>, t.b_threads, smem, grid, s, d_jobs, l);
 }
 
 cudaError_t launch_stage_c(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
-                           cudaStream_t s)
+                           cudaStream_t s, bool spec)
 {
-    return launch_persistent(k_stage_c, t.c_threads, smem, grid, s, d_jobs, l);
+    if (spec && t.c_threads == 256) return launch_persistent(k_stage_c<true>, 256, smem, grid, s, d_jobs, l);
+    return launch_persistent(k_stage_c<false>, t.c_threads, smem, grid, s, d_jobs, l);
 }
 
 // ---------------------------------------------------------------- misc kernels

@@ -245,6 +245,13 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
         return l;
     };
     u32 nl = (u32)b.lde.size(), nt = (u32)b.tree.size();
+    // The specialised stage kernels when every job of the launch has the
+    // large commit's plan and the default tiles.
+    auto all_spec = [&](u32 first, u32 count) {
+        for (u32 k = first; k < first + count; k++)
+            if (!lde_job_spec(b.lde[k])) return false;
+        return count > 0;
+    };
     auto stage = [&](int id, cudaError_t (*fn)(const Batch&, const Tiles&, StageList, const LdeJob*,
                                                const TreeJob*, size_t, cudaStream_t),
                      StageList l, size_t g) -> v3c_status {
@@ -272,7 +279,7 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
             }
             if (lb.total) {
                 StageTimer tm(ctx, timed ? 1 : -1, s);
-                CK(launch_stage_b(dj, lb, b.smem_b, t, 0, s));
+                CK(launch_stage_b(dj, lb, b.smem_b, t, 0, s, all_spec(b.chunks[g].first, nj)));
                 tm.done();
                 ctx->launches++;
             }
@@ -282,15 +289,17 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
                          cudaStream_t s) { return launch_stage_a(dl, l, b.smem_a, t, 0, s); },
                    list(2, b.fa, nl), 0);
         if (st) return st;
-        st = stage(1, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
-                         cudaStream_t s) { return launch_stage_b(dl, l, b.smem_b, t, 0, s); },
-                   list(3, b.fb, nl), 0);
+        const bool spec_b = all_spec(0, nl);
+        st = stage(1, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t g,
+                         cudaStream_t s) { return launch_stage_b(dl, l, b.smem_b, t, 0, s, g != 0); },
+                   list(3, b.fb, nl), spec_b ? 1 : 0);
         if (st) return st;
     }
     if (nl) {
-        st = stage(2, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
-                         cudaStream_t s) { return launch_stage_c(dl, l, b.smem_c, t, 0, s); },
-                   list(4, b.fc, nl), 0);
+        const bool spec_c = all_spec(0, nl);
+        st = stage(2, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t g,
+                         cudaStream_t s) { return launch_stage_c(dl, l, b.smem_c, t, 0, s, g != 0); },
+                   list(4, b.fc, nl), spec_c ? 1 : 0);
         if (st) return st;
     }
     if (nt && !b.leaves_ready) {
