@@ -232,6 +232,77 @@ __global__ void __launch_bounds__(256) k_fri_combine_ext(const u64* __restrict__
     }
 }
 
+// The same combination with two adjacent rows per thread: each 16-byte load
+// of alpha powers serves both rows, and the two rows' accumulator chains are
+// independent work for the same instructions' latencies.
+__global__ void __launch_bounds__(256, 2) k_fri_combine_ext2(const u64* __restrict__ rows, u32 ld, u32 c,
+                                                             const u64* __restrict__ pw, u64 nrows, int acc,
+                                                             u64* __restrict__ f)
+{
+    const u32 pairs = c >> 1;
+    const ulonglong2* pw2 = reinterpret_cast<const ulonglong2*>(pw);
+    for (u64 t = 2 * (blockIdx.x * (u64)blockDim.x + threadIdx.x); t < nrows; t += 2 * (u64)gridDim.x * blockDim.x) {
+        const bool two = t + 1 < nrows;
+        const ulonglong2* ra = reinterpret_cast<const ulonglong2*>(rows + t * ld);
+        const ulonglong2* rb = reinterpret_cast<const ulonglong2*>(rows + (two ? t + 1 : t) * ld);
+        u64 la0 = 0, ma0 = 0, la1 = 0, ma1 = 0, lb0 = 0, mb0 = 0, lb1 = 0, mb1 = 0;
+        u32 ha0 = 0, ha1 = 0, hb0 = 0, hb1 = 0;
+        u32 k = 0;
+        for (; k + kCombPairs <= pairs; k += kCombPairs) {
+            ulonglong2 va[kCombPairs], vb[kCombPairs];
+#pragma unroll
+            for (int j = 0; j < kCombPairs; j++) {
+                va[j] = __ldg(ra + k + j);
+                vb[j] = __ldg(rb + k + j);
+            }
+#pragma unroll
+            for (int j = 0; j < kCombPairs; j++) {
+                const ulonglong2 p0 = __ldg(pw2 + 2 * (k + j)), p1 = __ldg(pw2 + 2 * (k + j) + 1);
+                mac192(la0, ma0, ha0, va[j].x, p0.x);
+                mac192(la1, ma1, ha1, va[j].x, p0.y);
+                mac192(la0, ma0, ha0, va[j].y, p1.x);
+                mac192(la1, ma1, ha1, va[j].y, p1.y);
+                mac192(lb0, mb0, hb0, vb[j].x, p0.x);
+                mac192(lb1, mb1, hb1, vb[j].x, p0.y);
+                mac192(lb0, mb0, hb0, vb[j].y, p1.x);
+                mac192(lb1, mb1, hb1, vb[j].y, p1.y);
+            }
+        }
+        for (; k < pairs; k++) {
+            const ulonglong2 a = __ldg(ra + k), b = __ldg(rb + k);
+            const ulonglong2 p0 = __ldg(pw2 + 2 * k), p1 = __ldg(pw2 + 2 * k + 1);
+            mac192(la0, ma0, ha0, a.x, p0.x);
+            mac192(la1, ma1, ha1, a.x, p0.y);
+            mac192(la0, ma0, ha0, a.y, p1.x);
+            mac192(la1, ma1, ha1, a.y, p1.y);
+            mac192(lb0, mb0, hb0, b.x, p0.x);
+            mac192(lb1, mb1, hb1, b.x, p0.y);
+            mac192(lb0, mb0, hb0, b.y, p1.x);
+            mac192(lb1, mb1, hb1, b.y, p1.y);
+        }
+        if (c & 1) {
+            const u64 xa = __ldg(rows + t * ld + c - 1), xb = __ldg(rows + (two ? t + 1 : t) * ld + c - 1);
+            const ulonglong2 p0 = __ldg(pw2 + c - 1);
+            mac192(la0, ma0, ha0, xa, p0.x);
+            mac192(la1, ma1, ha1, xa, p0.y);
+            mac192(lb0, mb0, hb0, xb, p0.x);
+            mac192(lb1, mb1, hb1, xb, p0.y);
+        }
+        u64 r0 = fold192(la0, ma0, ha0), r1 = fold192(la1, ma1, ha1);
+        u64 s0 = fold192(lb0, mb0, hb0), s1 = fold192(lb1, mb1, hb1);
+        if (acc) {
+            r0 = gl::add(f[2 * t], r0);
+            r1 = gl::add(f[2 * t + 1], r1);
+            if (two) {
+                s0 = gl::add(f[2 * t + 2], s0);
+                s1 = gl::add(f[2 * t + 3], s1);
+            }
+        }
+        reinterpret_cast<ulonglong2*>(f)[t] = make_ulonglong2(r0, r1);
+        if (two) reinterpret_cast<ulonglong2*>(f)[t + 1] = make_ulonglong2(s0, s1);
+    }
+}
+
 // Per-round fold constants.  Step m of a round pairs positions (2u, 2u+1) of
 // the intermediate layer; with u = w 2^b + v' (b = a-1-m) the point of
 // position 2u is x = s^(2^m) w_{2^(b+1)}^bitrev_b(v') (w_{N_k}^e)^(2^m),
@@ -663,8 +734,8 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
         int grid = (int)std::min<u64>((u64)std::max(nb, 1) * num_sms(), (N + 255) / 256);
         StageTimer tm(ctx, 5, s);
         if (ext == 2)
-            k_fri_combine_ext<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + 2 * (size_t)e0, N,
-                                                                i > 0, st->f[0]);
+            k_fri_combine_ext2<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + 2 * (size_t)e0, N,
+                                                                 i > 0, st->f[0]);
         else
             k_fri_combine<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + e0, N, i > 0, st->f[0]);
         CKB(cudaGetLastError());

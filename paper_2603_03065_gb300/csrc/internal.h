@@ -112,11 +112,11 @@ size_t stage_c_smem(const LdeJob& j, const Tiles& t);
 
 cudaError_t launch_stage_a(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
                            cudaStream_t s);
-// spec: every job of the launch satisfies lde_job_spec (the specialised kernel).
+// spec: every job of the launch satisfies lde_job_spec (stage B's specialised kernel).
 cudaError_t launch_stage_b(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
                            cudaStream_t s, bool spec = false);
 cudaError_t launch_stage_c(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
-                           cudaStream_t s, bool spec = false);
+                           cudaStream_t s);
 // An LDE of columns with the 2^10 x 2^3 plan and the default tiles.
 bool lde_job_spec(const LdeJob& j);
 

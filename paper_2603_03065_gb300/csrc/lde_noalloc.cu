@@ -134,6 +134,6 @@ extern "C" v3c_status v3c_lde_noalloc(const uint64_t* d_cols, uint32_t c, uint32
     if (na && launch_stage_a(dj, la, stage_a_smem(j, t), t, 0, s) != cudaSuccess) return V3C_ECUDA;
     const bool spec = lde_job_spec(j);
     if (nb && launch_stage_b(dj, lb, stage_b_smem(j), t, 0, s, spec) != cudaSuccess) return V3C_ECUDA;
-    if (nc && launch_stage_c(dj, lc, stage_c_smem(j, t), t, 0, s, spec) != cudaSuccess) return V3C_ECUDA;
+    if (nc && launch_stage_c(dj, lc, stage_c_smem(j, t), t, 0, s) != cudaSuccess) return V3C_ECUDA;
     return V3C_OK;
 }

@@ -719,8 +719,6 @@ __device__ __forceinline__ void stage_c_load(const LdeJob& J, u64* data, u32 cg,
     }
 }
 
-// SPEC: as for stage B (n1 = 2^10, Z blocks of 4 q values, 2 per CTA).
-template <bool SPEC>
 __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ jobs, StageList L)
 {
     extern __shared__ u64 sm[];
@@ -729,10 +727,10 @@ __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ j
         u32 jid = find_job(L.first, L.njobs, item);
         const LdeJob& J = jobs[jid];
         u32 local = item - L.first[jid];
-        const u32 l1 = SPEC ? 10u : J.plan.log_n1, lM = SPEC ? 13u : J.plan.log_M;
+        const u32 l1 = J.plan.log_n1, lM = J.plan.log_M;
         const u32 n1 = 1u << l1;
-        const u32 Qz = SPEC ? 4u : J.c_q, lQz = __ffs(Qz) - 1;  // Z block size
-        const u32 Q = SPEC ? 2u : J.c_qc, lQ = __ffs(Q) - 1;    // q values of this CTA
+        const u32 Qz = J.c_q, lQz = __ffs(Qz) - 1;  // Z block size
+        const u32 Q = J.c_qc, lQ = __ffs(Q) - 1;    // q values of this CTA
         const u32 groups = (J.c + kStageCCols - 1) / kStageCCols;
         const u32 cg = local % groups, qt = local / groups;
         const u32 q0 = qt << lQ;
@@ -751,9 +749,7 @@ __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ j
         const u32 Jn = n1 / blockDim.x;
         // The fast path's 16-byte loads need Z 16-byte aligned (every offset
         // added to it is an even number of words).
-        if (SPEC && ((uintptr_t)J.Z & 15) == 0) {
-            stage_c_load<4>(J, data, cg, q0, qb, qoff);
-        } else if (n1 >= blockDim.x && per == 8 * blockDim.x && blockDim.x == 256 && ((uintptr_t)J.Z & 15) == 0) {
+        if (n1 >= blockDim.x && per == 8 * blockDim.x && blockDim.x == 256 && ((uintptr_t)J.Z & 15) == 0) {
             switch (Jn) {
             case 1: stage_c_load<1>(J, data, cg, q0, qb, qoff); break;
             case 2: stage_c_load<2>(J, data, cg, q0, qb, qoff); break;
@@ -777,7 +773,7 @@ __global__ void __launch_bounds__(256, 3) k_stage_c(const LdeJob* __restrict__ j
         __syncthreads();
         // Radix 2^4 at three CTAs per SM measured faster here than radix 2^5 at
         // two (12.5 against 13.1 ms on the 135 x 2^20 commit).
-        dft_dif<false, true, 4>(data, kStageCCols * Q, l1, tw, SPEC ? 4u : J.kcap);
+        dft_dif<false, true, 4>(data, kStageCCols * Q, l1, tw, J.kcap);
         const u32 c0 = kStageCCols * cg;
         for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
             u32 u = e & (n1 - 1), v = e >> l1;
@@ -877,10 +873,10 @@ cudaError_t launch_stage_b(const LdeJob* d_jobs, StageList l, size_t smem, const
 }
 
 cudaError_t launch_stage_c(const LdeJob* d_jobs, StageList l, size_t smem, const Tiles& t, int grid,
-                           cudaStream_t s, bool spec)
+                           cudaStream_t s)
 {
-    if (spec && t.c_threads == 256) return launch_persistent(k_stage_c<true>, 256, smem, grid, s, d_jobs, l);
-    return launch_persistent(k_stage_c<false>, t.c_threads, smem, grid, s, d_jobs, l);
+    // A stage C specialised like stage B's measured slower (13.0 against 12.5 ms).
+    return launch_persistent(k_stage_c, t.c_threads, smem, grid, s, d_jobs, l);
 }
 
 // ---------------------------------------------------------------- misc kernels

@@ -296,10 +296,9 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
         if (st) return st;
     }
     if (nl) {
-        const bool spec_c = all_spec(0, nl);
-        st = stage(2, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t g,
-                         cudaStream_t s) { return launch_stage_c(dl, l, b.smem_c, t, 0, s, g != 0); },
-                   list(4, b.fc, nl), spec_c ? 1 : 0);
+        st = stage(2, [](const Batch& b, const Tiles& t, StageList l, const LdeJob* dl, const TreeJob*, size_t,
+                         cudaStream_t s) { return launch_stage_c(dl, l, b.smem_c, t, 0, s); },
+                   list(4, b.fc, nl), 0);
         if (st) return st;
     }
     if (nt && !b.leaves_ready) {
