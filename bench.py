@@ -823,7 +823,7 @@ FRI_CFG = (4, 5, 4)   # arity 2^4, final polynomial 2^5 values, cap height 4 per
 FRI_EXT = 2           # challenges and layers in the quadratic extension (Plonky2's default)
 # DRAM traffic of one k_fri_combine launch on the 135 x 2^20 workload, from an
 # ncu capture of the same kernel.  Drop the entry when the kernel changes.
-FRI_COMBINE_TRAFFIC = {"fri_135x2_20": 9.657e9}
+FRI_COMBINE_TRAFFIC: dict = {}
 
 
 def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
@@ -970,7 +970,7 @@ def run_fri(args):
                     "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(launches),
             "clocks": clk,
-            "roofline": {"bound": "hbm", "kernel": "k_fri_combine_ext" if FRI_EXT == 2 else "k_fri_combine",
+            "roofline": {"bound": "hbm", "kernel": "k_fri_combine_ext2" if FRI_EXT == 2 else "k_fri_combine",
                          "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": FRI_COMBINE_TRAFFIC.get("fri_135x2_20"),
                          "bytes_per_launch": comb_bytes, "ms_per_launch": comb_per, "peak_source": "measured"},
