@@ -455,6 +455,10 @@ def run_v3c(args):
             # form, measured after the timed region of the line's value.
             try:
                 line["serving"] = serving_block(None, args.serve_duration, load=args.serve_load)
+                # 10 % above the serial capacity: the serial path falls behind,
+                # the served loop (more capacity) should keep up.
+                line["serving_over_serial_capacity"] = serving_block(None, args.serve_duration,
+                                                                     load=args.serve_load * 1.1)
             except Exception as e:  # pragma: no cover
                 line["serving"] = {"error": str(e)}
             try:

@@ -133,3 +133,33 @@ def test_borrowed_pinned_and_device_inputs(v3c):
             assert np.array_equal(done[t][0], want_cap)
             ctx.release(t)
         ctx.serve_stop()
+
+
+def test_small_requests_do_not_wait_for_a_large_one(v3c):
+    """Requests are batched by size class: small requests that arrive just
+    after a large one run as their own batch (on a higher-priority stream)
+    and finish before the large one, instead of completing with it."""
+    big = synth.Shape(c=135, log_n=18, rate_bits=3, cap_height=4, seed=13)
+    small = [synth.Shape(c=8, log_n=10, rate_bits=3, cap_height=4, seed=13, batch=b) for b in range(1, 6)]
+    xb = big.inputs()
+    xs = [s.inputs() for s in small]
+    with v3c.Context(0, max_inflight=4) as ctx:
+        # warm the plans of both shapes
+        ctx.release(ctx.commit([(xb, 3, 4)])[0])
+        ctx.release(ctx.commit([(xs[0], 3, 4)])[0])
+        ctx.serve_start(max_batch=8)
+        tb = ctx.serve_submit(xb, 3, 4)
+        ts = [ctx.serve_submit(x, 3, 4) for x in xs]
+        caps = {t: 4 for t in [tb] + ts}
+        done = wait_done(ctx, v3c, [tb] + ts, caps)
+        t_big = done[tb][1][3]
+        for t, s, x in zip(ts, small, xs):
+            cap, times = done[t]
+            assert times[3] < t_big, "a small request completed only with the large one"
+            _, _, want = oracle.commit(x, 3, 4)
+            assert np.array_equal(cap, want)
+        _, _, want_big = oracle.commit(xb, 3, 4)
+        assert np.array_equal(done[tb][0], want_big)
+        for t in [tb] + ts:
+            ctx.release(t)
+        ctx.serve_stop()
