@@ -355,3 +355,27 @@ def test_maximum_size_commit_sampled(v3c):
     with v3c.Context(0) as small:
         with pytest.raises(v3c.V3CError):
             small.commit([(v3c.to_device_u64(synth.columns(seed=1, c=1, log_n=log_n, mix="uniform")), 4, 0)])
+
+
+def test_pipelined_host_input_commits(v3c):
+    """Commits of large host inputs enqueued back to back, each cap read only
+    after the next commit is enqueued (the input copies of commit k+1 run on
+    the copy stream while commit k computes): every object equals the
+    oracle's commit of its own input."""
+    import torch
+
+    # 64 x 2^16 words: at the 2^22-word threshold of the chunked copy path
+    shapes = [synth.Shape(c=64, log_n=16, rate_bits=2, cap_height=3, seed=71, batch=b) for b in range(3)]
+    xs = [s.inputs() for s in shapes]
+    pinned = [torch.from_numpy(x.view(np.int64)).pin_memory().numpy().view(np.uint64) for x in xs]
+    with v3c.Context(0) as c:
+        stream = torch.cuda.current_stream()
+        ids = []
+        for p, s in zip(pinned, shapes):
+            ids.append(c.commit([(p, s.rate_bits, s.cap_height)], stream=stream)[0])
+        for cid, x, s in zip(ids, xs, shapes):
+            lde, tree, cap = oracle.commit(x, s.rate_bits, s.cap_height)
+            assert np.array_equal(c.cap(cid), cap)
+            got = c.commit_views(cid, s.c)
+            assert np.array_equal(got["lde"], lde)
+            c.release(cid)
