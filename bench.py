@@ -192,7 +192,7 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    if args.workload == "fri_135x2_20":
+    if args.workload in FRI_WORKLOADS:
         return run_reference_fri(args)
     if args.workload in ("snapshot_msmarco", "seteq_64x2_17"):
         return run_reference_other(args)
@@ -233,7 +233,8 @@ def run_reference_fri(args):
         "impl": "reference", "metric": FRI_METRIC, "value": base["value"], "unit": "Gelem/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "fri_135x2_20", "columns": 135, "log_rows": 20, "rate_bits": 3,
+        "config": {"workload": args.workload, "columns": FRI_WORKLOADS[args.workload].c,
+                   "log_rows": FRI_WORKLOADS[args.workload].log_n, "rate_bits": 3,
                    "arity_bits": FRI_CFG[0], "final_log": FRI_CFG[1], "layer_cap_height": FRI_CFG[2],
                    "queries": FRI_QUERIES, "ext_degree": FRI_EXT},
         "cpu_baseline": {k: base[k] for k in ("kind", "cores", "value", "unit", "sample")},
@@ -827,7 +828,13 @@ FRI_CFG = (4, 5, 4)   # arity 2^4, final polynomial 2^5 values, cap height 4 per
 FRI_EXT = 2           # challenges and layers in the quadratic extension (Plonky2's default)
 # DRAM traffic of one k_fri_combine launch on the 135 x 2^20 workload, from an
 # ncu capture of the same kernel.  Drop the entry when the kernel changes.
-FRI_COMBINE_TRAFFIC: dict = {}
+# DRAM bytes (read + write) of one k_fri_combine_tma<2> launch: the ncu capture of the 2^17-row
+# case, and that figure scaled by the 8x rows for the 2^20-row workload (same kernel and tiles,
+# traffic proportional to the rows).  Drop the entries when the kernel changes.
+FRI_COMBINE_TRAFFIC = {"fri_135x2_17": 1.194e9, "fri_135x2_20": 9.553e9}
+# The FRI workload, and a smaller capture case of the same kernels (1.1 GB of LDE).
+FRI_WORKLOADS = {"fri_135x2_20": synth.LARGE_135x2_20,
+                 "fri_135x2_17": synth.Shape(c=135, log_n=17, rate_bits=3, cap_height=4, seed=0)}
 
 
 def fri_cpu_baseline(s: "synth.Shape", steps: int = 1) -> dict:
@@ -885,7 +892,7 @@ def run_fri(args):
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
-    s = shard_workload(synth.LARGE_135x2_20, rank)
+    s = shard_workload(FRI_WORKLOADS[args.workload], rank)
     ctx = v3c.Context(local_rank, flags=v3c.FLAG_TIMING)
     stream = torch.cuda.current_stream()
     cid = ctx.commit([(v3c.to_device_u64(s.inputs()), s.rate_bits, s.cap_height)], stream=stream)[0]
@@ -964,7 +971,7 @@ def run_fri(args):
             "metric": FRI_METRIC, "value": value, "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "fri_135x2_20", "columns": s.c, "log_rows": s.log_n,
+            "config": {"workload": args.workload, "columns": s.c, "log_rows": s.log_n,
                        "rate_bits": s.rate_bits, "lde_rows": N, "arity_bits": a, "final_log": fl,
                        "layer_cap_height": h, "rounds": nr, "queries": FRI_QUERIES, "ext_degree": FRI_EXT,
                        "l2": "inputs larger than L2 (no flush needed)"},
@@ -974,9 +981,9 @@ def run_fri(args):
                     "ms_per_step": e2e_s * 1e3},
             "gpu_launches": int(launches),
             "clocks": clk,
-            "roofline": {"bound": "hbm", "kernel": "k_fri_combine_ext2" if FRI_EXT == 2 else "k_fri_combine",
+            "roofline": {"bound": "hbm", "kernel": "k_fri_combine_tma<%d>" % FRI_EXT,
                          "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": FRI_COMBINE_TRAFFIC.get("fri_135x2_20"),
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": FRI_COMBINE_TRAFFIC.get(args.workload),
                          "bytes_per_launch": comb_bytes, "ms_per_launch": comb_per, "peak_source": "measured"},
             "stages_ms_per_launch": stage_ms,
         }
@@ -1255,7 +1262,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["v3c", "reference"], default="v3c")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven_64", "serve_poisson", "fri_135x2_20",
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven_64", "serve_poisson", *sorted(FRI_WORKLOADS),
                                                                "snapshot_msmarco", "seteq_64x2_17"],
                     default="large_135x2_20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1283,7 +1290,7 @@ def main():
         return run_batched(args)
     if args.workload == "serve_poisson":
         return run_serving(args)
-    if args.workload == "fri_135x2_20":
+    if args.workload in FRI_WORKLOADS:
         return run_fri(args)
     if args.workload == "snapshot_msmarco":
         return run_snapshot(args)

@@ -9,16 +9,20 @@
 // with the same Poseidon Merkle kernels as the LDE.
 //
 // GB300 mapping: the combination streams the whole resident LDE once (the
-// only HBM-heavy step), one thread per row, 64-byte runs per load group and
-// an unreduced 192-bit sum per row.  A fold reads each coset (2^a
+// only HBM-heavy step): the tensor-memory accelerator copies tiles of 256
+// rows x 16 words into a ring of shared-memory stages and each thread sums
+// one row into an unreduced 192-bit accumulator (register loads, one row per
+// thread, where a shape does not fit a tensor map).  A fold reads each coset (2^a
 // contiguous values) into registers and applies a arity-2 steps there, one
 // output per thread.  The layer
 // trees go through the batched leaf-hash and Merkle launches.  Openings are
 // one gather launch per call over every (query, word) pair.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/v3c_fri.h"
@@ -47,6 +51,8 @@ struct FriState {
     u64* final_coef = nullptr;
     u64* pw_inv = nullptr;  // [3][512] powers of w_N^-1
     u64* alpha_pw = nullptr;
+    u32* err = nullptr;  // set by a combine whose bounded wait expired
+    bool err_checked = false;
     u32 committed = 0;  // layers [0, committed) have trees
     u64 query_words = 0;
     cudaEvent_t ev = nullptr;
@@ -307,6 +313,221 @@ __global__ void __launch_bounds__(256, 2) k_fri_combine_ext2(const u64* __restri
     }
 }
 
+// ------------------------------------------- combination fed by TMA tiles
+//
+// The register-load kernels above give each thread its own row, so one warp
+// load touches 32 rows (32 cache lines) and the L1's per-line throughput,
+// not DRAM, bounds them.  Here the tensor-memory accelerator copies tiles of
+// kTmaRows rows x kTmaCols words (one 128-byte line per row) from the LDE
+// into a ring of shared-memory stages, with the 128-byte swizzle: 16-byte
+// unit u of tile row r lands at unit u ^ (r mod 8) of that row's line, so the
+// eight threads of each quarter-warp phase (rows r..r+7, same unit) read
+// eight different bank groups.  One producer thread issues the copies;
+// consumer thread t owns tile row t and sums its words into the same
+// unreduced 192-bit accumulators as the register-load kernels.  Every wait
+// is bounded in time: on expiry the CTA records an error and stops, and the
+// producer waits (bounded) for the copies it issued before the CTA exits.
+constexpr u32 kTmaCols = 16;                        // words per tile row (128 bytes)
+constexpr u32 kTmaRows = 256;                       // tile rows = consumer threads
+constexpr u32 kTmaStages = 3;
+constexpr u32 kTmaBytes = kTmaCols * kTmaRows * 8;  // 32 KB per stage
+constexpr u32 kTmaThreads = kTmaRows + 32;          // consumers + one producer warp
+constexpr size_t kTmaSmem = (size_t)kTmaStages * kTmaBytes + 1024 + 128;
+constexpr u64 kTmaWaitNs = 1000000000ull;           // 1 s per wait
+
+struct TmaRing {
+    u64 full[kTmaStages];   // copy landed (producer's expect_tx + the copy's bytes)
+    u64 empty[kTmaStages];  // every consumer has read the stage
+    u32 abort;
+    u32 issued;
+};
+
+__device__ __forceinline__ u64 fri_global_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ u32 smem_addr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(u64* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(u64* bar, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity)
+{
+    u32 done;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t"
+        "}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for the phase of `bar` with the given parity; false after kTmaWaitNs.
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const u64 t0 = fri_global_ns();
+    for (u32 i = 1;; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0 && fri_global_ns() - t0 > kTmaWaitNs) return false;
+    }
+}
+
+// Tile (x, y) of the map (x in words, a multiple of kTmaCols; y in rows) into
+// shared memory at dst, completing `bar`'s transaction count.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u32 x, u32 y, u64* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<u64>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// f[t] (+)= sum_{i<c} alpha^i row_t[i] (EXT words per alpha power and per
+// output) over tiles of kTmaRows rows; requires c >= kTmaCols and
+// nrows >= kTmaRows (the host takes the register-load kernels otherwise).
+template <int EXT>
+__global__ void __launch_bounds__(kTmaThreads, 2) k_fri_combine_tma(const __grid_constant__ CUtensorMap map, u32 c,
+                                                                   const u64* __restrict__ pw, u64 nrows, int acc,
+                                                                   u64* __restrict__ f, u32* __restrict__ err)
+{
+    extern __shared__ unsigned char tma_raw[];
+    unsigned char* stage0 =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tma_raw) + 1023) & ~(uintptr_t)1023);
+    TmaRing* ring = reinterpret_cast<TmaRing*>(stage0 + (size_t)kTmaStages * kTmaBytes);
+    const u32 tiles = (u32)((nrows + kTmaRows - 1) / kTmaRows);
+    const u32 chunks = (c + kTmaCols - 1) / kTmaCols;
+    const u32 my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const u32 items = my_tiles * chunks;
+    if (threadIdx.x == 0) {
+        for (u32 s = 0; s < kTmaStages; s++) {
+            mbar_init(&ring->full[s], 1);
+            mbar_init(&ring->empty[s], kTmaRows);
+        }
+        ring->abort = 0;
+        ring->issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    volatile u32* abort = &ring->abort;
+    if (threadIdx.x >= kTmaRows) {
+        // Producer: one thread issues every copy of this CTA, in item order.
+        if (threadIdx.x == kTmaRows) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<u64>(&map)) : "memory");
+            u32 issued = 0;
+            for (u32 it = 0; it < items; it++) {
+                const u32 s = it % kTmaStages;
+                if (it >= kTmaStages && !mbar_wait(&ring->empty[s], ((it / kTmaStages) - 1) & 1)) {
+                    *abort = 1;
+                    break;
+                }
+                if (*abort) break;
+                const u32 tile = blockIdx.x + (it / chunks) * gridDim.x;
+                mbar_expect_tx(&ring->full[s], kTmaBytes);
+                tma_load_2d(stage0 + (size_t)s * kTmaBytes, &map, (it % chunks) * kTmaCols, tile * kTmaRows,
+                            &ring->full[s]);
+                issued = it + 1;
+            }
+            ring->issued = issued;
+        }
+    } else {
+        const u32 t = threadIdx.x, sw = t & 7;
+        u32 it = 0;
+        for (u32 ti = 0; ti < my_tiles && !*abort; ti++) {
+            const u64 row = (u64)(blockIdx.x + ti * gridDim.x) * kTmaRows + t;
+            u64 l0 = 0, m0 = 0, l1 = 0, m1 = 0;
+            u32 h0 = 0, h1 = 0;
+            bool ok = true;
+            for (u32 ch = 0; ch < chunks; ch++, it++) {
+                const u32 s = it % kTmaStages;
+                if (!mbar_wait(&ring->full[s], (it / kTmaStages) & 1)) {
+                    *abort = 1;
+                    ok = false;
+                    break;
+                }
+                const ulonglong2* line = reinterpret_cast<const ulonglong2*>(stage0 + (size_t)s * kTmaBytes + t * 128);
+                const u32 c0 = ch * kTmaCols;
+                if (c0 + kTmaCols <= c) {
+#pragma unroll
+                    for (u32 u = 0; u < kTmaCols / 2; u++) {
+                        const ulonglong2 v = line[u ^ sw];
+                        if (EXT == 2) {
+                            const ulonglong2* pw2 = reinterpret_cast<const ulonglong2*>(pw) + c0 + 2 * u;
+                            const ulonglong2 p0 = __ldg(pw2), p1 = __ldg(pw2 + 1);
+                            mac192(l0, m0, h0, v.x, p0.x);
+                            mac192(l1, m1, h1, v.x, p0.y);
+                            mac192(l0, m0, h0, v.y, p1.x);
+                            mac192(l1, m1, h1, v.y, p1.y);
+                        } else {
+                            // pw + c0 may be 8-byte aligned only (an odd column offset).
+                            mac192(l0, m0, h0, v.x, __ldg(pw + c0 + 2 * u));
+                            mac192(l1, m1, h1, v.y, __ldg(pw + c0 + 2 * u + 1));
+                        }
+                    }
+                } else {
+                    // The last, partial chunk (words past c are the copy's zero fill).
+                    for (u32 w = 0; c0 + w < c; w++) {
+                        const u64 x = reinterpret_cast<const u64*>(line + ((w >> 1) ^ sw))[w & 1];
+                        if (EXT == 2) {
+                            const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(pw) + c0 + w);
+                            mac192(l0, m0, h0, x, p.x);
+                            mac192(l1, m1, h1, x, p.y);
+                        } else {
+                            mac192(l0, m0, h0, x, __ldg(pw + c0 + w));
+                        }
+                    }
+                }
+                mbar_arrive(&ring->empty[s]);
+            }
+            if (!ok) break;
+            if (row < nrows) {
+                if (EXT == 2) {
+                    u64 r0 = fold192(l0, m0, h0), r1 = fold192(l1, m1, h1);
+                    if (acc) {
+                        r0 = gl::add(f[2 * row], r0);
+                        r1 = gl::add(f[2 * row + 1], r1);
+                    }
+                    reinterpret_cast<ulonglong2*>(f)[row] = make_ulonglong2(r0, r1);
+                } else {
+                    u64 r = gl::add(fold192(l0, m0, h0), fold192(l1, m1, h1));
+                    f[row] = acc ? gl::add(f[row], r) : r;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == kTmaRows && *abort) {
+        // Wait (bounded) for this CTA's copies still in flight: the last
+        // issued copy of each stage is that stage's latest full phase.
+        const u32 issued = ring->issued;
+        for (u32 it = issued > kTmaStages ? issued - kTmaStages : 0; it < issued; it++)
+            mbar_wait(&ring->full[it % kTmaStages], (it / kTmaStages) & 1);
+        atomicOr(err, 1u);
+    }
+}
+
 // Per-round fold constants.  Step m of a round pairs positions (2u, 2u+1) of
 // the intermediate layer; with u = w 2^b + v' (b = a-1-m) the point of
 // position 2u is x = s^(2^m) w_{2^(b+1)}^bitrev_b(v') (w_{N_k}^e)^(2^m),
@@ -479,6 +700,53 @@ int grid_for(u64 work, int threads)
 }
 
 // Enqueues round k's fold: f_{k+1} from f_k with challenge beta (st.ext words).
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The tensor map of an object's LDE for the TMA combination: c x N words,
+// rows ld words apart, tiles of kTmaRows x kTmaCols with the 128-byte
+// swizzle.  False when the shape or the buffer does not meet the copy
+// engine's rules (16-byte aligned base and row pitch) or is smaller than one
+// tile; the caller then takes the register-load kernel.
+bool combine_map(const Object& o, u64 N, CUtensorMap* map)
+{
+    if (o.c < kTmaCols || N < kTmaRows || N > 0xFFFFFFFFull || ((size_t)o.ld * 8) % 16 ||
+        (reinterpret_cast<uintptr_t>(o.lde) & 15))
+        return false;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {o.c, N};
+    const cuuint64_t pitch[1] = {(cuuint64_t)o.ld * 8};
+    const cuuint32_t box[2] = {kTmaCols, kTmaRows};
+    const cuuint32_t step[2] = {1, 1};
+    if (fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, (void*)o.lde, dims, pitch, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    return cudaFuncSetAttribute(k_fri_combine_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_fri_combine_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) ==
+               cudaSuccess;
+}
+
 v3c_status launch_fold(v3c_ctx* ctx, FriState& st, u32 k, const u64* beta, cudaStream_t s)
 {
     const u32 a = st.arity[k];
@@ -687,6 +955,8 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
     }
     size_t off_final = words;
     words += even(((size_t)1 << st->log_size[st->rounds]) * ext);
+    const size_t off_err = words;
+    words += 2;
     st->bytes = words * 8;
     if (ctx->resident + st->bytes > ctx->cfg.hbm_budget_bytes) {
         size_t need = st->bytes;
@@ -710,6 +980,7 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
         st->cap[k] = base + off_c[k];
     }
     st->final_coef = base + off_final;
+    st->err = reinterpret_cast<u32*>(base + off_err);
     auto bail = [&](v3c_status code) {
         cudaFreeAsync(st->mem, s);
         cudaEventDestroy(st->ev);
@@ -723,6 +994,7 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
             return bail(fail(ctx, V3C_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)));     \
     } while (0)
     for (auto& o : objs) CKB(cudaStreamWaitEvent(s, o.done, 0));
+    CKB(cudaMemsetAsync(st->err, 0, 8, s));
     k_fri_root_tables<<<6, 256, 0, s>>>(gl::h_inv(gl::h_root(log_N)), log_N, st->pw_inv);
     CKB(cudaGetLastError());
     if (ext == 2) k_fri_powers_ext<<<grid_for(ncols, 256), 256, 0, s>>>(alpha[0], alpha[1], ncols, st->alpha_pw);
@@ -733,15 +1005,29 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
     const u64 N = (u64)1 << log_N;
     for (size_t i = 0; i < objs.size(); i++) {
         const Object& o = objs[i];
+        const u64* pw = st->alpha_pw + (size_t)ext * e0;
+        CUtensorMap map;
+        if (combine_map(o, N, &map)) {
+            StageTimer tm(ctx, 5, s);
+            const int grid = (int)std::min<u64>((u64)2 * num_sms(), (N + kTmaRows - 1) / kTmaRows);
+            if (ext == 2)
+                k_fri_combine_tma<2><<<grid, kTmaThreads, kTmaSmem, s>>>(map, o.c, pw, N, i > 0, st->f[0], st->err);
+            else
+                k_fri_combine_tma<1><<<grid, kTmaThreads, kTmaSmem, s>>>(map, o.c, pw, N, i > 0, st->f[0], st->err);
+            CKB(cudaGetLastError());
+            tm.done();
+            ctx->launches++;
+            e0 += o.c;
+            continue;
+        }
         int nb = 0;
         CKB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fri_combine, 256, 0));
         int grid = (int)std::min<u64>((u64)std::max(nb, 1) * num_sms(), (N + 255) / 256);
         StageTimer tm(ctx, 5, s);
         if (ext == 2)
-            k_fri_combine_ext2<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + 2 * (size_t)e0, N,
-                                                                 i > 0, st->f[0]);
+            k_fri_combine_ext2<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, pw, N, i > 0, st->f[0]);
         else
-            k_fri_combine<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, st->alpha_pw + e0, N, i > 0, st->f[0]);
+            k_fri_combine<<<std::max(grid, 1), 256, 0, s>>>(o.lde, o.ld, o.c, pw, N, i > 0, st->f[0]);
         CKB(cudaGetLastError());
         tm.done();
         ctx->launches++;
@@ -796,6 +1082,18 @@ v3c_status v3c_fri_info(v3c_ctx* ctx, v3c_fri_id fri, v3c_fri_info_t* out)
     return V3C_OK;
 }
 
+// The combination runs once, at v3c_fri_begin; the first call that reads a
+// result back (after waiting for the state's work) also reads its error word.
+v3c_status check_combine(v3c_ctx* ctx, FriState& st)
+{
+    if (st.err_checked) return V3C_OK;
+    u32 e = 0;
+    CK(cudaMemcpy(&e, st.err, 4, cudaMemcpyDeviceToHost));
+    if (e) return fail(ctx, V3C_ETIMEDOUT, "FRI combination: a wait of the copy pipeline timed out");
+    st.err_checked = true;
+    return V3C_OK;
+}
+
 v3c_status v3c_fri_cap(v3c_ctx* ctx, v3c_fri_id fri, uint32_t layer, uint64_t* h_cap)
 {
     if (!ctx || !h_cap) return V3C_EINVAL;
@@ -806,6 +1104,8 @@ v3c_status v3c_fri_cap(v3c_ctx* ctx, v3c_fri_id fri, uint32_t layer, uint64_t* h
     if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
     if (layer >= st->committed) return fail(ctx, V3C_EINVAL, "v3c_fri_cap: layer %u is not committed", layer);
     CK(cudaEventSynchronize(st->ev));
+    r = check_combine(ctx, *st);
+    if (r) return r;
     CK(cudaMemcpy(h_cap, st->cap[layer], ((size_t)4 << st->h[layer]) * 8, cudaMemcpyDeviceToHost));
     return V3C_OK;
 }
@@ -820,6 +1120,8 @@ v3c_status v3c_fri_final(v3c_ctx* ctx, v3c_fri_id fri, uint64_t* h_coeffs)
     if (!st) return fail(ctx, V3C_ENOTFOUND, "fri id %llu", (unsigned long long)fri);
     if (st->done != st->rounds) return fail(ctx, V3C_EINVAL, "v3c_fri_final: %u of %u rounds done", st->done, st->rounds);
     CK(cudaEventSynchronize(st->ev));
+    r = check_combine(ctx, *st);
+    if (r) return r;
     CK(cudaMemcpy(h_coeffs, st->final_coef, ((size_t)1 << st->log_size[st->rounds]) * st->ext * 8,
                   cudaMemcpyDeviceToHost));
     return V3C_OK;
@@ -878,7 +1180,7 @@ v3c_status v3c_fri_query(v3c_ctx* ctx, v3c_fri_id fri, const uint64_t* h_idx, ui
     cudaFreeAsync(d, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(ctx, V3C_ECUDA, "v3c_fri_query: %s", cudaGetErrorString(e));
-    return V3C_OK;
+    return check_combine(ctx, *st);
 }
 
 v3c_status v3c_fri_release(v3c_ctx* ctx, v3c_fri_id fri)

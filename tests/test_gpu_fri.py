@@ -102,6 +102,12 @@ FRI_CASES = [
     ([(135, 10)], 3, 4, 4, 5, 4),   # wide rows, several 64-column passes per warp
     ([(13, 11), (6, 11)], 3, 2, 4, 4, 3),  # two commitments combined
     ([(1, 4)], 1, 0, 4, 5, 0),      # no fold at all: log N = 5 = final_log
+    # Copy-engine (tiled) combination: at least 16 columns and 256 rows.
+    ([(17, 9), (33, 9)], 2, 1, 3, 4, 3),   # two tiled objects, the second at an odd power offset
+    ([(21, 10), (5, 10)], 3, 2, 4, 5, 4),  # one tiled, one register-load, summed
+    ([(16, 8)], 1, 0, 2, 3, 2),            # whole tiles only (no partial column chunk)
+    ([(20, 7)], 1, 0, 4, 5, 4),            # exactly one tile of 256 rows
+    ([(16, 15)], 2, 0, 4, 5, 4),           # 512 tiles: several tiles per CTA, one chunk each
 ]
 
 
@@ -116,6 +122,10 @@ EXT_CASES = [
     ([(5, 9)], 2, 1, 1, 3, 3),      # arity 2: leaves of 4 words, zero-padded, not hashed
     ([(13, 11), (6, 11)], 3, 2, 4, 4, 3),
     ([(1, 4)], 1, 0, 4, 5, 0),      # no fold
+    ([(17, 9), (33, 9)], 2, 1, 3, 4, 3),   # tiled combination, two objects
+    ([(21, 10), (5, 10)], 3, 2, 4, 5, 4),  # tiled + register-load
+    ([(20, 7)], 1, 0, 4, 5, 4),            # one tile
+    ([(40, 14)], 3, 2, 4, 5, 4),           # 512 tiles, three chunks per tile
 ]
 
 
