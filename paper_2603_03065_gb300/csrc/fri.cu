@@ -29,6 +29,7 @@
 #include "ctx.h"
 #include "gl.cuh"
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace v3c {
 
@@ -105,47 +106,8 @@ __device__ __forceinline__ u64 pow3(const u64* __restrict__ pw, u64 e)
     return gl::mul(r, __ldg(pw + 1024 + (e >> 18)));
 }
 
-// (lo, mid, hi) += a * b: a 64x64 -> 128-bit product added into a 192-bit
-// accumulator whose top word counts the carries (at most one per product).
-// The product is four 32x32 + 64 -> 64 wide multiply-adds, each taking the
-// carry word of the one before: t = a0 b1 + hi(a0 b0), u = a1 b0 + lo(t),
-// high half a1 b1 + hi(t) + hi(u); no sum leaves 64 bits.  On the IMAD pipe
-// this is a third cheaper than a 64-bit multiply's low and high halves.
-__device__ __forceinline__ void mac192(u64& lo, u64& mid, u32& hi, u64 a, u64 b)
-{
-    asm("{\n\t"
-        ".reg .u32 a0, a1, b0, b1, p0, p1, t0, t1, u0, u1;\n\t"
-        ".reg .u64 p, t, u, h, c, pl;\n\t"
-        "mov.b64 {a0, a1}, %3;\n\t"
-        "mov.b64 {b0, b1}, %4;\n\t"
-        "mul.wide.u32 p, a0, b0;\n\t"
-        "mov.b64 {p0, p1}, p;\n\t"
-        "cvt.u64.u32 c, p1;\n\t"
-        "mad.wide.u32 t, a0, b1, c;\n\t"
-        "mov.b64 {t0, t1}, t;\n\t"
-        "cvt.u64.u32 c, t0;\n\t"
-        "mad.wide.u32 u, a1, b0, c;\n\t"
-        "mov.b64 {u0, u1}, u;\n\t"
-        "cvt.u64.u32 c, t1;\n\t"
-        "mad.wide.u32 h, a1, b1, c;\n\t"
-        "cvt.u64.u32 c, u1;\n\t"
-        "add.u64 h, h, c;\n\t"
-        "mov.b64 pl, {p0, u0};\n\t"
-        "add.cc.u64 %0, %0, pl;\n\t"
-        "addc.cc.u64 %1, %1, h;\n\t"
-        "addc.u32 %2, %2, 0;\n\t"
-        "}"
-        : "+l"(lo), "+l"(mid), "+r"(hi)
-        : "l"(a), "l"(b));
-}
-
-// The accumulator's value lo + mid 2^64 + hi 2^128 mod p.  With 2^64 = 2^32 - 1
-// and 2^128 = (2^32 - 1)^2 = 2^64 - 2^33 + 1 = -2^32 (mod p), it is
-// reduce(lo + mid 2^64) - hi 2^32, and hi 2^32 < 2^63 < p for hi < 2^31.
-__device__ __forceinline__ u64 fold192(u64 lo, u64 mid, u32 hi)
-{
-    return gl::sub(gl::canon(gl::reduce128_ptx(lo, mid)), (u64)hi << 32);
-}
+using gl::fold192;
+using gl::mac192;
 
 // Column pairs loaded per iteration of the combine: 4 pairs are one 64-byte
 // run (two whole sectors) per thread; 8 measured no faster.
@@ -342,68 +304,6 @@ struct TmaRing {
     u32 issued;
 };
 
-__device__ __forceinline__ u64 fri_global_ns()
-{
-    u64 t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ u32 smem_addr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(u64* bar, u32 count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(u64* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(u64* bar, u32 bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity)
-{
-    u32 done;
-    asm volatile(
-        "{\n\t"
-        ".reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t"
-        "}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Waits for the phase of `bar` with the given parity; false after kTmaWaitNs.
-__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const u64 t0 = fri_global_ns();
-    for (u32 i = 1;; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 0 && fri_global_ns() - t0 > kTmaWaitNs) return false;
-    }
-}
-
-// Tile (x, y) of the map (x in words, a multiple of kTmaCols; y in rows) into
-// shared memory at dst, completing `bar`'s transaction count.
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u32 x, u32 y, u64* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_addr(dst)),
-        "l"(reinterpret_cast<u64>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
-}
-
 // f[t] (+)= sum_{i<c} alpha^i row_t[i] (EXT words per alpha power and per
 // output) over tiles of kTmaRows rows; requires c >= kTmaCols and
 // nrows >= kTmaRows (the host takes the register-load kernels otherwise).
@@ -427,8 +327,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_fri_combine_tma(const __grid
         }
         ring->abort = 0;
         ring->issued = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_init_fence();
     }
     __syncthreads();
     volatile u32* abort = &ring->abort;
@@ -439,7 +338,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_fri_combine_tma(const __grid
             u32 issued = 0;
             for (u32 it = 0; it < items; it++) {
                 const u32 s = it % kTmaStages;
-                if (it >= kTmaStages && !mbar_wait(&ring->empty[s], ((it / kTmaStages) - 1) & 1)) {
+                if (it >= kTmaStages && !mbar_wait(&ring->empty[s], ((it / kTmaStages) - 1) & 1, kTmaWaitNs)) {
                     *abort = 1;
                     break;
                 }
@@ -462,7 +361,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_fri_combine_tma(const __grid
             bool ok = true;
             for (u32 ch = 0; ch < chunks; ch++, it++) {
                 const u32 s = it % kTmaStages;
-                if (!mbar_wait(&ring->full[s], (it / kTmaStages) & 1)) {
+                if (!mbar_wait(&ring->full[s], (it / kTmaStages) & 1, kTmaWaitNs)) {
                     *abort = 1;
                     ok = false;
                     break;
@@ -523,7 +422,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2) k_fri_combine_tma(const __grid
         // issued copy of each stage is that stage's latest full phase.
         const u32 issued = ring->issued;
         for (u32 it = issued > kTmaStages ? issued - kTmaStages : 0; it < issued; it++)
-            mbar_wait(&ring->full[it % kTmaStages], (it / kTmaStages) & 1);
+            mbar_wait(&ring->full[it % kTmaStages], (it / kTmaStages) & 1, kTmaWaitNs);
         atomicOr(err, 1u);
     }
 }

@@ -14,7 +14,9 @@
 // With the prefix (N_pre, D_pre) known, the tile takes one inversion,
 // inv = (D_pre D_tile)^-1, and writes Z_i = N_pre N_{<i} D_{>=i} inv, where
 // N_{<i} and D_{>=i} run inside the tile (block scans with warp shuffles).
-// X and Y are read once and Z written once.  A second, small launch zeroes
+// X and Y are read once and Z written once.  Products inside the scan (the
+// thread, block and look-back products) stay in [0, 2^64), congruent mod p;
+// only the Z words written out are reduced to [0, p).  A second, small launch zeroes
 // the column of an instance whose denominator product is zero (alpha equal
 // to some compressed y).
 #include <cuda_runtime.h>
@@ -44,6 +46,7 @@ struct SeqJob {
     u64* z;
     u64 L;
     u64 alpha, beta;
+    u64 beta2, beta3;  // beta^2, beta^3 (width-4 tuples)
     u32* status;  // the instance's status word: 1 when its denominator product is zero
     u32 T;
     u32 tile0;    // first global tile
@@ -112,7 +115,7 @@ __device__ __forceinline__ u64 block_exclusive(u64 v, u64* sh)
     for (int o = 1; o < 32; o <<= 1) {
         u64 t = SUFFIX ? __shfl_down_sync(0xffffffffu, inc, o) : __shfl_up_sync(0xffffffffu, inc, o);
         bool take = SUFFIX ? lane + o < 32 : lane >= (u32)o;
-        if (take) inc = gl::mul(inc, t);
+        if (take) inc = gl::mul_nc(inc, t);
     }
     u64 excl = SUFFIX ? __shfl_down_sync(0xffffffffu, inc, 1) : __shfl_up_sync(0xffffffffu, inc, 1);
     if (SUFFIX ? lane == 31 : lane == 0) excl = 1;
@@ -125,11 +128,11 @@ __device__ __forceinline__ u64 block_exclusive(u64 v, u64* sh)
             u32 w = SUFFIX ? nw - 1 - k : k;
             u64 t = sh[w];
             sh[w] = run;
-            run = gl::mul(run, t);
+            run = gl::mul_nc(run, t);
         }
     }
     __syncthreads();
-    u64 r = gl::mul(excl, sh[wid]);
+    u64 r = gl::mul_nc(excl, sh[wid]);
     __syncthreads();
     return r;
 }
@@ -161,7 +164,9 @@ __device__ u64 seq_inverse(u64 x)
 // [first, first + nthr) of the CTA, thread j taking elements j + nthr k.
 // Width-4 tuples at 16-byte aligned addresses (the query circuit's (list,
 // slot, distance, item)) are requested two elements at a time, eight
-// 16-byte loads in flight per thread, before any is compressed.
+// 16-byte loads in flight per thread, before any is compressed; their
+// Compress is t_0 + t_1 beta + t_2 beta^2 + t_3 beta^3 as three independent
+// 64x64 products summed unreduced in 192 bits and reduced once.
 __device__ __forceinline__ u32 seq_pad(u32 i);
 __device__ __forceinline__ void seq_load(const SeqJob& J, u64 tbase, u64* bn, u64* bd, u32 first, u32 nthr)
 {
@@ -187,14 +192,19 @@ __device__ __forceinline__ void seq_load(const SeqJob& J, u64 tbase, u64* bn, u6
                 if (i >= kSeqTile) break;
                 u64 n = 1, d = 1;
                 if (tbase + i < J.L) {
-                    u64 h = gl::add_nc(gl::mul_nc(xb[k].y, J.beta), xb[k].x);
-                    h = gl::add_nc(gl::mul_nc(h, J.beta), xa[k].y);
-                    h = gl::add_nc(gl::mul_nc(h, J.beta), xa[k].x);
-                    n = gl::sub(J.alpha, gl::canon(h));
-                    h = gl::add_nc(gl::mul_nc(yb[k].y, J.beta), yb[k].x);
-                    h = gl::add_nc(gl::mul_nc(h, J.beta), ya[k].y);
-                    h = gl::add_nc(gl::mul_nc(h, J.beta), ya[k].x);
-                    d = gl::sub(J.alpha, gl::canon(h));
+                    u64 lo = xa[k].x, mid = 0;
+                    u32 hi = 0;
+                    gl::mac192(lo, mid, hi, xa[k].y, J.beta);
+                    gl::mac192(lo, mid, hi, xb[k].x, J.beta2);
+                    gl::mac192(lo, mid, hi, xb[k].y, J.beta3);
+                    n = gl::sub(J.alpha, gl::fold192(lo, mid, hi));
+                    lo = ya[k].x;
+                    mid = 0;
+                    hi = 0;
+                    gl::mac192(lo, mid, hi, ya[k].y, J.beta);
+                    gl::mac192(lo, mid, hi, yb[k].x, J.beta2);
+                    gl::mac192(lo, mid, hi, yb[k].y, J.beta3);
+                    d = gl::sub(J.alpha, gl::fold192(lo, mid, hi));
                 }
                 bn[seq_pad(i)] = n;
                 bd[seq_pad(i)] = d;
@@ -222,7 +232,7 @@ __device__ __forceinline__ u32 seq_pad(u32 i) { return i + (i >> 3); }
 __device__ __forceinline__ u64 warp_product(u64 v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = gl::mul(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = gl::mul_nc(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -280,16 +290,16 @@ __device__ __forceinline__ void seq_lookback(const SeqJob& J, u32 tile, u64 Nt, 
         }
         vn = warp_product(vn);
         vd = warp_product(vd);
-        Np = gl::mul(Np, vn);
-        Dp = gl::mul(Dp, vd);
+        Np = gl::mul_nc(Np, vn);
+        Dp = gl::mul_nc(Dp, vd);
         if (inc) break;
         p -= 32;
         spins = 0;
     }
     if (lane == 0) {
         SeqTile& me = st[tile];
-        me.inc_n = gl::mul(Np, Nt);
-        me.inc_d = gl::mul(Dp, Dt);
+        me.inc_n = gl::mul_nc(Np, Nt);
+        me.inc_d = gl::mul_nc(Dp, Dt);
         __threadfence();
         atomicExch(&flags[tile], 2u);
     }
@@ -331,13 +341,13 @@ __global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const
         u64 pn = 1, pd = 1;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
-            pn = gl::mul(pn, s_num[b][seq_pad(kSeqPer * t + k)]);
-            pd = gl::mul(pd, s_den[b][seq_pad(kSeqPer * t + k)]);
+            pn = gl::mul_nc(pn, s_num[b][seq_pad(kSeqPer * t + k)]);
+            pd = gl::mul_nc(pd, s_den[b][seq_pad(kSeqPer * t + k)]);
         }
         const u64 en = block_exclusive<false>(pn, sh);  // numerators of the earlier threads
         const u64 sd = block_exclusive<true>(pd, sh);   // denominators of the later threads
-        if (t == blockDim.x - 1) s_tot[0] = gl::mul(en, pn);
-        if (t == 0) s_tot[1] = gl::mul(sd, pd);
+        if (t == blockDim.x - 1) s_tot[0] = gl::mul_nc(en, pn);
+        if (t == 0) s_tot[1] = gl::mul_nc(sd, pd);
         __syncthreads();
         const u32 next = s_tile[b ^ 1];
         if (t < 32) {
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const
             if (t == 0) {
                 const u64 inv = seq_inverse(gl::mul(Dp, s_tot[1]));
                 if (inv == 0) atomicOr(J.status, 1u);
-                s_k = gl::mul(Np, inv);
+                s_k = gl::mul_nc(Np, inv);
             }
         } else if (next < ntiles) {
             const SeqJob& Jn = jobs[seq_find(jobs, njobs, next)];
@@ -360,20 +370,20 @@ __global__ void __launch_bounds__(kSeqThreads, kSeqMinBlocks) k_seteq_scan(const
             num[k] = s_num[b][seq_pad(kSeqPer * t + k)];
             den[k] = s_den[b][seq_pad(kSeqPer * t + k)];
         }
-        u64 N = gl::mul(s_k, en);
+        u64 N = gl::mul_nc(s_k, en);
         u64 S = sd;
         u64 suf[kSeqPer];
 #pragma unroll
         for (int k = kSeqPer - 1; k >= 0; k--) {
-            S = gl::mul(S, den[k]);
+            S = gl::mul_nc(S, den[k]);
             suf[k] = S;
         }
         const u64 ebase = tbase + (u64)kSeqPer * t;
 #pragma unroll
         for (u32 k = 0; k < kSeqPer; k++) {
             s_num[b][seq_pad(kSeqPer * t + k)] = gl::mul(N, suf[k]);  // each thread rewrites only its own words
-            N = gl::mul(N, num[k]);
-            if (ebase + k + 1 == J.L) J.z[J.L] = N;
+            N = gl::mul_nc(N, num[k]);
+            if (ebase + k + 1 == J.L) J.z[J.L] = gl::canon(N);
         }
         __syncthreads();
 #pragma unroll
@@ -444,6 +454,8 @@ extern "C" v3c_status v3c_seteq(v3c_ctx* ctx, const v3c_seteq_desc* descs, uint3
         J.T = d.T;
         J.alpha = d.alpha;
         J.beta = d.beta;
+        J.beta2 = gl::h_mul(d.beta, d.beta);
+        J.beta3 = gl::h_mul(J.beta2, d.beta);
         J.tile0 = t0;
         J.ntiles = (u32)((d.L + kSeqTile - 1) / kSeqTile);
         J.status = status + i;
