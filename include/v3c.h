@@ -320,6 +320,22 @@ v3c_status v3c_int_pipe_rate(v3c_ctx* ctx, uint32_t kind, uint32_t reps, double*
 /* v3c_int_pipe_rate with kind 0. */
 v3c_status v3c_int_peak(v3c_ctx* ctx, uint32_t reps, double* rate, double* mhz);
 
+/* Self-test of the library's bounded device waits (no counterpart in the
+ * paper).  The kernels that wait on the GPU (the SetEq look-back, the copy
+ * pipeline of the FRI combination) give every wait a time or poll limit,
+ * after which they record an error word that the host turns into
+ * V3C_ETIMEDOUT, and the context stays usable.  This call runs one
+ * single-thread kernel whose wait can never be satisfied and that gives up
+ * after `limit_us` microseconds of the GPU's global timer:
+ *   kind 0: a shared-memory barrier (mbarrier) phase that expects two
+ *           arrivals and gets one, waited on with the same bounded wait as
+ *           the FRI copy pipeline;
+ *   kind 1: a device word that nothing sets, polled with short sleeps.
+ * Synchronous on `stream`.  Returns V3C_ETIMEDOUT when the wait gave up (the
+ * expected outcome).  Errors: EINVAL (kind > 1, limit_us of 0 or above
+ * 2000000), ECUDA. */
+v3c_status v3c_wait_selftest(v3c_ctx* ctx, uint32_t kind, uint32_t limit_us, void* stream);
+
 /* ---------------- allocation-free LDE ---------------- */
 
 /* No counterpart in the paper: this entry point serves callers that cannot

@@ -137,6 +137,7 @@ SIGNATURES = {
     "v3c_int_peak": (ctypes.c_int, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "v3c_int_pipe_rate": (ctypes.c_int, [_vp, _u32, _u32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]),
+    "v3c_wait_selftest": (ctypes.c_int, [_vp, _u32, _u32, _vp]),
     # include/v3c_fri.h
     "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64p, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
     "v3c_fri_fold": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _vp]),
@@ -582,6 +583,12 @@ class Context:
     def int_peak(self, reps: int = 10) -> tuple[float, float]:
         """Measured 32x32->64 wide multiply-adds per second and the SM MHz of that run."""
         return self.int_pipe_rate(0, reps)
+
+    def wait_selftest(self, kind: int, limit_us: int, stream=None) -> None:
+        """v3c_wait_selftest: a device wait that nothing satisfies gives up after
+        limit_us; raises V3CError with status V3C_ETIMEDOUT (the expected
+        outcome)."""
+        self._check(self.lib.v3c_wait_selftest(self.h, kind, limit_us, _stream(stream)))
 
     def int_pipe_rate(self, kind: int, reps: int = 10) -> tuple[float, float]:
         """v3c_int_pipe_rate: kind 0 = wide multiply-adds, 1 = 32-bit multiply-adds."""

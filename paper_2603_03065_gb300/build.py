@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libv3c.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["ntt.cu", "hash.cu", "v3c.cu", "serve.cu", "lde_noalloc.cu", "fri.cu", "snapshot.cu", "seteq.cu"]
+UNITS = ["ntt.cu", "hash.cu", "v3c.cu", "serve.cu", "lde_noalloc.cu", "fri.cu", "snapshot.cu", "seteq.cu",
+         "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
