@@ -115,7 +115,9 @@ v3c_status v3c_lde(v3c_ctx* ctx, const uint64_t* d_cols, uint32_t c, uint32_t lo
  *   d_rows   device, row-major, stride ld (uint64), the first `width` entries hashed
  *   d_tree   device, (2N - 2^(h+1)) * 4 uint64, level-major (may be NULL iff h == log_rows)
  *   d_cap    device, 2^h * 4 uint64
- * Uses no scratch.  Errors: EINVAL (h > log_rows, width > ld, NULL), ECUDA. */
+ * d_tree and d_cap are 16-byte aligned (digests are stored as 16-byte pairs).
+ * Uses no scratch.  Errors: EINVAL (h > log_rows, width > ld, NULL, a
+ * misaligned d_tree or d_cap), ECUDA. */
 v3c_status v3c_merkle(v3c_ctx* ctx, const uint64_t* d_rows, uint32_t ld, uint32_t width,
                       uint32_t log_rows, uint32_t cap_height, uint64_t* d_tree, uint64_t* d_cap,
                       void* stream);
