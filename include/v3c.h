@@ -291,6 +291,17 @@ uint64_t v3c_kernel_launches(v3c_ctx* ctx);
 /* Number of v3c_commit calls served by replaying a captured CUDA graph. */
 uint64_t v3c_graph_replays(v3c_ctx* ctx);
 
+/* Device memory accounting, for leak checks and budgeting:
+ *   out[0]  bytes of resident objects (commit objects, FRI states, snapshots)
+ *           the context counts against its HBM budget;
+ *   out[1]  bytes currently allocated from the device's default
+ *           stream-ordered pool by this process (every context and any other
+ *           user of that pool; memory whose stream-ordered free has not yet
+ *           executed still counts, so synchronise first);
+ *   out[2]  bytes of the context's scratch arena (kept for reuse).
+ * Errors: EINVAL (NULL), ECUDA. */
+v3c_status v3c_mem_stats(v3c_ctx* ctx, uint64_t* out);
+
 /* Per-stage timing.  With V3C_FLAG_TIMING in the context's flags, every
  * stage launch is bracketed by two CUDA events recorded on the stream it is
  * launched on.  v3c_stage_stats waits for the pending events and returns

@@ -138,6 +138,7 @@ SIGNATURES = {
     "v3c_int_pipe_rate": (ctypes.c_int, [_vp, _u32, _u32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]),
     "v3c_wait_selftest": (ctypes.c_int, [_vp, _u32, _u32, _vp]),
+    "v3c_mem_stats": (ctypes.c_int, [_vp, _u64p]),
     # include/v3c_fri.h
     "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64p, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
     "v3c_fri_fold": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _vp]),
@@ -583,6 +584,13 @@ class Context:
     def int_peak(self, reps: int = 10) -> tuple[float, float]:
         """Measured 32x32->64 wide multiply-adds per second and the SM MHz of that run."""
         return self.int_pipe_rate(0, reps)
+
+    def mem_stats(self) -> dict:
+        """v3c_mem_stats: resident bytes counted against the budget, bytes in use
+        in the device's default stream-ordered pool, and the scratch arena size."""
+        out = (_u64 * 3)()
+        self._check(self.lib.v3c_mem_stats(self.h, out))
+        return {"resident": out[0], "pool_used": out[1], "arena": out[2]}
 
     def wait_selftest(self, kind: int, limit_us: int, stream=None) -> None:
         """v3c_wait_selftest: a device wait that nothing satisfies gives up after

@@ -1285,6 +1285,22 @@ uint64_t v3c_kernel_launches(v3c_ctx* ctx) { return ctx ? ctx->launches.load() :
 
 uint64_t v3c_graph_replays(v3c_ctx* ctx) { return ctx ? ctx->graph_replays.load() : 0; }
 
+v3c_status v3c_mem_stats(v3c_ctx* ctx, uint64_t* out)
+{
+    if (!ctx || !out) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaMemPool_t pool = nullptr;
+    uint64_t used = 0;
+    CK(cudaDeviceGetDefaultMemPool(&pool, ctx->device));
+    CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    out[0] = ctx->resident;
+    out[1] = used;
+    out[2] = (uint64_t)ctx->arena.words * sizeof(u64);
+    return V3C_OK;
+}
+
 v3c_status v3c_stage_stats(v3c_ctx* ctx, v3c_stage_stats_t* out, int reset)
 {
     if (!ctx || !out) return V3C_EINVAL;
