@@ -283,6 +283,16 @@ v3c_status v3c_serve_poll(v3c_ctx* ctx, uint64_t ticket, v3c_req_state* state, u
  * requests resolve to FAILED with ECANCELED. */
 v3c_status v3c_serve_stop(v3c_ctx* ctx);
 
+/* Host-side failure injection for tests of the serving loop (no counterpart
+ * in the paper).  The scheduler thread raises an exception at the start of
+ * its pass number `after_passes` from now (0: the next pass).  As after any
+ * failure of that thread, batches already on the device complete (their
+ * requests become DONE), queued and admitted requests resolve to FAILED with
+ * ECANCELED, later submits return ECANCELED, and v3c_serve_stop still
+ * releases the loop; the context stays usable for v3c_commit.  Errors:
+ * EINVAL (not serving), ECANCELED (already stopped or failed). */
+v3c_status v3c_serve_inject_failure(v3c_ctx* ctx, uint32_t after_passes);
+
 /* ---------------- introspection ---------------- */
 
 /* Number of this library's kernel launches enqueued by the context so far. */

@@ -139,6 +139,7 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_double)]),
     "v3c_wait_selftest": (ctypes.c_int, [_vp, _u32, _u32, _vp]),
     "v3c_mem_stats": (ctypes.c_int, [_vp, _u64p]),
+    "v3c_serve_inject_failure": (ctypes.c_int, [_vp, _u32]),
     # include/v3c_fri.h
     "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64p, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
     "v3c_fri_fold": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _vp]),
@@ -442,6 +443,11 @@ class Context:
 
     def serve_stop(self):
         self._check(self.lib.v3c_serve_stop(self.h))
+
+    def serve_inject_failure(self, after_passes: int = 0):
+        """v3c_serve_inject_failure: the scheduler thread raises at its pass
+        `after_passes` from now (host-side failure injection for tests)."""
+        self._check(self.lib.v3c_serve_inject_failure(self.h, after_passes))
 
     # --------------------------------------------------------------- openings
     def open_batch(self, cid: int, leaves, c: int, rows: bool = True, paths: bool = True):

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <stdexcept>
 
 #include "serve.h"
 
@@ -241,6 +242,7 @@ void run(Server* S)
     std::unique_lock<std::mutex> lk(S->mu);
     try {
         while (!S->stop) {
+            if (S->inject_after >= 0 && S->inject_after-- == 0) throw std::runtime_error("injected scheduler failure");
             reap(S, false);
             bool launched = admit_and_launch(S);
             bool busy = false;
@@ -257,7 +259,13 @@ void run(Server* S)
         reap(S, true);
         fail_all_pending(S, V3C_ECANCELED);
     } catch (...) {
+        // The scheduler cannot go on: batches already on the device finish
+        // (their requests become DONE), everything still queued fails.
         S->crashed = true;
+        try {
+            reap(S, true);
+        } catch (...) {
+        }
         fail_all_pending(S, V3C_ECANCELED);
     }
 }
@@ -367,6 +375,18 @@ v3c_status v3c_serve_poll(v3c_ctx* ctx, uint64_t ticket, v3c_req_state* state, u
     }
     if (stt == V3C_REQ_FAILED) return status;
     return V3C_EAGAIN;
+}
+
+v3c_status v3c_serve_inject_failure(v3c_ctx* ctx, uint32_t after_passes)
+{
+    if (!ctx) return V3C_EINVAL;
+    Server* S = ctx_server(ctx);
+    if (!S) return ctx_fail(ctx, V3C_EINVAL, "v3c_serve_inject_failure: not serving");
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->stop || S->crashed) return V3C_ECANCELED;
+    S->inject_after = (long)after_passes;
+    S->cv.notify_all();
+    return V3C_OK;
 }
 
 v3c_status v3c_serve_stop(v3c_ctx* ctx)

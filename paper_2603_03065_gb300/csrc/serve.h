@@ -61,6 +61,7 @@ struct Server {
     std::vector<Slot> slots;
     bool stop = false;
     bool crashed = false;
+    long inject_after = -1;  // scheduler passes before an injected failure (-1: none)
 };
 
 }  // namespace serve

@@ -3,7 +3,8 @@
 Requests of different shapes arrive while others run.  Each request's cap
 must equal the oracle's and the cap of the same commit made alone (tolerance
 zero).  Objects stay resident after DONE until released.  Admission respects
-the HBM budget, and stop() resolves queued requests with ECANCELED.
+the HBM budget, and stop() resolves queued requests with ECANCELED, as does
+a failure of the scheduler thread (injected on the host).
 """
 import time
 
@@ -111,6 +112,46 @@ def test_admission_waits_for_budget_and_stop_cancels(v3c):
                 ctx.release(t)
             except v3c.V3CError:
                 pass
+
+
+def test_scheduler_failure_fails_queued_requests_and_keeps_the_context(v3c):
+    # Host-side injection: the scheduler thread raises.  Requests already on
+    # the device finish (DONE, caps equal to the oracle's); those waiting for
+    # memory resolve to FAILED with ECANCELED; later submits are refused;
+    # stop still works and the context still commits.
+    s = synth.Shape(c=16, log_n=12, rate_bits=2, cap_height=4, seed=4)
+    fp = v3c.footprint(s.c, s.log_n, s.rate_bits, s.cap_height)
+    x = s.inputs()
+    _, _, want = oracle.commit(x, s.rate_bits, s.cap_height)
+    with v3c.Context(0, hbm_budget_bytes=2 * fp + fp // 2, max_inflight=2) as ctx:
+        ctx.serve_start(max_batch=8)
+        tickets = [ctx.serve_submit(x, s.rate_bits, s.cap_height) for _ in range(5)]
+        done = wait_done(ctx, v3c, tickets[:2], {t: s.cap_height for t in tickets[:2]})
+        for t in tickets[:2]:
+            assert np.array_equal(np.asarray(done[t][0]).reshape(-1), np.asarray(want).reshape(-1))
+        time.sleep(0.05)
+        for t in tickets[2:]:  # nothing released: they wait for memory
+            st, state, _, _ = ctx.serve_poll(t, s.cap_height)
+            assert st == v3c.V3C_EAGAIN and state == v3c.REQ_QUEUED
+        ctx.serve_inject_failure(0)
+        t0 = time.time()
+        states = {}
+        while len(states) < 3 and time.time() - t0 < 10:
+            for t in tickets[2:]:
+                st, state, _, _ = ctx.serve_poll(t, s.cap_height)
+                if st != v3c.V3C_EAGAIN:
+                    states[t] = (st, state)
+            time.sleep(0.005)
+        assert all(v == (v3c.V3C_ECANCELED, v3c.REQ_FAILED) for v in states.values()) and len(states) == 3
+        with pytest.raises(v3c.V3CError) as e:
+            ctx.serve_submit(x, s.rate_bits, s.cap_height)
+        assert e.value.status == v3c.V3C_ECANCELED
+        ctx.serve_stop()
+        for t in tickets[:2]:
+            ctx.release(t)
+        cid = ctx.commit([(x, s.rate_bits, s.cap_height)])[0]
+        assert np.array_equal(np.asarray(ctx.cap(cid)).reshape(-1), np.asarray(want).reshape(-1))
+        ctx.release(cid)
 
 
 def test_borrowed_pinned_and_device_inputs(v3c):
