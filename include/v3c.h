@@ -89,6 +89,18 @@ const char* v3c_strerror(v3c_status s);
 /* Detail of the last failure on this context (thread-local copy, never NULL). */
 const char* v3c_last_error_detail(v3c_ctx* ctx);
 
+/* Library log messages (no counterpart in the paper).  level 0: a call
+ * failed (the text of v3c_last_error_detail); 1: resources and choices
+ * (plan tables built, scratch arena grown, autotuned tiles, serving started
+ * or stopped); 2: detail (CUDA graphs captured, the FRI combination's load
+ * path).  Messages up to max_level go to fn(user, level, text).  fn may be
+ * called from any thread that calls the library and from the serving
+ * thread, sometimes with the context's lock held: it must return quickly
+ * and must not call into the library.  fn = NULL (the default) keeps the
+ * library silent.  Errors: EINVAL (ctx NULL). */
+typedef void (*v3c_log_fn)(void* user, int level, const char* text);
+v3c_status v3c_set_log(v3c_ctx* ctx, v3c_log_fn fn, void* user, int max_level);
+
 /* Creates a context on CUDA device `device`.  cfg may be NULL (defaults).
  * The first call on a device derives the Poseidon parameters and allocates
  * nothing else.  *out receives the context; v3c_destroy frees it.  Errors:
@@ -300,6 +312,22 @@ uint64_t v3c_kernel_launches(v3c_ctx* ctx);
 
 /* Number of v3c_commit calls served by replaying a captured CUDA graph. */
 uint64_t v3c_graph_replays(v3c_ctx* ctx);
+
+/* The autotuner's tile choices as text (no counterpart in the paper), so
+ * that a later process on the same kind of GPU can skip the timing runs:
+ *   {"sm_count": 152, "entries": [{"log_n": 20, "rate_bits": 3, "a_cols": 8,
+ *     "c_q": 8, "c_qc": 2, "kcap": 4, "h_threads": 128}, ...]}
+ * One entry per (log_n, rate_bits): the choices depend on the per-CTA shape,
+ * not on the column count.  v3c_tune_export writes the text, NUL-terminated,
+ * into buf (cap bytes) and its length into *len; with cap too small it
+ * returns EINVAL with *len set, so a caller can retry.  v3c_tune_import
+ * reads such text and replaces the context's choices for its shapes; with
+ * v3c_config.autotune set, an imported shape is not timed again.  It refuses
+ * (EINVAL, context unchanged) text for another SM count, malformed text and
+ * out-of-range values (tiles powers of two up to 16384, c_qc <= c_q, kcap
+ * 1..4, h_threads 64 or 128). */
+v3c_status v3c_tune_export(v3c_ctx* ctx, char* buf, size_t cap, size_t* len);
+v3c_status v3c_tune_import(v3c_ctx* ctx, const char* text);
 
 /* Device memory accounting, for leak checks and budgeting:
  *   out[0]  bytes of resident objects (commit objects, FRI states, snapshots)

@@ -40,6 +40,9 @@ _vp = ctypes.c_void_p
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
+_LOG_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p)
+
+
 class V3CError(RuntimeError):
     def __init__(self, status: int, detail: str = ""):
         self.status = status
@@ -140,6 +143,9 @@ SIGNATURES = {
     "v3c_wait_selftest": (ctypes.c_int, [_vp, _u32, _u32, _vp]),
     "v3c_mem_stats": (ctypes.c_int, [_vp, _u64p]),
     "v3c_serve_inject_failure": (ctypes.c_int, [_vp, _u32]),
+    "v3c_set_log": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "v3c_tune_export": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "v3c_tune_import": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     # include/v3c_fri.h
     "v3c_fri_begin": (ctypes.c_int, [_vp, _u64p, _u32, _u64p, ctypes.POINTER(FriCfg), _u64p, _u32, _u64p, _vp]),
     "v3c_fri_fold": (ctypes.c_int, [_vp, _u64, _u64p, _u32, _vp]),
@@ -590,6 +596,30 @@ class Context:
     def int_peak(self, reps: int = 10) -> tuple[float, float]:
         """Measured 32x32->64 wide multiply-adds per second and the SM MHz of that run."""
         return self.int_pipe_rate(0, reps)
+
+    def set_log(self, fn=None, max_level: int = 1):
+        """v3c_set_log: fn(level, text) receives the library's messages up to
+        max_level (0 failures, 1 resources and choices, 2 detail); None
+        silences it.  fn runs on library threads and must not call back."""
+        if fn is None:
+            self._log_cb = None
+            self._check(self.lib.v3c_set_log(self.h, None, None, -1))
+            return
+        cb = _LOG_FN(lambda user, level, text: fn(level, text.decode(errors="replace")))
+        self._log_cb = cb  # kept alive while the library may call it
+        self._check(self.lib.v3c_set_log(self.h, ctypes.cast(cb, _vp), None, max_level))
+
+    def tune_export(self) -> str:
+        """v3c_tune_export: the autotuner's choices as JSON text."""
+        n = ctypes.c_size_t(0)
+        self.lib.v3c_tune_export(self.h, None, 0, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        self._check(self.lib.v3c_tune_export(self.h, buf, n.value + 1, ctypes.byref(n)))
+        return buf.value.decode()
+
+    def tune_import(self, text: str):
+        """v3c_tune_import: adopt tile choices exported by tune_export."""
+        self._check(self.lib.v3c_tune_import(self.h, text.encode()))
 
     def mem_stats(self) -> dict:
         """v3c_mem_stats: resident bytes counted against the budget, bytes in use

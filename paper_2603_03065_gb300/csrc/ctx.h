@@ -2,6 +2,7 @@
 // the translation units that implement the C ABI (v3c.cu, fri.cu).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <map>
@@ -93,6 +94,11 @@ struct v3c_ctx {
     std::atomic<u64> launches{0};
     std::mutex err_mu;
     std::string err;
+    // Log callback (v3c_set_log); silent while log_fn is null.
+    std::mutex log_mu;
+    v3c_log_fn log_fn = nullptr;
+    void* log_user = nullptr;
+    int log_level = -1;
     Tiles tiles;
     u32* d_flag = nullptr;
     serve::Server* server = nullptr;
@@ -124,8 +130,11 @@ struct v3c_ctx {
 };
 
 
-// Records the error text of the last failing call and returns s.
+// Records the error text of the last failing call (and logs it at level 0)
+// and returns s.
 v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...);
+// Sends a message to the context's log callback if one is set for `level`.
+void log_msg(v3c_ctx* ctx, int level, const char* fmt, ...);
 // Makes the context's device current for this thread.
 v3c_status use_device(v3c_ctx* ctx);
 // Frees every FRI state of the context (fri.cu).
@@ -230,18 +239,43 @@ struct Batch {
 cudaEvent_t pool_event(v3c_ctx* ctx);
 
 // Brackets one stage launch with events on its stream when timing is on.
+// NVTX range over a scope.  On the host it spans the enqueue of the work it
+// names; a profiler lines it up with the kernels launched inside it.  With
+// no profiler attached the calls return at once.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
+// NVTX names of the stages, in v3c_stage_stats order.
+inline const char* stage_range_name(int id)
+{
+    static const char* const names[V3C_NUM_STAGES] = {
+        "v3c stage A", "v3c stage B", "v3c stage C", "v3c leaf hash", "v3c Merkle", "v3c FRI combination",
+        "v3c FRI fold", "v3c openings", "v3c SetEq", "v3c snapshot slots", "v3c snapshot codebook"};
+    return id >= 0 && id < V3C_NUM_STAGES ? names[id] : "v3c";
+}
+
+// Events around one stage launch (V3C_FLAG_TIMING, stage >= 0) and an NVTX
+// range named after `name_id` (the stage itself when not given).
 struct StageTimer {
     v3c_ctx* ctx;
     int stage;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
-    StageTimer(v3c_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str)
+    StageTimer(v3c_ctx* c, int st, cudaStream_t str, int name_id = -2) : ctx(c), stage(st), s(str)
     {
+        nvtxRangePushA(stage_range_name(name_id == -2 ? st : name_id));
         if ((ctx->cfg.flags & V3C_FLAG_TIMING) && st >= 0) {
             a = pool_event(ctx);
             if (a) cudaEventRecord(a, s);
         }
     }
+    ~StageTimer() { nvtxRangePop(); }
+    StageTimer(const StageTimer&) = delete;
+    StageTimer& operator=(const StageTimer&) = delete;
     void done()
     {
         if (!a) return;

@@ -791,6 +791,7 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
                          const v3c_fri_cfg* cfg, const uint64_t* h_betas, uint32_t n_betas, v3c_fri_id* out,
                          void* stream)
 {
+    NvtxScope range("v3c_fri_begin");
     if (!ctx) return V3C_EINVAL;
     if (!ids || !n_ids || !cfg || !out || !alpha || (n_betas && !h_betas))
         return fail(ctx, V3C_EINVAL, "v3c_fri_begin: NULL argument or no commitments");
@@ -906,7 +907,10 @@ v3c_status v3c_fri_begin(v3c_ctx* ctx, const v3c_commit_id* ids, uint32_t n_ids,
         const Object& o = objs[i];
         const u64* pw = st->alpha_pw + (size_t)ext * e0;
         CUtensorMap map;
-        if (combine_map(o, N, &map)) {
+        const bool tiled = combine_map(o, N, &map);
+        log_msg(ctx, 2, "FRI combination of a %u x 2^%u object: %s", o.c, log_N,
+                tiled ? "tensor-map tiles" : "register loads");
+        if (tiled) {
             StageTimer tm(ctx, 5, s);
             const int grid = (int)std::min<u64>((u64)2 * num_sms(), (N + kTmaRows - 1) / kTmaRows);
             if (ext == 2)

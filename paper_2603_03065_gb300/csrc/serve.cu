@@ -259,6 +259,7 @@ void run(Server* S)
         reap(S, true);
         fail_all_pending(S, V3C_ECANCELED);
     } catch (...) {
+        log_msg(S->ctx, 0, "serving: the scheduler thread failed; queued requests are cancelled");
         // The scheduler cannot go on: batches already on the device finish
         // (their requests become DONE), everything still queued fails.
         S->crashed = true;
@@ -311,6 +312,8 @@ v3c_status v3c_serve_start(v3c_ctx* ctx, const v3c_serve_cfg* cfg)
     }
     S = srv;
     srv->th = std::thread(run, srv);
+    log_msg(ctx, 1, "serving started: %u slots, batches up to %u requests", (unsigned)srv->slots.size(),
+            (unsigned)srv->cfg.max_batch);
     return V3C_OK;
 }
 
@@ -411,6 +414,7 @@ v3c_status v3c_serve_stop(v3c_ctx* ctx)
     }
     delete S;
     S = nullptr;
+    log_msg(ctx, 1, "serving stopped");
     return V3C_OK;
 }
 

@@ -72,6 +72,8 @@ namespace detail {
 
 // Arena words a batched commit of nb descs adds for block alignment.
 size_t arena_padding(v3c::u32 nb);
+// The context's log callback (v3c_set_log), if set for `level`.
+void log_msg(v3c_ctx* ctx, int level, const char* fmt, ...);
 
 namespace v3c {
 namespace detail {

@@ -413,6 +413,7 @@ using namespace v3c::detail;
 extern "C" v3c_status v3c_seteq(v3c_ctx* ctx, const v3c_seteq_desc* descs, uint32_t n, uint32_t* h_status,
                                 void* stream)
 {
+    NvtxScope range("v3c_seteq");
     if (!ctx) return V3C_EINVAL;
     if (!descs || !n) return fail(ctx, V3C_EINVAL, "v3c_seteq: no instances");
     u64 tiles = 0;

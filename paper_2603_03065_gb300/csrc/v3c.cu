@@ -65,6 +65,16 @@ using namespace v3c;
 
 static thread_local std::string g_err_copy;
 
+// The callback and its level, read under the log lock; called without it.
+static bool log_target(v3c_ctx* ctx, int level, v3c_log_fn* fn, void** user)
+{
+    std::lock_guard<std::mutex> g(ctx->log_mu);
+    if (!ctx->log_fn || level > ctx->log_level) return false;
+    *fn = ctx->log_fn;
+    *user = ctx->log_user;
+    return true;
+}
+
 v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...)
 {
     if (ctx) {
@@ -73,10 +83,38 @@ v3c_status fail(v3c_ctx* ctx, v3c_status s, const char* fmt, ...)
         va_start(ap, fmt);
         vsnprintf(buf, sizeof buf, fmt, ap);
         va_end(ap);
-        std::lock_guard<std::mutex> g(ctx->err_mu);
-        ctx->err = buf;
+        {
+            std::lock_guard<std::mutex> g(ctx->err_mu);
+            ctx->err = buf;
+        }
+        v3c_log_fn fn;
+        void* user;
+        if (log_target(ctx, 0, &fn, &user)) fn(user, 0, buf);
     }
     return s;
+}
+
+void log_msg(v3c_ctx* ctx, int level, const char* fmt, ...)
+{
+    v3c_log_fn fn;
+    void* user;
+    if (!ctx || !log_target(ctx, level, &fn, &user)) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    fn(user, level, buf);
+}
+
+v3c_status v3c_set_log(v3c_ctx* ctx, v3c_log_fn fn, void* user, int max_level)
+{
+    if (!ctx) return V3C_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->log_mu);
+    ctx->log_fn = fn;
+    ctx->log_user = user;
+    ctx->log_level = fn ? max_level : -1;
+    return V3C_OK;
 }
 
 
@@ -133,6 +171,7 @@ v3c_status get_plan(v3c_ctx* ctx, u32 log_n, u32 r, cudaStream_t s, Plan* out, u
     ctx->launches++;
     ctx->plans[key] = pe;
     *out = pe.plan;
+    log_msg(ctx, 1, "plan tables for log_n %u, rate_bits %u: %zu bytes", log_n, r, words * sizeof(u64));
     return V3C_OK;
 }
 
@@ -154,6 +193,7 @@ v3c_status arena_acquire(v3c_ctx* ctx, size_t words, cudaStream_t s, u64** out)
             return fail(ctx, V3C_ENOMEM, "scratch arena of %zu bytes: %s", want * 8, cudaGetErrorString(e));
         }
         a.words = want;
+        log_msg(ctx, 1, "scratch arena grown to %zu bytes", want * sizeof(u64));
         a.used = false;
     }
     if (a.used && a.last != s) CK(cudaStreamWaitEvent(s, a.ev, 0));
@@ -256,7 +296,7 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
                                                const TreeJob*, size_t, cudaStream_t),
                      StageList l, size_t g) -> v3c_status {
         if (!l.total) return V3C_OK;
-        StageTimer tm(ctx, timed ? id : -1, s);
+        StageTimer tm(ctx, timed ? id : -1, s, id);
         CK(fn(b, t, l, dl, dt, g, s));
         tm.done();
         ctx->launches++;
@@ -272,13 +312,13 @@ static v3c_status enqueue_stages(v3c_ctx* ctx, const Batch& b, const Tiles& t, c
             const u32 nj = b.chunks[g].second;
             StageList la = list(base + g, b.fac[g], nj), lb = list(base + b.chunks.size() + g, b.fbc[g], nj);
             if (la.total) {
-                StageTimer tm(ctx, timed ? 0 : -1, s);
+                StageTimer tm(ctx, timed ? 0 : -1, s, 0);
                 CK(launch_stage_a(dj, la, b.smem_a, t, 0, s));
                 tm.done();
                 ctx->launches++;
             }
             if (lb.total) {
-                StageTimer tm(ctx, timed ? 1 : -1, s);
+                StageTimer tm(ctx, timed ? 1 : -1, s, 1);
                 CK(launch_stage_b(dj, lb, b.smem_b, t, 0, s, all_spec(b.chunks[g].first, nj)));
                 tm.done();
                 ctx->launches++;
@@ -405,6 +445,7 @@ v3c_status launch_batch_graph(v3c_ctx* ctx, Batch& b, cudaStream_t s)
         e = cudaGraphInstantiate(&gi.exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(ctx, V3C_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        log_msg(ctx, 2, "captured a CUDA graph of %u kernels for a batch of %zu commits", gi.kernels, b.lde.size());
     }
     if (blob.size() != gi.bytes) return fail(ctx, V3C_ECUDA, "graph table size mismatch");
     CK(cudaEventSynchronize(gi.done));  // the previous replay of this instance read h_blob/d_blob
@@ -597,6 +638,8 @@ static v3c_status autotune_shape(v3c_ctx* ctx, u32 log_n, u32 r)
     cleanup();
     if (st) return st;
     ctx->tuned[key] = best;
+    log_msg(ctx, 1, "autotuned log_n %u, rate_bits %u: stage A %u columns, stage C %u/%u q, radix cap 2^%u, hash %u threads",
+            log_n, r, best.a_cols, best.c_q, best.c_qc, best.kcap, best.h_threads);
     return V3C_OK;
 }
 
@@ -739,6 +782,7 @@ v3c_status v3c_destroy(v3c_ctx* ctx)
 v3c_status v3c_lde(v3c_ctx* ctx, const uint64_t* d_cols, uint32_t c, uint32_t log_n, uint32_t rate_bits,
                    uint64_t* d_lde, uint32_t ld, void* stream)
 {
+    NvtxScope range("v3c_lde");
     if (!ctx) return V3C_EINVAL;
     if (!d_cols || !d_lde) return fail(ctx, V3C_EINVAL, "v3c_lde: NULL pointer");
     if (!shape_ok(c, log_n, rate_bits) || ld < c)
@@ -772,6 +816,7 @@ v3c_status v3c_lde(v3c_ctx* ctx, const uint64_t* d_cols, uint32_t c, uint32_t lo
 v3c_status v3c_merkle(v3c_ctx* ctx, const uint64_t* d_rows, uint32_t ld, uint32_t width, uint32_t log_rows,
                       uint32_t cap_height, uint64_t* d_tree, uint64_t* d_cap, void* stream)
 {
+    NvtxScope range("v3c_merkle");
     if (!ctx) return V3C_EINVAL;
     if (!d_rows || !d_cap || (!d_tree && cap_height != log_rows))
         return fail(ctx, V3C_EINVAL, "v3c_merkle: NULL pointer");
@@ -1047,6 +1092,7 @@ extern "C" {
 
 v3c_status v3c_commit(v3c_ctx* ctx, const v3c_commit_desc* descs, uint32_t nb, v3c_commit_id* ids, void* stream)
 {
+    NvtxScope range("v3c_commit");
     if (!ctx) return V3C_EINVAL;
     if (!descs || !ids || nb == 0) return fail(ctx, V3C_EINVAL, "v3c_commit: empty batch or NULL");
     v3c_status st = use_device(ctx);
@@ -1284,6 +1330,90 @@ v3c_status v3c_release(v3c_ctx* ctx, v3c_commit_id id)
 uint64_t v3c_kernel_launches(v3c_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
 uint64_t v3c_graph_replays(v3c_ctx* ctx) { return ctx ? ctx->graph_replays.load() : 0; }
+
+// Value of the non-negative integer field "key" inside [b, e), or -1.
+static long long tune_field(const char* b, const char* e, const char* key)
+{
+    const std::string pat = std::string("\"") + key + "\"";
+    const char* p = std::search(b, e, pat.begin(), pat.end());
+    if (p == e) return -1;
+    p += pat.size();
+    while (p < e && (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r')) p++;
+    if (p == e || *p != ':') return -1;
+    p++;
+    while (p < e && (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r')) p++;
+    if (p == e || *p < '0' || *p > '9') return -1;
+    long long v = 0;
+    while (p < e && *p >= '0' && *p <= '9' && v < (1ll << 40)) v = v * 10 + (*p++ - '0');
+    return v;
+}
+
+v3c_status v3c_tune_export(v3c_ctx* ctx, char* buf, size_t cap, size_t* len)
+{
+    if (!ctx || !len || (cap && !buf)) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    std::string t = "{\"sm_count\": " + std::to_string(num_sms()) + ", \"entries\": [";
+    bool first = true;
+    for (const auto& kv : ctx->tuned) {
+        const TuneEntry& e = kv.second;
+        char row[256];
+        snprintf(row, sizeof row,
+                 "%s{\"log_n\": %u, \"rate_bits\": %u, \"a_cols\": %u, \"c_q\": %u, \"c_qc\": %u, \"kcap\": %u, "
+                 "\"h_threads\": %u}",
+                 first ? "" : ", ", kv.first.first, kv.first.second, e.a_cols, e.c_q, e.c_qc, e.kcap, e.h_threads);
+        t += row;
+        first = false;
+    }
+    t += "]}";
+    *len = t.size();
+    if (cap < t.size() + 1)  // a size query (cap 0) is not logged as a failure
+        return cap ? fail(ctx, V3C_EINVAL, "v3c_tune_export: %zu bytes needed", t.size() + 1) : V3C_EINVAL;
+    memcpy(buf, t.c_str(), t.size() + 1);
+    return V3C_OK;
+}
+
+v3c_status v3c_tune_import(v3c_ctx* ctx, const char* text)
+{
+    if (!ctx || !text) return V3C_EINVAL;
+    v3c_status st = use_device(ctx);
+    if (st) return st;
+    const char* end = text + strlen(text);
+    const char* ent = strstr(text, "\"entries\"");
+    if (!ent) return fail(ctx, V3C_EINVAL, "v3c_tune_import: no \"entries\"");
+    const long long sms = tune_field(text, ent, "sm_count");
+    if (sms != (long long)num_sms())
+        return fail(ctx, V3C_EINVAL, "v3c_tune_import: tuned for %lld SMs, this device has %d", sms, num_sms());
+    const char* p = strchr(ent, '[');
+    if (!p) return fail(ctx, V3C_EINVAL, "v3c_tune_import: \"entries\" is not a list");
+    auto pow2 = [](long long x) { return x > 0 && !(x & (x - 1)); };
+    std::vector<std::pair<std::pair<u32, u32>, TuneEntry>> got;
+    for (p++;;) {
+        const char* ob = strchr(p, '{');
+        const char* rb = strchr(p, ']');
+        if (!rb) return fail(ctx, V3C_EINVAL, "v3c_tune_import: unterminated \"entries\"");
+        if (!ob || rb < ob) break;
+        const char* oe = strchr(ob, '}');
+        if (!oe || oe > end) return fail(ctx, V3C_EINVAL, "v3c_tune_import: unterminated entry");
+        const char* names[7] = {"log_n", "rate_bits", "a_cols", "c_q", "c_qc", "kcap", "h_threads"};
+        long long f[7];
+        for (int i = 0; i < 7; i++) {
+            f[i] = tune_field(ob, oe, names[i]);
+            if (f[i] < 0) return fail(ctx, V3C_EINVAL, "v3c_tune_import: entry %zu has no \"%s\"", got.size(), names[i]);
+        }
+        if (f[0] > V3C_MAX_LOG_N || f[1] > V3C_MAX_RATE_BITS || f[0] + f[1] > V3C_MAX_LOG_LDE || !pow2(f[2]) ||
+            !pow2(f[3]) || !pow2(f[4]) || f[2] > 16384 || f[3] > 16384 || f[4] > f[3] || f[5] < 1 || f[5] > 4 ||
+            (f[6] != 64 && f[6] != 128))
+            return fail(ctx, V3C_EINVAL, "v3c_tune_import: entry %zu is out of range", got.size());
+        got.push_back({{(u32)f[0], (u32)f[1]}, TuneEntry{(u32)f[2], (u32)f[3], (u32)f[4], (u32)f[5], (u32)f[6]}});
+        p = oe + 1;
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (const auto& kv : got) ctx->tuned[kv.first] = kv.second;
+    log_msg(ctx, 1, "imported the tuned tiles of %zu shapes", got.size());
+    return V3C_OK;
+}
 
 v3c_status v3c_mem_stats(v3c_ctx* ctx, uint64_t* out)
 {
