@@ -628,7 +628,9 @@ EncodeTiledFn encode_tiled()
 // tile; the caller then takes the register-load kernel.
 bool combine_map(const Object& o, u64 N, CUtensorMap* map)
 {
-    if (o.c < kTmaCols || N < kTmaRows || N > 0xFFFFFFFFull || ((size_t)o.ld * 8) % 16 ||
+    // Item counters are 32-bit: tiles x column chunks must stay below 2^32.
+    const u64 items = ((N + kTmaRows - 1) / kTmaRows) * (((u64)o.c + kTmaCols - 1) / kTmaCols);
+    if (o.c < kTmaCols || N < kTmaRows || N > 0xFFFFFFFFull || items >= (1ull << 32) || ((size_t)o.ld * 8) % 16 ||
         (reinterpret_cast<uintptr_t>(o.lde) & 15))
         return false;
     EncodeTiledFn fn = encode_tiled();
