@@ -37,7 +37,7 @@ using gl::u64;
 
 constexpr u32 kSeqThreads = 256;
 constexpr u32 kSeqPer = 8;
-constexpr u32 kSeqMinBlocks = 2;  // resident CTAs per SM the scan is compiled for
+constexpr u32 kSeqMinBlocks = 3;  // resident CTAs per SM the scan is compiled for (80 registers)
 constexpr u32 kSeqTile = kSeqThreads * kSeqPer;
 
 struct SeqJob {
