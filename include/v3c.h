@@ -348,8 +348,10 @@ v3c_status v3c_mem_stats(v3c_ctx* ctx, uint64_t* out);
  * + coset + forward DFT), 2 = stage C (forward DFTs and row writes), 3 =
  * leaf hash, 4 = Merkle levels, 5 = FRI batch combination, 6 = FRI folds and
  * final coefficients, 7 = opening gathers (v3c_fri_query, v3c_open_batch,
- * v3c_snapshot_open_lists), 8 = SetEq grand products (three launches as one
- * stage), 9 = snapshot slot digests, 10 = snapshot codebook digest. */
+ * v3c_snapshot_open_lists), 8 = SetEq grand products (the scan and the
+ * zeroing launch as one stage), 9 = snapshot slot digests, 10 = snapshot
+ * codebook digest.  Each stage launch also opens an NVTX range named after
+ * its stage, with or without V3C_FLAG_TIMING. */
 #define V3C_FLAG_TIMING 0x2u
 #define V3C_NUM_STAGES 11
 typedef struct {
