@@ -51,7 +51,9 @@
  * on `stream` (a cudaStream_t, NULL = legacy default stream) after the listed
  * commitments are complete.  The calls that return host data wait for the
  * work they read.  Statuses: EINVAL (bad argument, or a call out of order),
- * ENOTFOUND (unknown id), ENOMEM (HBM budget or allocation), ECUDA. */
+ * ENOTFOUND (unknown id), ENOMEM (HBM budget or allocation), ECUDA,
+ * ETIMEDOUT (a bounded wait of the combination's copy pipeline gave up;
+ * returned by the first call that reads a result of that FRI state back). */
 #pragma once
 #include "v3c.h"
 

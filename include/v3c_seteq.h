@@ -8,15 +8,18 @@
  * Z_L = 1 exactly when the two products agree.  For random alpha and beta,
  * that means the multisets of tuples agree (with high probability).  The GPU evaluates
  *   Z_i = [prod_{k<i} (alpha - x_k)] * [prod_{k>=i} (alpha - y_k)] * [prod_k (alpha - y_k)]^-1,
- * with two product scans and one field inversion per instance, instead of an
- * inversion per element.  If some alpha - y_k is zero, the inverse is taken
- * as 0: the instance's whole column is then written as zeros (Z_0 = 0 marks
- * it), and its status is 1.
+ * in tiles of 2048 elements: product scans inside a tile, the products of
+ * the earlier tiles carried by a decoupled look-back, and one field
+ * inversion per tile instead of one per element.  If some alpha - y_k is
+ * zero, the inverse is taken as 0: the instance's whole column is then
+ * written as zeros (Z_0 = 0 marks it), and its status is 1.
  *
- * Many instances run in one launch per phase.  Inputs are canonical, and
+ * All instances run in one scan launch (and one zeroing launch that only
+ * touches degenerate instances).  Inputs are canonical, and
  * all pointers are device memory: X, Y [L][T] row-major, Z [L + 1].
  * Statuses: EINVAL (NULL pointer, T outside 1..32, L = 0 or L >= 2^40, or a
- * non-canonical alpha or beta), ENOMEM, ECUDA. */
+ * non-canonical alpha or beta), ENOMEM, ECUDA, ETIMEDOUT (a bounded wait of
+ * the look-back gave up; reported when the call waits). */
 #pragma once
 #include "v3c.h"
 
